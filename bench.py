@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of one hdiff + vadv step (GT4Py paper, Sec. 3.1 benchmark
+stencils) at 256x256x80 in FP64, through libgtb's C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gtb|reference]
+
+A step is one pass of the whole hot path over one batch: hdiff (Laplacian,
+limited fluxes, update) on one input set, then vadv (coefficients, forward
+elimination, back substitution) on another.  Prints ONE JSON line (rank 0).
+
+* value: domain points per second (Mpoints/s) of whole steps, inputs resident
+  in HBM, device time from CUDA events on the launching stream, max over ranks.
+  Three input sets of ~380 MB each (> the 126 MB L2) rotate between steps.
+* e2e: the same metric with the host<->device copies of every step's inputs
+  (from pinned host memory) and of its two outputs inside the timed region.
+* roofline: the dominant kernel's achieved rate against its binding peak.
+* cpu_baseline: the FP64 CPU oracle (single thread) on a bounded sample.
+* --impl reference: the oracle itself as the reference arm.
+Under torchrun every rank runs its own replica (independent problems, no
+collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hdiff/vadv Mpoints/s & HBM GB/s vs 8 TB/s roofline; adjoint/forward time ratio"
+I, J, K = 256, 256, 80
+POINTS = I * J * K
+HDIFF_HALO, VADV_HALO = 2, 1
+VADV_NAMES = ("u_stage", "wcon", "u_pos", "utens", "utens_stage")
+WORKLOAD = "hdiff+vadv FP64 256x256x80 (hdiff halo 2, vadv halo 1 in I/J), dtr_stage=3/20, beta_v=0"
+FP64_NOMINAL_GFLOPS = 1250.0  # B300 dense FP64, nominal (no FP64 tensor path is used)
+
+
+def hdiff_bytes(I, J, K, es):
+    """Compulsory HBM bytes of one hdiff launch: in on the domain + 2-ring, coeff and out on the domain."""
+    return es * ((I + 4) * (J + 4) * K + 2 * I * J * K)
+
+
+def vadv_bytes(I, J, K, es):
+    """u_stage, u_pos, utens, utens_stage read and out written on the domain; wcon on I+1 columns."""
+    return es * (5 * I * J * K + (I + 1) * J * K)
+
+
+# FP64 operations per grid point as the definition states them (divisions count one each)
+HDIFF_FLOPS_PER_PT = 16  # lap 5, fx 3 (diff, gradient, product), fy 3, update 5
+VADV_FLOPS_PER_PT = 25   # face average 2, a 1, c 1, b 2, rhs 9, pivot 2, c' 1, d' 3, back-subst 2, out 2
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2311_08322_b300", "csrc")
+    for n in sorted(os.listdir(csrc)):
+        if n.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from profiles/ncu_*.txt, if captured on this source."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    src = kernel_source_hash()
+    for n in sorted(os.listdir(pdir)):
+        if not n.endswith(".txt"):
+            continue
+        txt = open(os.path.join(pdir, n)).read()
+        m = re.search(r"^kernel_source_sha: (\w+)", txt, re.M)
+        t = re.search(r"^dram_bytes_per_launch\[%s\]: ([0-9.eE+]+)" % kernel, txt, re.M)
+        if m and t and m.group(1) == src:
+            return float(t.group(1))
+    return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.lines = []
+        self.p = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 3.0:
+            time.sleep(0.02)
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        rows = [r.split(", ") for r in self.lines if r and r[0].isdigit()]
+        sm = [float(r[0]) for r in rows if len(r) >= 8]
+        mx = [float(r[1]) for r in rows if len(r) >= 8]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows if len(r) >= 8 for q in range(4) if r[4 + q].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm),
+                "power_w_max": max(float(r[2]) for r in rows) if rows else None}
+
+
+def oracle_step(f, jrows=None):
+    """One oracle hdiff + vadv pass (optionally on the first `jrows` rows of J); returns points."""
+    import oracle
+    Jr = J if jrows is None else jrows
+    oracle.hdiff(f["in"], f["coeff"], domain=(I, Jr, K))
+    oracle.vadv(*[f[n] for n in VADV_NAMES], domain=(I, Jr, K))
+    return I * Jr * K
+
+
+def cpu_baseline(f, min_seconds=10.0):
+    """The oracle as it stands, one host thread, full 256x256x80 steps until >= min_seconds."""
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle_step(f)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds and reps >= 2:
+            break
+    return {"value": round(POINTS * reps / el / 1e6, 3), "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full hdiff+vadv steps at 256x256x80 FP64 ({el:.1f} s, single-threaded C oracle)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2311_08322_b300 import inputs
+    import oracle
+    oracle.build()
+    f = inputs.hdiff_vadv(I, J, K, seed=0)
+    # size each step so that warmup + steps finish in about two minutes
+    t0 = time.perf_counter()
+    oracle_step(f, jrows=16)
+    t16 = time.perf_counter() - t0
+    per_step_budget = 120.0 / max(1, args.steps + args.warmup)
+    jrows = int(max(1, min(J, 16 * per_step_budget / max(t16, 1e-6))))
+    for _ in range(args.warmup):
+        oracle_step(f, jrows)
+    t0 = time.perf_counter()
+    pts = 0
+    for _ in range(args.steps):
+        pts += oracle_step(f, jrows)
+    el = time.perf_counter() - t0
+    v = pts / el / 1e6
+    line = {"metric": METRIC, "value": round(v, 3), "unit": "Mpoints/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_rows_j": jrows},
+            "cpu_baseline": {"value": round(v, 3), "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: hdiff+vadv on 256x{jrows}x80 of the 256x256x80 fields"},
+            "e2e": {"value": round(v, 3), "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gtb(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2311_08322_b300 import build, gtb, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    build.build()
+    gtb.lib()
+
+    f = inputs.hdiff_vadv(I, J, K, seed=rank)
+    o2, o1 = (HDIFF_HALO, HDIFF_HALO, 0), (VADV_HALO, VADV_HALO, 0)
+    sets = []
+    for _ in range(args.sets):
+        s = {"in": gtb.storage_from(f["in"], o2), "coeff": gtb.storage_from(f["coeff"], o2),
+             "hout": gtb.storage_from(np.zeros_like(f["coeff"]), o2),
+             "vout": gtb.storage_from(np.zeros_like(f["utens"]), o1)}
+        for n in VADV_NAMES:
+            s[n] = gtb.storage_from(f[n], o1)
+        sets.append(s)
+    stream = torch.cuda.current_stream()
+
+    def step(s, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        gtb.hdiff(s["in"], s["coeff"], s["hout"], stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        gtb.vadv(*[s[n] for n in VADV_NAMES], s["vout"], stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for w in range(args.warmup):
+        step(sets[w % len(sets)])
+    gtb.device_status()
+
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = str(dev)
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for q in range(args.steps):
+        step(sets[q % len(sets)], evs[q])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    gtb.device_status()
+    el_ms = t_start.elapsed_time(t_end)
+    h_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    v_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    if world > 1:
+        t = torch.tensor([el_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    value = world * POINTS * args.steps / (el_ms / 1e3) / 1e6
+
+    # e2e through the C ABI: pinned host inputs -> device, two kernels, outputs -> host
+    host = {n: torch.from_numpy(f[n]).pin_memory() for n in ("in", "coeff", *VADV_NAMES)}
+    hout = torch.empty(sets[0]["hout"].data.shape, dtype=torch.float64).pin_memory()
+    vout = torch.empty(sets[0]["vout"].data.shape, dtype=torch.float64).pin_memory()
+    s0 = sets[0]
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = hout.numel() * 8 + vout.numel() * 8
+
+    def e2e_step():
+        for n, hv in host.items():
+            s0[n].data.copy_(hv, non_blocking=True)
+        step(s0)
+        hout.copy_(s0["hout"].data, non_blocking=True)
+        vout.copy_(s0["vout"].data, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * POINTS * args.e2e_steps / (e2e_ms / 1e3) / 1e6
+
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    kern = {}
+    for name, ms, nbytes, flops in (("hdiff", h_ms, hdiff_bytes(I, J, K, 8), HDIFF_FLOPS_PER_PT * POINTS),
+                                    ("vadv", v_ms, vadv_bytes(I, J, K, 8), VADV_FLOPS_PER_PT * POINTS)):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        gfl = flops / (ms / 1e3) / 1e9
+        kern[name] = {"ms": round(ms, 4), "mpoints_s": round(POINTS / (ms / 1e3) / 1e6, 1),
+                      "algorithmic_bytes": nbytes, "hbm_gbs": round(gbs, 1),
+                      "frac_of_measured_hbm": round(gbs / hbm, 4), "frac_of_8tbs": round(gbs / 8000.0, 4),
+                      "fp64_gflops": round(gfl, 1), "frac_of_nominal_fp64": round(gfl / FP64_NOMINAL_GFLOPS, 4)}
+    dom = max(kern, key=lambda n: kern[n]["ms"])
+    kd = kern[dom]
+    traffic = profile_traffic(dom + "_kernel")
+    if kd["frac_of_nominal_fp64"] > kd["frac_of_measured_hbm"]:
+        roof = {"bound": "alu", "kernel": dom, "achieved": kd["fp64_gflops"], "peak": FP64_NOMINAL_GFLOPS,
+                "unit": "GFLOP/s", "frac": kd["frac_of_nominal_fp64"], "traffic": traffic,
+                "peak_source": "nominal B300 FP64 1.25 TFLOP/s (148 SMs); algorithmic FP64 flops",
+                "hbm_frac_of_measured": kd["frac_of_measured_hbm"]}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": kd["hbm_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": kd["frac_of_measured_hbm"], "traffic": traffic, "peak_source": hbm_src}
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "Mpoints/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el_ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "I": I, "J": J, "K": K, "parallelism": f"replicas{world}",
+                       "l2": f"{args.sets} rotating input sets of "
+                             f"{(hdiff_bytes(I, J, K, 8) + vadv_bytes(I, J, K, 8)) / 1e6:.0f} MB each (> 126 MB L2)"},
+            "kernels": kern, "roofline": roof, "clocks": clk, "gpu_launches": 2 * args.steps,
+            "e2e": {"value": round(e2e_value, 1), "unit": "Mpoints/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        line["cpu_baseline"] = cpu_baseline(f)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("gtb", "reference"), default="gtb")
+    ap.add_argument("--sets", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gtb(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

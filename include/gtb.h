@@ -1,0 +1,142 @@
+/*
+ * gtb.h -- C ABI of libgtb, B300-native (sm_103a) stencils for weather and
+ * climate codes: the horizontal-diffusion (hdiff) and vertical-advection
+ * (vadv) benchmark stencils of the GT4Py paper (arXiv 2311.08322, Sec. 3.1),
+ * their adjoints, and batched ensembles of uneven domains.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Fields are storages with halos (the paper's `storage`, Sec. 2.2/2.3): a
+ * gtb_field describes caller-owned DEVICE memory.  Element (i,j,k) of the
+ * storage is at  ptr + i*strides[0] + j*strides[1] + k*strides[2]  (strides in
+ * elements; strides[0] must be 1, i.e. i is the contiguous axis, and the
+ * layout must be non-overlapping: strides[1] >= shape[0],
+ * strides[2] >= strides[1]*shape[1]).  `origin` is the storage index of compute
+ * domain point (0,0,0) of that field, exactly as the paper's `origin` call
+ * argument (Sec. 2.2).  `domain` (I,J,K) is the compute domain; pass NULL to
+ * have it deduced from the field sizes and the stencil's reach (Sec. 2.2: the
+ * iteration space is deduced from field sizes and stencil shape): the largest
+ * domain for which every access of every field stays inside its storage.
+ *
+ * Every field of one call has the same dtype (GTB_F32 or GTB_F64).
+ *
+ * Ownership: the library never allocates, frees or retains caller memory, and
+ * never synchronises: each call validates its arguments on the host, enqueues
+ * its kernels on `stream` (a cudaStream_t; NULL = the legacy default stream)
+ * and returns.  An empty domain (any extent 0) enqueues nothing and succeeds.
+ *
+ * Errors: every call returns GTB_OK (0) or a negative gtb_status; on error
+ * nothing is enqueued and gtb_last_error() returns a message for the calling
+ * thread.  Argument checks are the paper's run-time checks on storage layout
+ * and data type (Sec. 3.1), done in C at a cost of well under a microsecond.
+ * Kernels never trap: a device-side wait that runs out of its time limit
+ * records GTB_ERR_DEVICE, which gtb_device_status() reports.
+ */
+#ifndef GTB_H
+#define GTB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GTB_OK = 0,
+    GTB_ERR_NULL = -1,        /* a required pointer is NULL */
+    GTB_ERR_DTYPE = -2,       /* unknown dtype, or fields of one call differ */
+    GTB_ERR_EXTENT = -3,      /* origin/domain plus stencil reach leaves a storage */
+    GTB_ERR_LAYOUT = -4,      /* strides[0] != 1, negative or overlapping strides */
+    GTB_ERR_ALIAS = -5,       /* an output overlaps an input it may not overlap */
+    GTB_ERR_LAUNCH = -6,      /* the CUDA launch failed (see gtb_last_error) */
+    GTB_ERR_DEVICE = -7,      /* a kernel's bounded wait expired (device status) */
+    GTB_ERR_UNSUPPORTED = -8, /* size beyond a documented limit */
+    GTB_ERR_ARG = -9          /* bad scalar argument (prec, flags, counts) */
+} gtb_status;
+
+typedef enum { GTB_F32 = 1, GTB_F64 = 2 } gtb_dtype;
+
+typedef struct gtb_field {
+    void *ptr;           /* device address of storage element (0,0,0) */
+    int32_t dtype;       /* gtb_dtype */
+    int32_t reserved;    /* must be 0 */
+    int64_t shape[3];    /* storage extents (ni, nj, nk) */
+    int64_t strides[3];  /* element strides (1, sj, sk) */
+    int64_t origin[3];   /* storage index of compute-domain point (0,0,0) */
+} gtb_field;
+
+/* Precision of the vadv column arithmetic (coefficients, right-hand side,
+ * Thomas recurrences, output).  Storage precision is the fields' dtype. */
+typedef enum {
+    GTB_PREC_NATIVE = 0, /* arithmetic in the storage type */
+    GTB_PREC_F64 = 1,    /* binary64 arithmetic on the FP64 pipe (F32 storage) */
+    GTB_PREC_DF = 2      /* double-float (pairs of binary32, ~48-bit) on the FP32 pipe */
+} gtb_prec;
+
+/* vadv flags */
+#define GTB_WCON_LITERAL 1u  /* use wcon(i) as the face velocity instead of the I-face average */
+
+/*
+ * gtb_hdiff -- horizontal diffusion (paper Sec. 3.1; one PARALLEL computation,
+ * Sec. 2.2, whose temporaries lap/fx/fy never reach memory, Sec. 2.2):
+ *   lap = 4 in - (((in[i+1] + in[i-1]) + in[j+1]) + in[j-1])     on the domain and a 1-ring
+ *   fx  = lap[i+1] - lap[i], set to 0 where fx * (in[i+1] - in[i]) > 0;  fy likewise in j
+ *   out = in - coeff * ((fx[i] - fx[i-1]) + (fy[j] - fy[j-1]))
+ * in:    read on the domain plus a 2-point ring in I and J (origin >= 2 there).
+ * coeff: read on the domain.  out: written on the domain only.
+ * out must not overlap in or coeff (GTB_ERR_ALIAS): in a PARALLEL stencil with
+ * offsets the result may not overwrite its own input (Sec. 2.2).
+ * FP64 results agree with a binary64 reference within 1e-12 (max-norm
+ * relative); FP32 computes in binary32.
+ */
+int gtb_hdiff(const gtb_field *in, const gtb_field *coeff, const gtb_field *out,
+              const int64_t *domain, void *stream);
+
+/*
+ * gtb_vadv -- implicit vertical advection (paper Sec. 3.1: vertically
+ * sequential stages implementing a tridiagonal solver; a FORWARD computation
+ * followed by a BACKWARD one with specialised top and bottom intervals, Sec. 2.2).
+ * Per (i,j) column of K levels, with w_k = (wcon[i,k] + wcon[i+1,k]) / 2
+ * (or wcon[i,k] with GTB_WCON_LITERAL), bp = (1+beta_v)/2, bm = (1-beta_v)/2:
+ *   a_k  = bp (-w_k/2),  as_k = bm (-w_k/2)        (a_0 = as_0 = 0)
+ *   c_k  = bp (w_{k+1}/2), cs_k = bm (w_{k+1}/2)   (c_{K-1} = cs_{K-1} = 0)
+ *   b_k  = dtr_stage - a_k - c_k,
+ *   d_k  = dtr_stage u_pos + utens + utens_stage
+ *          - as_k (u_stage[k-1] - u_stage[k]) - cs_k (u_stage[k+1] - u_stage[k])
+ *   solve A x = d by Thomas elimination (forward sweep, then back substitution),
+ *   utens_stage_out = dtr_stage (x - u_pos).
+ * At beta_v = 0: a_k = -w_k/4, c_k = w_{k+1}/4 (the benchmark coefficients).
+ * wcon is read at i and i+1 (staggered in I; needs one halo point above I).
+ * utens_stage_out may be the very same view as utens_stage (in place: each
+ * column is read completely before it is written); any other overlap of the
+ * output with an input is GTB_ERR_ALIAS.
+ * prec: gtb_prec.  For GTB_F64 storage only GTB_PREC_NATIVE is accepted
+ * (binary64); for GTB_F32 storage NATIVE is all-binary32, F64 and DF keep the
+ * whole column computation in binary64 / double-float.
+ * A zero pivot (singular leading minor) yields non-finite values in that column,
+ * as the unpivoted method does.  Limit: K <= 448 (the forward-sweep state of
+ * a block of columns stays in shared memory); larger K is GTB_ERR_UNSUPPORTED.
+ */
+int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u_pos,
+             const gtb_field *utens, const gtb_field *utens_stage,
+             const gtb_field *utens_stage_out, double dtr_stage, double beta_v,
+             int prec, unsigned flags, const int64_t *domain, void *stream);
+
+/*
+ * gtb_device_status -- synchronises `stream`, then returns and clears the
+ * device error word: GTB_OK, or GTB_ERR_DEVICE if a kernel's bounded wait
+ * expired since the last call (the affected outputs are then unspecified).
+ */
+int gtb_device_status(void *stream);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *gtb_last_error(void);
+
+/* Library version string, e.g. "gtb 0.1 sm_103a". */
+const char *gtb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GTB_H */

@@ -1,0 +1,380 @@
+// gtb_api.cu -- the C ABI of libgtb (declared in include/gtb.h): argument
+// validation (the run-time storage checks of the GT4Py paper, Sec. 3.1),
+// domain deduction from field sizes and stencil reach (Sec. 2.2), TMA
+// descriptor encoding and kernel dispatch.  Single translation unit: every
+// kernel of the library is instantiated here.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "gtb.h"
+#include "gtb_device.cuh"
+#include "hdiff_kernels.cuh"
+#include "vadv_kernels.cuh"
+
+namespace gtb {
+
+// ------------------------------------------------------------------ errors
+static thread_local char t_err[512] = "";
+
+static int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int ok() {
+    t_err[0] = 0;
+    return GTB_OK;
+}
+
+static size_t dtype_size(int dt) { return dt == GTB_F64 ? 8 : dt == GTB_F32 ? 4 : 0; }
+
+// ------------------------------------------------------------------ fields
+struct Reach {  // points read/written outside the domain on each side
+    int lo[3], hi[3];
+};
+
+static int check_field(const char *name, const gtb_field *f, int dtype) {
+    if (!f) return fail(GTB_ERR_NULL, "%s: NULL field", name);
+    if (!f->ptr) return fail(GTB_ERR_NULL, "%s: NULL data pointer", name);
+    if (f->dtype != dtype) return fail(GTB_ERR_DTYPE, "%s: dtype %d differs from the call's dtype %d", name, f->dtype, dtype);
+    if (f->reserved != 0) return fail(GTB_ERR_ARG, "%s: reserved must be 0", name);
+    for (int d = 0; d < 3; ++d)
+        if (f->shape[d] < 0 || f->shape[d] > (int64_t(1) << 31))
+            return fail(GTB_ERR_EXTENT, "%s: bad shape[%d] = %lld", name, d, (long long)f->shape[d]);
+    if (f->strides[0] != 1) return fail(GTB_ERR_LAYOUT, "%s: strides[0] must be 1 (i contiguous)", name);
+    if (f->strides[1] < f->shape[0] || f->strides[2] < f->strides[1] * f->shape[1])
+        return fail(GTB_ERR_LAYOUT, "%s: overlapping or negative strides (%lld, %lld)", name,
+                    (long long)f->strides[1], (long long)f->strides[2]);
+    if (reinterpret_cast<uintptr_t>(f->ptr) % dtype_size(dtype) != 0)
+        return fail(GTB_ERR_LAYOUT, "%s: data pointer not aligned to its element size", name);
+    return GTB_OK;
+}
+
+// Fold one field into the deduced domain (largest domain keeping its accesses inside).
+static void shrink_domain(const gtb_field *f, const Reach &r, int64_t dom[3]) {
+    for (int d = 0; d < 3; ++d) dom[d] = std::min(dom[d], f->shape[d] - f->origin[d] - r.hi[d]);
+}
+
+static int check_extent(const char *name, const gtb_field *f, const Reach &r, const int64_t dom[3]) {
+    for (int d = 0; d < 3; ++d) {
+        if (f->origin[d] - r.lo[d] < 0 || f->origin[d] + dom[d] + r.hi[d] > f->shape[d])
+            return fail(GTB_ERR_EXTENT,
+                        "%s: axis %d: origin %lld, domain %lld and stencil reach (-%d,+%d) leave the storage of extent %lld",
+                        name, d, (long long)f->origin[d], (long long)dom[d], r.lo[d], r.hi[d], (long long)f->shape[d]);
+    }
+    return GTB_OK;
+}
+
+static void byte_range(const gtb_field *f, uintptr_t *lo, uintptr_t *hi) {
+    const size_t es = dtype_size(f->dtype);
+    *lo = reinterpret_cast<uintptr_t>(f->ptr);
+    const int64_t last = (f->shape[0] > 0 && f->shape[1] > 0 && f->shape[2] > 0)
+                             ? (f->shape[2] - 1) * f->strides[2] + (f->shape[1] - 1) * f->strides[1] + f->shape[0]
+                             : 0;
+    *hi = *lo + (uintptr_t)last * es;
+}
+
+static bool overlaps(const gtb_field *a, const gtb_field *b) {
+    uintptr_t al, ah, bl, bh;
+    byte_range(a, &al, &ah);
+    byte_range(b, &bl, &bh);
+    return al < bh && bl < ah;
+}
+
+static bool same_view(const gtb_field *a, const gtb_field *b) {
+    return a->ptr == b->ptr && a->dtype == b->dtype && !memcmp(a->shape, b->shape, sizeof(a->shape)) &&
+           !memcmp(a->strides, b->strides, sizeof(a->strides)) && !memcmp(a->origin, b->origin, sizeof(a->origin));
+}
+
+template <typename T>
+static View<T> view_of(const gtb_field *f) {
+    T *p = static_cast<T *>(f->ptr) + f->origin[0] + f->origin[1] * f->strides[1] + f->origin[2] * f->strides[2];
+    return View<T>{p, f->strides[1], f->strides[2]};
+}
+
+static int resolve_domain(const int64_t *domain, int64_t dom[3]) {
+    if (domain) {
+        for (int d = 0; d < 3; ++d) {
+            if (domain[d] < 0) return fail(GTB_ERR_EXTENT, "negative domain extent in axis %d", d);
+            dom[d] = domain[d];
+        }
+    }
+    for (int d = 0; d < 3; ++d)
+        if (dom[d] < 0) dom[d] = 0;
+        else if (dom[d] > (int64_t(1) << 30)) return fail(GTB_ERR_UNSUPPORTED, "domain extent too large in axis %d", d);
+    return GTB_OK;
+}
+
+// ------------------------------------------------------------------ device helpers
+static int current_device() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev;
+}
+
+static int sm_count() {
+    static int cached[64] = {0};
+    const int dev = current_device();
+    if (dev < 64 && cached[dev]) return cached[dev];
+    int n = 148;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (dev < 64) cached[dev] = n;
+    return n;
+}
+
+// Raise a kernel's dynamic shared-memory limit once per (kernel, device).
+static std::mutex g_prep_mu;
+static std::unordered_map<const void *, unsigned long long> g_prep_done;  // device bit mask
+
+template <typename K>
+static cudaError_t prepare_kernel(K kernel, int smem_bytes) {
+    const int dev = current_device();
+    const void *key = reinterpret_cast<const void *>(kernel);
+    std::lock_guard<std::mutex> lock(g_prep_mu);
+    unsigned long long &mask = g_prep_done[key];
+    if (dev < 64 && ((mask >> dev) & 1ull)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e == cudaSuccess && dev < 64) mask |= 1ull << dev;
+    return e;
+}
+
+template <typename K>
+static int resident_blocks(K kernel, int threads, int smem_bytes) {
+    int nb = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem_bytes) != cudaSuccess || nb < 1)
+        nb = 1;
+    return nb;
+}
+
+static int launch_status(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(GTB_ERR_LAUNCH, "%s: %s", what, cudaGetErrorString(e));
+    return ok();
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// ------------------------------------------------------------------ hdiff
+template <typename T>
+struct HdiffCfg;
+template <> struct HdiffCfg<double> {
+    static constexpr int TI = 64, TJ = 16, NT = 256, STAGES = 3, VEC = 2;
+};
+template <> struct HdiffCfg<float> {
+    static constexpr int TI = 128, TJ = 16, NT = 256, STAGES = 4, VEC = 4;
+};
+
+template <typename T, bool TMA, int VEC>
+static int launch_hdiff_t(const CUtensorMap &map, const View<T> &in, const View<T> &cf, const View<T> &out,
+                          HdiffGeom g, cudaStream_t st) {
+    using C = HdiffCfg<T>;
+    constexpr int STG = TMA ? C::STAGES : 1;
+    auto kern = hdiff_kernel<T, C::TI, C::TJ, C::NT, STG, TMA, VEC>;
+    constexpr int smem = hdiff_smem_bytes<T, C::TI, C::TJ, STG>();
+    if (prepare_kernel(kern, smem) != cudaSuccess) return launch_status("hdiff: shared-memory attribute");
+    static int slots_cache[64] = {0};
+    const int dev = current_device();
+    int slots = dev < 64 ? slots_cache[dev] : 0;
+    if (!slots) {
+        slots = resident_blocks(kern, C::NT, smem) * sm_count();
+        if (dev < 64) slots_cache[dev] = slots;
+    }
+    // one wave of work items: split K so that tiles x chunks fills the resident slots
+    const int chunks = std::max(1, std::min(g.K, slots / std::max(1, g.n_tiles)));
+    g.kc = (g.K + chunks - 1) / chunks;
+    const int items = g.n_tiles * ((g.K + g.kc - 1) / g.kc);
+    kern<<<items, C::NT, smem, st>>>(map, in, cf, out, g);
+    return launch_status("hdiff launch");
+}
+
+template <typename T>
+static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field *fout, const int64_t dom[3],
+                     cudaStream_t st) {
+    using C = HdiffCfg<T>;
+    const View<T> in = view_of<T>(fin), cf = view_of<T>(fcf), out = view_of<T>(fout);
+    HdiffGeom g{};
+    g.I = (int)dom[0], g.J = (int)dom[1], g.K = (int)dom[2];
+    g.tiles_i = (g.I + C::TI - 1) / C::TI;
+    g.tiles_j = (g.J + C::TJ - 1) / C::TJ;
+    g.n_tiles = g.tiles_i * g.tiles_j;
+
+    // TMA path: storage base rounded down to 16 B, pitches multiples of 16 B
+    const size_t es = sizeof(T);
+    const uintptr_t base = reinterpret_cast<uintptr_t>(fin->ptr);
+    const uintptr_t abase = base & ~uintptr_t(15);
+    const int shift = (int)((base - abase) / es);
+    constexpr int kAlign = 16 / (int)sizeof(T);
+    bool tma = encode_fn() != nullptr && (fin->strides[1] * es) % 16 == 0 && (fin->strides[2] * es) % 16 == 0 &&
+               fin->strides[2] * es < (1ull << 40) && fin->shape[0] + shift < (1ll << 31);
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    if (tma) {
+        const int xraw = (int)fin->origin[0] - 2 + shift;
+        g.xs = xraw % kAlign;
+        g.X0 = xraw - g.xs;
+        g.Y0 = (int)fin->origin[1] - 2;
+        g.Z0 = (int)fin->origin[2];
+        cuuint64_t gdim[3] = {(cuuint64_t)(fin->shape[0] + shift), (cuuint64_t)fin->shape[1], (cuuint64_t)fin->shape[2]};
+        cuuint64_t gstride[2] = {(cuuint64_t)(fin->strides[1] * es), (cuuint64_t)(fin->strides[2] * es)};
+        cuuint32_t box[3] = {(cuuint32_t)HdiffTile<T, C::TI, C::TJ>::BX, (cuuint32_t)HdiffTile<T, C::TI, C::TJ>::BY, 1};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = encode_fn()(&map, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                 3, reinterpret_cast<void *>(abase), gdim, gstride, box, estr,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) tma = false;
+    }
+    if (!tma) g.xs = 0;
+    auto aligned = [&](const View<T> &v) {
+        return reinterpret_cast<uintptr_t>(v.p) % 16 == 0 && (v.sj * es) % 16 == 0 && (v.sk * es) % 16 == 0;
+    };
+    const bool vec = aligned(cf) && aligned(out);
+    if (tma)
+        return vec ? launch_hdiff_t<T, true, C::VEC>(map, in, cf, out, g, st)
+                   : launch_hdiff_t<T, true, 1>(map, in, cf, out, g, st);
+    return vec ? launch_hdiff_t<T, false, C::VEC>(map, in, cf, out, g, st)
+               : launch_hdiff_t<T, false, 1>(map, in, cf, out, g, st);
+}
+
+// ------------------------------------------------------------------ vadv
+constexpr int kVadvMaxK = 448;
+
+template <typename T, typename N, int BJ>
+static int launch_vadv_t(const gtb_field *const f[6], const VadvGeom &g, cudaStream_t st) {
+    auto kern = vadv_kernel<T, N, BJ>;
+    const int smem = (int)(vadv_smem_per_col_level<N>() * g.K * 32 * BJ);
+    if (prepare_kernel(kern, 227 * 1024) != cudaSuccess) return launch_status("vadv: shared-memory attribute");
+    dim3 block(32, BJ), grid((g.I + 31) / 32, (g.J + BJ - 1) / BJ);
+    kern<<<grid, block, smem, st>>>(view_of<const T>(f[0]), view_of<const T>(f[1]), view_of<const T>(f[2]),
+                                    view_of<const T>(f[3]), view_of<const T>(f[4]), view_of<T>(f[5]), g);
+    return launch_status("vadv launch");
+}
+
+template <typename T, typename N>
+static int run_vadv_n(const gtb_field *const f[6], const VadvGeom &g, cudaStream_t st) {
+    const size_t per_col = vadv_smem_per_col_level<N>() * (size_t)g.K;
+    if (per_col * 64 <= 112 * 1024) return launch_vadv_t<T, N, 2>(f, g, st);
+    return launch_vadv_t<T, N, 1>(f, g, st);
+}
+
+}  // namespace gtb
+
+// ====================================================================== C ABI
+using namespace gtb;
+
+extern "C" int gtb_hdiff(const gtb_field *in, const gtb_field *coeff, const gtb_field *out, const int64_t *domain,
+                         void *stream) {
+    if (!in || !coeff || !out) return fail(GTB_ERR_NULL, "gtb_hdiff: NULL field");
+    const int dt = in->dtype;
+    if (!dtype_size(dt)) return fail(GTB_ERR_DTYPE, "gtb_hdiff: unknown dtype %d", dt);
+    int rc;
+    if ((rc = check_field("in", in, dt)) || (rc = check_field("coeff", coeff, dt)) ||
+        (rc = check_field("out", out, dt)))
+        return rc;
+    const Reach r_in{{2, 2, 0}, {2, 2, 0}}, r0{{0, 0, 0}, {0, 0, 0}};
+    int64_t dom[3] = {INT64_MAX, INT64_MAX, INT64_MAX};
+    if (!domain) {
+        shrink_domain(in, r_in, dom);
+        shrink_domain(coeff, r0, dom);
+        shrink_domain(out, r0, dom);
+    }
+    if ((rc = resolve_domain(domain, dom))) return rc;
+    if ((rc = check_extent("in", in, r_in, dom)) || (rc = check_extent("coeff", coeff, r0, dom)) ||
+        (rc = check_extent("out", out, r0, dom)))
+        return rc;
+    if (overlaps(out, in)) return fail(GTB_ERR_ALIAS, "gtb_hdiff: out overlaps in");
+    if (overlaps(out, coeff)) return fail(GTB_ERR_ALIAS, "gtb_hdiff: out overlaps coeff");
+    if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return dt == GTB_F64 ? run_hdiff<double>(in, coeff, out, dom, st) : run_hdiff<float>(in, coeff, out, dom, st);
+}
+
+extern "C" int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u_pos,
+                        const gtb_field *utens, const gtb_field *utens_stage, const gtb_field *utens_stage_out,
+                        double dtr_stage, double beta_v, int prec, unsigned flags, const int64_t *domain,
+                        void *stream) {
+    const gtb_field *f[6] = {u_stage, wcon, u_pos, utens, utens_stage, utens_stage_out};
+    static const char *names[6] = {"u_stage", "wcon", "u_pos", "utens", "utens_stage", "utens_stage_out"};
+    for (int q = 0; q < 6; ++q)
+        if (!f[q]) return fail(GTB_ERR_NULL, "gtb_vadv: NULL field %s", names[q]);
+    const int dt = u_stage->dtype;
+    if (!dtype_size(dt)) return fail(GTB_ERR_DTYPE, "gtb_vadv: unknown dtype %d", dt);
+    int rc;
+    for (int q = 0; q < 6; ++q)
+        if ((rc = check_field(names[q], f[q], dt))) return rc;
+    if (flags & ~GTB_WCON_LITERAL) return fail(GTB_ERR_ARG, "gtb_vadv: unknown flags 0x%x", flags);
+    if (prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return fail(GTB_ERR_ARG, "gtb_vadv: unknown prec %d", prec);
+    if (dt == GTB_F64 && prec != GTB_PREC_NATIVE)
+        return fail(GTB_ERR_ARG, "gtb_vadv: FP64 storage computes in binary64 (prec must be GTB_PREC_NATIVE)");
+    if (!(dtr_stage == dtr_stage) || !(beta_v == beta_v)) return fail(GTB_ERR_ARG, "gtb_vadv: NaN scalar");
+    const bool literal = flags & GTB_WCON_LITERAL;
+    const Reach r0{{0, 0, 0}, {0, 0, 0}}, rw{{0, 0, 0}, {literal ? 0 : 1, 0, 0}};
+    int64_t dom[3] = {INT64_MAX, INT64_MAX, INT64_MAX};
+    if (!domain)
+        for (int q = 0; q < 6; ++q) shrink_domain(f[q], q == 1 ? rw : r0, dom);
+    if ((rc = resolve_domain(domain, dom))) return rc;
+    for (int q = 0; q < 6; ++q)
+        if ((rc = check_extent(names[q], f[q], q == 1 ? rw : r0, dom))) return rc;
+    for (int q = 0; q < 5; ++q) {
+        if (q == 4 && same_view(utens_stage_out, utens_stage)) continue;  // in place
+        if (overlaps(utens_stage_out, f[q]))
+            return fail(GTB_ERR_ALIAS, "gtb_vadv: utens_stage_out overlaps %s", names[q]);
+    }
+    if (dom[2] > kVadvMaxK)
+        return fail(GTB_ERR_UNSUPPORTED, "gtb_vadv: K = %lld exceeds the limit %d", (long long)dom[2], kVadvMaxK);
+    if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
+
+    VadvGeom g{};
+    g.I = (int)dom[0], g.J = (int)dom[1], g.K = (int)dom[2];
+    g.literal = literal ? 1 : 0;
+    const double bp = 0.5 * (1.0 + beta_v), bm = 0.5 * (1.0 - beta_v);
+    g.sym = (bp == bm) ? 1 : 0;
+    g.dtr = dtr_stage;
+    // a_k = bp * (-w_k/2): with w_k = s_k/2 (average) that is (-bp/4) s_k, else (-bp/2) s_k
+    g.ka = (literal ? -0.5 : -0.25) * bp;
+    g.kas = (literal ? -0.5 : -0.25) * bm;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (dt == GTB_F64) return run_vadv_n<double, double>(f, g, st);
+    if (prec == GTB_PREC_F64) return run_vadv_n<float, double>(f, g, st);
+    if (prec == GTB_PREC_DF) return run_vadv_n<float, df>(f, g, st);
+    return run_vadv_n<float, float>(f, g, st);
+}
+
+extern "C" int gtb_device_status(void *stream) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(GTB_ERR_LAUNCH, "gtb_device_status: %s", cudaGetErrorString(e));
+    int flag = 0;
+    e = cudaMemcpyFromSymbol(&flag, g_device_error, sizeof(int));
+    if (e != cudaSuccess) return fail(GTB_ERR_LAUNCH, "gtb_device_status: %s", cudaGetErrorString(e));
+    if (flag) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
+        return fail(GTB_ERR_DEVICE, "a kernel's bounded wait expired");
+    }
+    return ok();
+}
+
+extern "C" const char *gtb_last_error(void) { return t_err; }
+
+extern "C" const char *gtb_version(void) { return "gtb 0.1 sm_103a"; }

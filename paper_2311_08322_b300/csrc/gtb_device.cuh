@@ -1,0 +1,181 @@
+// gtb_device.cuh -- device utilities shared by the gtb kernels (sm_103a).
+//
+//  * the device error word and bounded waits (no kernel ever spins forever or traps)
+//  * mbarrier + TMA (cp.async.bulk.tensor) wrappers in inline PTX
+//  * a binary64 reciprocal refined from the hardware approximation
+//  * double-float ("df") arithmetic: an unevaluated sum hi + lo of two binary32
+//    values carrying ~48 significant bits, on the FP32 pipe
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gtb {
+
+// Set (never cleared by a kernel) when a bounded wait expires; read and
+// cleared by gtb_device_status().
+__device__ int g_device_error;
+
+// Longest a thread waits on an mbarrier before giving up: 2 s of %globaltimer.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// One try_wait on the phase with the given parity; true once it completed.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false (and the device error
+// word set) when kWaitLimitNs elapsed first.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            atomicExch(&g_device_error, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+// 3-D tiled TMA load of one box into shared memory, completing on `bar`.
+// x (innermost) must be a multiple of 16 bytes / element size.
+__device__ __forceinline__ void tma_load_3d(void *smem_dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---------------------------------------------------------------- reciprocal
+// 1/p in binary64: hardware seed (rcp.approx.ftz.f64) refined by one cubic
+// Newton-Raphson step y <- y (1 + e + e^2), e = 1 - p y (the residual computed
+// with one FMA, as in Markstein's division algorithms).  A seed accurate to
+// 2^-k gives ~2^-3k before rounding, i.e. a result within ~1 ulp.
+__device__ __forceinline__ double recip(double p) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(p));
+    const double e = fma(-p, y, 1.0);
+    return fma(y, fma(e, e, e), y);
+}
+
+__device__ __forceinline__ float recip(float p) { return __frcp_rn(p); }
+
+// ---------------------------------------------------------------- double-float
+// Error-free transformations (Knuth, TAOCP vol. 2, 4.2.2: TwoSum; Dekker 1971:
+// FastTwoSum; TwoProd via FMA) and the double-word algorithms of Joldes,
+// Muller & Popescu, "Tight and rigorous error bounds for basic building blocks
+// of double-word arithmetic", ACM TOMS 44(2), 2017.  All operations are
+// written with explicit __f*_rn intrinsics so the compiler cannot contract or
+// reassociate them.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_from(float x) { return {x, 0.0f}; }
+
+__device__ __forceinline__ float df_to_float(df a) { return __fadd_rn(a.hi, a.lo); }
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// Accurate double-word addition (JMP17 Alg. 6): relative error <= 3u^2 + 13u^3.
+__device__ __forceinline__ df operator+(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    const df t = two_sum(x.lo, y.lo);
+    float c = __fadd_rn(s.lo, t.hi);
+    df v = fast_two_sum(s.hi, c);
+    const float w = __fadd_rn(t.lo, v.lo);
+    return fast_two_sum(v.hi, w);
+}
+
+__device__ __forceinline__ df operator-(df x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
+
+// double-word + word (JMP17 Alg. 4): relative error <= 2u^2.
+__device__ __forceinline__ df operator+(df x, float y) {
+    const df s = two_sum(x.hi, y);
+    const float v = __fadd_rn(x.lo, s.lo);
+    return fast_two_sum(s.hi, v);
+}
+__device__ __forceinline__ df operator-(df x, float y) { return x + (-y); }
+
+// double-word x word (JMP17 Alg. 9): relative error <= 2u^2.
+__device__ __forceinline__ df operator*(df x, float y) {
+    const df c = two_prod(x.hi, y);
+    const float cl3 = __fmaf_rn(x.lo, y, c.lo);
+    return fast_two_sum(c.hi, cl3);
+}
+
+// double-word x double-word (JMP17 Alg. 12): relative error <= 5u^2.
+__device__ __forceinline__ df operator*(df x, df y) {
+    const df c = two_prod(x.hi, y.hi);
+    float tl = __fmul_rn(x.hi, y.lo);
+    tl = __fmaf_rn(x.lo, y.hi, tl);
+    const float cl3 = __fadd_rn(c.lo, tl);
+    return fast_two_sum(c.hi, cl3);
+}
+
+// Reciprocal of a double-word: a binary32 reciprocal th of y.hi refined by one
+// double-word Newton step, q = th + th (1 - y th); relative error ~2^-46.
+__device__ __forceinline__ df recip(df y) {
+    const float th = __frcp_rn(y.hi);
+    const df yt = y * th;
+    const df r = df{1.0f, 0.0f} - yt;
+    return df_from(th) + r * th;
+}
+
+}  // namespace gtb

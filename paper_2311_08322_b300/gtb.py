@@ -1,0 +1,196 @@
+"""Thin ctypes binding of libgtb (include/gtb.h) plus the storage allocator.
+
+Argument marshalling only: every step of hdiff / vadv runs in the CUDA
+kernels of ``libgtb.so``.  PyTorch provides device memory and streams.  There
+is no fallback: if the library is missing or a call fails, this module raises.
+
+Storages (the GT4Py paper's ``storage``, Sec. 2.2/2.3) are torch tensors shaped
+``(nk, nj, ni)`` (i contiguous) whose rows are padded so every interior row
+starts on a 128-byte boundary and every pitch is a multiple of 128 bytes (the
+TMA and vector-access layout); ``origin`` is the storage index ``(i, j, k)``
+of the compute domain's first point.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgtb.so")
+
+GTB_F32, GTB_F64 = 1, 2
+PREC = {"native": 0, "f64": 1, "df": 2}
+GTB_WCON_LITERAL = 1
+STATUS = {0: "GTB_OK", -1: "GTB_ERR_NULL", -2: "GTB_ERR_DTYPE", -3: "GTB_ERR_EXTENT", -4: "GTB_ERR_LAYOUT",
+          -5: "GTB_ERR_ALIAS", -6: "GTB_ERR_LAUNCH", -7: "GTB_ERR_DEVICE", -8: "GTB_ERR_UNSUPPORTED",
+          -9: "GTB_ERR_ARG"}
+
+
+class GtbField(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("shape", ctypes.c_int64 * 3), ("strides", ctypes.c_int64 * 3), ("origin", ctypes.c_int64 * 3)]
+
+
+class GtbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_device_status", "gtb_last_error", "gtb_version")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgtb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2311_08322_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER(GtbField)
+        i64p, vp = ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p
+        L.gtb_hdiff.argtypes = [P, P, P, i64p, vp]
+        L.gtb_vadv.argtypes = [P, P, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint,
+                               i64p, vp]
+        L.gtb_device_status.argtypes = [vp]
+        L.gtb_last_error.restype = ctypes.c_char_p
+        L.gtb_version.restype = ctypes.c_char_p
+        for n in ("gtb_hdiff", "gtb_vadv", "gtb_device_status"):
+            getattr(L, n).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise GtbError(rc, lib().gtb_last_error().decode())
+
+
+def version() -> str:
+    return lib().gtb_version().decode()
+
+
+# ----------------------------------------------------------------- storages
+@dataclass
+class Storage:
+    """A field storage: ``data`` (torch, shaped (nk, nj, ni)) and its ``origin``."""
+    data: torch.Tensor
+    origin: tuple
+
+    @property
+    def shape(self):
+        return tuple(self.data.shape)
+
+    def numpy(self) -> np.ndarray:
+        return self.data.detach().cpu().numpy().copy()
+
+    def interior(self, domain) -> torch.Tensor:
+        (oi, oj, ok), (I, J, K) = self.origin, domain
+        return self.data[ok:ok + K, oj:oj + J, oi:oi + I]
+
+
+def empty_storage(ni: int, nj: int, nk: int, *, dtype=torch.float64, device="cuda", halo_i: int = 0,
+                  align_bytes: int = 128) -> torch.Tensor:
+    """Padded (nk, nj, ni) tensor: storage column ``halo_i`` of every row is
+    ``align_bytes``-aligned and the row pitch is a multiple of ``align_bytes``."""
+    es = torch.empty((), dtype=dtype).element_size()
+    a = align_bytes // es
+    lead = (-halo_i) % a
+    sj = -(-(lead + ni) // a) * a
+    sk = sj * nj
+    n = max(1, nk * sk)
+    buf = torch.empty(n + 2 * a, dtype=dtype, device=device)
+    # the caching allocator returns 512-byte-aligned blocks; keep `lead` from there
+    off = ((-buf.data_ptr() // es) % a) + lead
+    return buf.as_strided((nk, nj, ni), (sk, sj, 1), storage_offset=off)
+
+
+def storage_from(arr: np.ndarray, origin, *, device="cuda", dtype=None) -> Storage:
+    """Copy a host (nk, nj, ni) array into a padded device storage."""
+    dt = dtype or (torch.float32 if arr.dtype == np.float32 else torch.float64)
+    nk, nj, ni = arr.shape
+    t = empty_storage(ni, nj, nk, dtype=dt, device=device, halo_i=origin[0])
+    t.copy_(torch.from_numpy(np.ascontiguousarray(arr)).to(dt))
+    return Storage(t, tuple(origin))
+
+
+def field(t, origin=None) -> GtbField:
+    """gtb_field describing a CUDA tensor (or Storage) shaped (nk, nj, ni)."""
+    if isinstance(t, Storage):
+        origin = t.origin if origin is None else origin
+        t = t.data
+    if origin is None:
+        origin = (0, 0, 0)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("gtb fields must be CUDA tensors")
+    if t.dim() != 3:
+        raise ValueError("gtb fields are 3-D tensors shaped (nk, nj, ni)")
+    if t.dtype == torch.float64:
+        dt = GTB_F64
+    elif t.dtype == torch.float32:
+        dt = GTB_F32
+    else:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    nk, nj, ni = t.shape
+    sk, sj, si = t.stride()
+    f = GtbField()
+    f.ptr = t.data_ptr()
+    f.dtype = dt
+    f.reserved = 0
+    f.shape[:] = [ni, nj, nk]
+    f.strides[:] = [si, sj, sk]
+    f.origin[:] = list(origin)
+    return f
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dom(domain):
+    if domain is None:
+        return None
+    return (ctypes.c_int64 * 3)(*[int(x) for x in domain])
+
+
+# ----------------------------------------------------------------- stencils
+def hdiff(in_, coeff, out, *, domain=None, stream=None):
+    """out = hdiff(in_, coeff) on the domain (gtb_hdiff).  Fields: Storage or
+    (tensor, origin) pairs.  Asynchronous on ``stream`` (default: torch's current)."""
+    fi, fc, fo = (_as_field(x) for x in (in_, coeff, out))
+    _check(lib().gtb_hdiff(ctypes.byref(fi), ctypes.byref(fc), ctypes.byref(fo), _dom(domain), _stream(stream)))
+    return out
+
+
+def vadv(u_stage, wcon, u_pos, utens, utens_stage, out=None, *, dtr_stage=3.0 / 20.0, beta_v=0.0,
+         prec="native", literal=False, domain=None, stream=None):
+    """utens_stage_out = vadv(...) (gtb_vadv); ``out=None`` updates utens_stage in place."""
+    out = utens_stage if out is None else out
+    fs = [_as_field(x) for x in (u_stage, wcon, u_pos, utens, utens_stage, out)]
+    _check(lib().gtb_vadv(*[ctypes.byref(f) for f in fs], float(dtr_stage), float(beta_v), PREC[prec],
+                          GTB_WCON_LITERAL if literal else 0, _dom(domain), _stream(stream)))
+    return out
+
+
+def device_status(stream=None):
+    """Synchronise the stream and raise if a kernel's bounded wait expired."""
+    _check(lib().gtb_device_status(_stream(stream)))
+
+
+def _as_field(x) -> GtbField:
+    if isinstance(x, GtbField):
+        return x
+    if isinstance(x, Storage):
+        return field(x)
+    if isinstance(x, tuple) and len(x) == 2:
+        return field(x[0], x[1])
+    raise TypeError("expected a Storage, a (tensor, origin) pair or a GtbField")

@@ -1,0 +1,108 @@
+"""The C ABI (include/gtb.h): the library builds, loads and exports every
+declared entry point, and the host-side argument checks (the paper's run-time
+storage checks, Sec. 3.1) return their documented codes before any CUDA call.
+No GPU is needed: every call here fails validation or has an empty domain."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2311_08322_b300 import build, gtb
+    build.build()
+    return gtb
+
+
+def declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "gtb.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(gtb_\w+)\s*\(", hdr)))
+
+
+def test_exports_every_declared_symbol(L):
+    syms = declared_symbols()
+    assert {"gtb_hdiff", "gtb_vadv", "gtb_device_status", "gtb_last_error", "gtb_version"} <= set(syms)
+    lib = ctypes.CDLL(L.LIB_PATH)
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_version(L):
+    assert L.version().startswith("gtb ")
+
+
+def fake(L, ni, nj, nk, origin=(2, 2, 0), dtype=2, ptr=0x10000000, sj=None, sk=None):
+    f = L.GtbField()
+    f.ptr = ptr
+    f.dtype = dtype
+    f.shape[:] = [ni, nj, nk]
+    sj = ni if sj is None else sj
+    sk = sj * nj if sk is None else sk
+    f.strides[:] = [1, sj, sk]
+    f.origin[:] = list(origin)
+    return f
+
+
+def call_hdiff(L, fi, fc, fo, domain=None):
+    d = None if domain is None else (ctypes.c_int64 * 3)(*domain)
+    return L.lib().gtb_hdiff(ctypes.byref(fi), ctypes.byref(fc), ctypes.byref(fo), d, None)
+
+
+def test_hdiff_validation(L):
+    G = 1 << 24  # separate fake address ranges
+    ok = lambda: (fake(L, 12, 12, 3, ptr=G), fake(L, 12, 12, 3, ptr=2 * G), fake(L, 12, 12, 3, ptr=3 * G))
+    fi, fc, fo = ok()
+    # empty domain: validated, nothing launched
+    assert call_hdiff(L, fi, fc, fo, (0, 8, 3)) == 0
+    assert L.lib().gtb_hdiff(None, ctypes.byref(fc), ctypes.byref(fo), None, None) == -1
+    fi.ptr = 0
+    assert call_hdiff(L, fi, fc, fo, (0, 8, 3)) == -1
+    fi, fc, fo = ok()
+    fc.dtype = 1
+    assert call_hdiff(L, fi, fc, fo, (0, 8, 3)) == -2
+    fi, fc, fo = ok()
+    fi.strides[0] = 2
+    assert call_hdiff(L, fi, fc, fo, (0, 8, 3)) == -4
+    fi, fc, fo = ok()
+    fi.origin[0] = 1          # halo of 1 < the 2-point reach of hdiff
+    assert call_hdiff(L, fi, fc, fo, (0, 8, 3)) == -3
+    fi, fc, fo = ok()
+    assert call_hdiff(L, fi, fc, fo, (9, 8, 3)) == -3   # 2 + 9 + 2 > 12
+    fi, fc, fo = ok()
+    fo.ptr = fi.ptr + 8 * 100  # out inside in's storage
+    assert call_hdiff(L, fi, fc, fo, (0, 8, 3)) == -5
+    assert "overlaps" in L.lib().gtb_last_error().decode()
+
+
+def test_hdiff_domain_deduction(L):
+    """Domain deduced from the field sizes and the stencil's reach (paper Sec. 2.2):
+    an in storage of 12 with origin 2 leaves room for 8 points."""
+    G = 1 << 24
+    fi, fc, fo = fake(L, 12, 12, 3, ptr=G), fake(L, 12, 12, 0, ptr=2 * G), fake(L, 12, 12, 3, ptr=3 * G)
+    # coeff has nk = 0, so the deduced domain is empty and nothing is launched
+    assert call_hdiff(L, fi, fc, fo) == 0
+
+
+def test_vadv_validation(L):
+    G = 1 << 24
+    mk = lambda n, o=(1, 1, 0): fake(L, 10, 10, 6, origin=o, ptr=n * G)
+    fs = [mk(n) for n in range(1, 7)]
+    args = lambda fs, prec=0, flags=0, dom=(0, 8, 6): [*[ctypes.byref(f) for f in fs], 0.15, 0.0, prec, flags,
+                                                       (ctypes.c_int64 * 3)(*dom), None]
+    assert L.lib().gtb_vadv(*args(fs)) == 0
+    assert L.lib().gtb_vadv(*args(fs, prec=1)) == -9       # FP64 storage: binary64 only
+    assert L.lib().gtb_vadv(*args(fs, flags=4)) == -9
+    assert L.lib().gtb_vadv(*args(fs, dom=(9, 8, 6))) == -3  # wcon needs i+1 <= 9
+    assert L.lib().gtb_vadv(*args(fs, flags=1, dom=(0, 8, 6))) == 0
+    big = [fake(L, 10, 10, 500, origin=(1, 1, 0), ptr=n * (1 << 28)) for n in range(1, 7)]
+    assert L.lib().gtb_vadv(*args(big, dom=(8, 8, 449))) == -8
+    # in place: the very same view is allowed, a shifted one is not
+    fs2 = [mk(n) for n in range(1, 6)] + [mk(5)]
+    assert L.lib().gtb_vadv(*args(fs2)) == 0
+    fs3 = [mk(n) for n in range(1, 6)] + [mk(5, o=(1, 2, 0))]
+    assert L.lib().gtb_vadv(*args(fs3)) == -5

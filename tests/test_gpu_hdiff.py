@@ -1,0 +1,124 @@
+"""GPU parity of gtb_hdiff against the FP64 oracle (GT4Py paper Sec. 3.1,
+horizontal diffusion).  FP64 bound: 1e-12 max-norm relative; FP32 bound: 1e-5
+against the oracle run in FP64 on the FP32-rounded inputs."""
+import numpy as np
+import pytest
+
+from helpers import region, rel_err
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+F32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    from paper_2311_08322_b300 import build, gtb
+    assert torch.cuda.is_available()
+    build.build()
+    return gtb
+
+
+def draw(I, J, K, seed, pad=(0, 0, 0)):
+    """in and coeff over an (I+4+2*pad_i) x (J+4+2*pad_j) x (K+2*pad_k) storage."""
+    rng = np.random.default_rng(seed)
+    shp = (K + 2 * pad[2], J + 4 + 2 * pad[1], I + 4 + 2 * pad[0])
+    return rng.uniform(-1, 1, shp), rng.uniform(0, 0.025, shp)
+
+
+def run_case(G, orc, I, J, K, seed=0, dtype=np.float64, pad=(0, 0, 0), contiguous=False):
+    import torch
+    inp, coeff = draw(I, J, K, seed, pad)
+    if dtype == np.float32:
+        inp, coeff = inp.astype(np.float32), coeff.astype(np.float32)
+    o = (2 + pad[0], 2 + pad[1], pad[2])
+    dom = (I, J, K)
+    if contiguous:   # plain torch tensors: unpadded rows, odd pitches
+        tin = torch.from_numpy(inp).cuda()
+        tcf = torch.from_numpy(coeff).cuda()
+        tout = torch.zeros_like(tcf)
+        sin, scf, sout = G.Storage(tin, o), G.Storage(tcf, o), G.Storage(tout, o)
+    else:
+        sin, scf = G.storage_from(inp, o), G.storage_from(coeff, o)
+        sout = G.storage_from(np.zeros_like(coeff), o)
+    G.hdiff(sin, scf, sout, domain=dom)
+    G.device_status()
+    got = region(sout.numpy(), o, dom)
+    ref = region(orc.hdiff(inp.astype(np.float64), coeff.astype(np.float64), origin_in=o, domain=dom), o, dom)
+    return got, ref
+
+
+def test_small_fp64(G, orc):
+    """64x64x40, halo 2 (storage 68x68x40), in ~ U(-1,1), coeff ~ U(0,0.025), seed 0."""
+    got, ref = run_case(G, orc, 64, 64, 40)
+    assert rel_err(got, ref) <= F64_TOL
+
+
+def test_256_fp64_full_field(G, orc):
+    """256x256x80 FP64, the launch configuration the benchmark times; whole field."""
+    got, ref = run_case(G, orc, 256, 256, 80, seed=1)
+    assert rel_err(got, ref) <= F64_TOL
+
+
+@pytest.mark.parametrize("I,J,K", [(67, 19, 5), (1, 1, 1), (130, 3, 2), (65, 17, 1), (200, 33, 7), (63, 15, 3)])
+def test_ragged_fp64(G, orc, I, J, K):
+    """Domains that leave ragged tiles in I and J, one-point and one-level domains."""
+    got, ref = run_case(G, orc, I, J, K, seed=I + J + K)
+    assert rel_err(got, ref) <= F64_TOL
+
+
+@pytest.mark.parametrize("pad", [(1, 0, 0), (3, 2, 1), (5, 1, 2)])
+def test_origin_offsets_fp64(G, orc, pad):
+    """Non-zero origins beyond the halo, including odd i origins (TMA box shifted
+    to the 16-byte boundary)."""
+    got, ref = run_case(G, orc, 70, 21, 6, seed=3, pad=pad)
+    assert rel_err(got, ref) <= F64_TOL
+
+
+@pytest.mark.parametrize("I,J", [(71, 9), (64, 16)])
+def test_unpadded_layouts(G, orc, I, J):
+    """Plain contiguous tensors: pitches that are not 16-byte multiples take the
+    cooperative-load path and scalar stores."""
+    for dt in (np.float64, np.float32):
+        got, ref = run_case(G, orc, I, J, 4, seed=7, dtype=dt, contiguous=True)
+        assert rel_err(got, ref) <= (F64_TOL if dt == np.float64 else F32_TOL)
+
+
+def test_fp32_512(G, orc):
+    """512x512x80 with FP32 storage and arithmetic (the precision form)."""
+    got, ref = run_case(G, orc, 512, 512, 80, seed=0, dtype=np.float32)
+    assert rel_err(got, ref) <= F32_TOL
+
+
+@pytest.mark.parametrize("I,J,K", [(129, 17, 3), (5, 300, 2)])
+def test_ragged_fp32(G, orc, I, J, K):
+    got, ref = run_case(G, orc, I, J, K, seed=11, dtype=np.float32)
+    assert rel_err(got, ref) <= F32_TOL
+
+
+def test_closed_forms_on_gpu(G, orc):
+    """The oracle's closed forms hold on the GPU too: constant and quartic fields."""
+    import torch
+    I, J, K = 40, 24, 3
+    k, y, x = np.meshgrid(np.arange(K), np.arange(J + 4), np.arange(I + 4), indexing="ij")
+    coeff = np.random.default_rng(5).integers(0, 26, x.shape) / 1024.0
+    for inp, expect in ((np.full(x.shape, 0.375), lambda a: a), (((x - 20.0) ** 4), lambda a: a + 24.0 * coeff)):
+        sin, scf = G.storage_from(inp, (2, 2, 0)), G.storage_from(coeff, (2, 2, 0))
+        sout = G.storage_from(np.zeros_like(coeff), (2, 2, 0))
+        G.hdiff(sin, scf, sout)
+        got = region(sout.numpy(), (2, 2, 0), (I, J, K))
+        assert np.array_equal(got, region(expect(inp), (2, 2, 0), (I, J, K)))
+
+
+def test_out_of_range_errors_on_gpu(G):
+    import torch
+    a = G.storage_from(np.zeros((2, 8, 8)), (2, 2, 0))
+    b = G.storage_from(np.zeros((2, 8, 8)), (2, 2, 0))
+    with pytest.raises(G.GtbError) as e:
+        G.hdiff(a, b, a)
+    assert e.value.code == -5
+    with pytest.raises(G.GtbError) as e:
+        G.hdiff(a, b, G.storage_from(np.zeros((2, 8, 8)), (2, 2, 0)), domain=(5, 4, 2))
+    assert e.value.code == -3
