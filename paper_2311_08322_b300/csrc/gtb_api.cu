@@ -190,8 +190,13 @@ static int launch_hdiff_t(const CUtensorMap &map, const View<T> &in, const View<
                           HdiffGeom g, cudaStream_t st) {
     using C = HdiffCfg<T>;
     constexpr int STG = TMA ? C::STAGES : 1;
-    auto kern = hdiff_kernel<T, C::TI, C::TJ, C::NT, STG, TMA, VEC>;
-    constexpr int smem = hdiff_smem_bytes<T, C::TI, C::TJ, STG>();
+    // binary64: the exact fixed-point form (integer pipe); binary32: the definition in binary32
+    constexpr bool FX = sizeof(T) == 8;
+    constexpr int smem = hdiff_smem_bytes<T, C::TI, C::TJ, STG, FX>();
+    auto kern = [] {
+        if constexpr (FX) return hdiff_fx_kernel<C::TI, C::TJ, C::NT, STG, TMA, VEC>;
+        else return hdiff_kernel<T, C::TI, C::TJ, C::NT, STG, TMA, VEC>;
+    }();
     if (prepare_kernel(kern, smem) != cudaSuccess) return launch_status("hdiff: shared-memory attribute");
     static int slots_cache[64] = {0};
     const int dev = current_device();
@@ -262,8 +267,9 @@ constexpr int kVadvMaxK = 448;
 
 template <typename T, typename N, int BJ>
 static int launch_vadv_t(const gtb_field *const f[6], const VadvGeom &g, cudaStream_t st) {
-    auto kern = vadv_kernel<T, N, BJ>;
-    const int smem = (int)(vadv_smem_per_col_level<N>() * g.K * 32 * BJ);
+    constexpr bool DPG = vadv_dp_global<T, N>();
+    auto kern = vadv_kernel<T, N, BJ, DPG>;
+    const int smem = (int)(vadv_smem_per_col_level<T, N>() * g.K * 32 * BJ);
     if (prepare_kernel(kern, 227 * 1024) != cudaSuccess) return launch_status("vadv: shared-memory attribute");
     dim3 block(32, BJ), grid((g.I + 31) / 32, (g.J + BJ - 1) / BJ);
     kern<<<grid, block, smem, st>>>(view_of<const T>(f[0]), view_of<const T>(f[1]), view_of<const T>(f[2]),
@@ -271,10 +277,12 @@ static int launch_vadv_t(const gtb_field *const f[6], const VadvGeom &g, cudaStr
     return launch_status("vadv launch");
 }
 
+// Columns per block: two warps while a block's column state stays within
+// 48 KB (several blocks per SM), else one warp (K up to the 448 limit).
 template <typename T, typename N>
 static int run_vadv_n(const gtb_field *const f[6], const VadvGeom &g, cudaStream_t st) {
-    const size_t per_col = vadv_smem_per_col_level<N>() * (size_t)g.K;
-    if (per_col * 64 <= 112 * 1024) return launch_vadv_t<T, N, 2>(f, g, st);
+    const size_t per_col = vadv_smem_per_col_level<T, N>() * (size_t)g.K;
+    if (per_col * 64 <= 48 * 1024) return launch_vadv_t<T, N, 2>(f, g, st);
     return launch_vadv_t<T, N, 1>(f, g, st);
 }
 

@@ -60,14 +60,40 @@ __device__ __forceinline__ N face_sum(const T *__restrict__ wcol, const T *__res
     return to_num<N, T>(lo) + to_num<N, T>(hi);
 }
 
-template <typename T, typename N, int BJ>
+// Inputs of one level k for this lane's column, loaded PD levels ahead.
+template <typename T>
+struct Level {
+    T up, ut, uts, us1, w;  // u_pos_k, utens_k, utens_stage_k, u_stage_{k+1}, wcon_{k+1}(i)
+    T w1;                   // wcon_{k+1}(i+1) (last lane only; others take it by shuffle)
+};
+
+template <typename T>
+__device__ __forceinline__ void load_level(Level<T> &L, int k, int K, const T *pup, const T *put, const T *puts,
+                                           const T *pus, const T *pw, const T *pw1, int64_t sk_up, int64_t sk_ut,
+                                           int64_t sk_uts, int64_t sk_us, int64_t sk_w, bool last_lane) {
+    if (k < K) {
+        L.up = pup[(int64_t)k * sk_up];
+        L.ut = put[(int64_t)k * sk_ut];
+        L.uts = puts[(int64_t)k * sk_uts];
+    }
+    if (k + 1 < K) {
+        L.us1 = pus[(int64_t)(k + 1) * sk_us];
+        L.w = pw[(int64_t)(k + 1) * sk_w];
+        if (last_lane) L.w1 = pw1[(int64_t)(k + 1) * sk_w];
+    }
+}
+
+// DPG: d'_k is parked in the output array (same element size as N) and read
+// back by the backward sweep from L2; only c'_k stays in shared memory.
+// Otherwise both live in shared memory.
+template <typename T, typename N, int BJ, bool DPG>
 __global__ void __launch_bounds__(32 * BJ)
     vadv_kernel(const View<const T> us, const View<const T> wc, const View<const T> up, const View<const T> ut,
                 const View<const T> uts, const View<T> out, const VadvGeom g) {
     constexpr int NT = 32 * BJ;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     N *cpb = reinterpret_cast<N *>(smem_raw);  // [K][NT]
-    N *dpb = cpb + (size_t)g.K * NT;           // [K][NT]
+    N *dpb = cpb + (size_t)g.K * NT;           // [K][NT] (unused when DPG)
 
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
     const int i = blockIdx.x * 32 + tx, j = blockIdx.y * BJ + ty;
@@ -76,79 +102,99 @@ __global__ void __launch_bounds__(32 * BJ)
     const int iw = min(i, g.I);  // wcon is valid up to i = I (staggered)
     const int K = g.K;
 
-    const T *__restrict__ pus = us.p + ic + (int64_t)jc * us.sj;
-    const T *__restrict__ pup = up.p + ic + (int64_t)jc * up.sj;
-    const T *__restrict__ put = ut.p + ic + (int64_t)jc * ut.sj;
-    const T *puts = uts.p + ic + (int64_t)jc * uts.sj;  // may alias out (in place)
-    const T *__restrict__ pw = wc.p + iw + (int64_t)jc * wc.sj;
-    const T *__restrict__ pw1 = wc.p + min(i + 1, g.I) + (int64_t)jc * wc.sj;
+    const T *pus = us.p + ic + (int64_t)jc * us.sj;
+    const T *pup = up.p + ic + (int64_t)jc * up.sj;
+    const T *put = ut.p + ic + (int64_t)jc * ut.sj;
+    const T *puts = uts.p + ic + (int64_t)jc * uts.sj;  // may alias po (in place)
+    const T *pw = wc.p + iw + (int64_t)jc * wc.sj;
+    const T *pw1 = wc.p + min(i + 1, g.I) + (int64_t)jc * wc.sj;
+    T *po = out.p + ic + (int64_t)jc * out.sj;
     const bool last_lane = (tx == 31);
+    const bool lit = g.literal != 0;
 
     const N dtr = num_const<N>(g.dtr);
     const N ka = num_const<N>(g.ka);
     const N kas = num_const<N>(g.kas);
     const N zero = num_const<N>(0.0);
 
-    // level 0 state
-    N us_prev = zero;
+#define GTB_LOAD(L, k) load_level<T>(L, k, K, pup, put, puts, pus, pw, pw1, up.sk, ut.sk, uts.sk, us.sk, wc.sk, last_lane)
+    Level<T> L0, L1, L2;  // levels k, k+1, k+2
+    GTB_LOAD(L0, 0);
+    GTB_LOAD(L1, 1);
+    GTB_LOAD(L2, 2);
+
     N us_cur = to_num<N, T>(pus[0]);
+    N dm = zero;                    // u_stage_{k-1} - u_stage_k
     N a_cur = zero, as_cur = zero;  // a_0 = as_0 = 0
     N cp_prev = zero, dp_prev = zero;
 
-#pragma unroll 2
     for (int k = 0; k < K; ++k) {
-        const int64_t ok_us = (int64_t)k * us.sk;
-        N us_next = zero, a_next = zero, as_next = zero;
         const bool has_next = (k + 1 < K);
+        N a_next = zero, as_next = zero, dpl = zero;
         if (has_next) {
-            us_next = to_num<N, T>(pus[ok_us + us.sk]);
-            const N s = face_sum<T, N>(pw, pw1, (int64_t)(k + 1) * wc.sk, last_lane, g.literal);
+            N s;
+            if (lit) {
+                s = to_num<N, T>(L0.w);
+            } else {
+                T hi = __shfl_down_sync(0xffffffffu, L0.w, 1);
+                if (last_lane) hi = L0.w1;
+                s = to_num<N, T>(L0.w) + to_num<N, T>(hi);
+            }
             a_next = ka * s;
             as_next = g.sym ? a_next : kas * s;
+            const N us_next = to_num<N, T>(L0.us1);
+            dpl = us_next - us_cur;  // u_stage_{k+1} - u_stage_k
+            us_cur = us_next;
         }
-        const N c_cur = -a_next, cs_cur = -as_next;  // c_k = -a_{k+1}; zero at k = K-1
-        const N b = (dtr - a_cur) - c_cur;
-        N d = dtr * to_num<N, T>(pup[(int64_t)k * up.sk]) + to_num<N, T>(put[(int64_t)k * ut.sk]);
-        d = d + to_num<N, T>(puts[(int64_t)k * uts.sk]);
-        if (k > 0) d = d - as_cur * (us_prev - us_cur);
-        if (has_next) d = d - cs_cur * (us_next - us_cur);
-
-        N p, num;
-        if (k == 0) {
-            p = b;
-            num = d;
-        } else {
+        const N b = (dtr - a_cur) + a_next;  // dtr - a_k - c_k with c_k = -a_{k+1}
+        N d = dtr * to_num<N, T>(L0.up) + to_num<N, T>(L0.ut);
+        d = d + to_num<N, T>(L0.uts);
+        if (k > 0) d = d - as_cur * dm;
+        if (has_next) d = d + as_next * dpl;  // - cs_k (u_{k+1} - u_k), cs_k = -as_{k+1}
+        N p = b, num = d;
+        if (k > 0) {
             p = b - a_cur * cp_prev;
             num = d - a_cur * dp_prev;
         }
         const N r = recip(p);
-        const N cpk = c_cur * r, dpk = num * r;
+        const N cpk = (-a_next) * r, dpk = num * r;
         cpb[(size_t)k * NT + t] = cpk;
-        dpb[(size_t)k * NT + t] = dpk;
+        if (DPG) {
+            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(dpk);
+        } else {
+            dpb[(size_t)k * NT + t] = dpk;
+        }
         cp_prev = cpk, dp_prev = dpk;
-        us_prev = us_cur, us_cur = us_next;
+        dm = -dpl;
         a_cur = a_next, as_cur = as_next;
+        L0 = L1;
+        L1 = L2;
+        GTB_LOAD(L2, k + 3);
     }
+#undef GTB_LOAD
 
     // backward substitution and output, utens_stage_out = dtr (x - u_pos)
-    T *po = out.p + ic + (int64_t)jc * out.sj;
     N x = dp_prev;
-    {
-        const int k = K - 1;
-        const N o = dtr * (x - to_num<N, T>(pup[(int64_t)k * up.sk]));
-        if (active) po[(int64_t)k * out.sk] = to_store<T, N>(o);
-    }
+    if (active) po[(int64_t)(K - 1) * out.sk] = to_store<T, N>(dtr * (x - to_num<N, T>(pup[(int64_t)(K - 1) * up.sk])));
 #pragma unroll 4
     for (int k = K - 2; k >= 0; --k) {
-        x = dpb[(size_t)k * NT + t] - cpb[(size_t)k * NT + t] * x;
+        N dk;
+        if (DPG) dk = to_num<N, T>(po[(int64_t)k * out.sk]);
+        else dk = dpb[(size_t)k * NT + t];
+        x = dk - cpb[(size_t)k * NT + t] * x;
         const N o = dtr * (x - to_num<N, T>(pup[(int64_t)k * up.sk]));
         if (active) po[(int64_t)k * out.sk] = to_store<T, N>(o);
     }
 }
 
-template <typename N>
+template <typename T, typename N>
+constexpr bool vadv_dp_global() {
+    return sizeof(T) == sizeof(N);
+}
+
+template <typename T, typename N>
 constexpr size_t vadv_smem_per_col_level() {
-    return 2 * sizeof(N);
+    return (vadv_dp_global<T, N>() ? 1 : 2) * sizeof(N);
 }
 
 }  // namespace gtb

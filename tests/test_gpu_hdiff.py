@@ -122,3 +122,55 @@ def test_out_of_range_errors_on_gpu(G):
     with pytest.raises(G.GtbError) as e:
         G.hdiff(a, b, G.storage_from(np.zeros((2, 8, 8)), (2, 2, 0)), domain=(5, 4, 2))
     assert e.value.code == -3
+
+
+def run_fields(G, orc, inp, coeff, origin=(2, 2, 0)):
+    nk, nj, ni = inp.shape
+    dom = (ni - 4, nj - 4, nk)
+    sin, scf = G.storage_from(inp, origin), G.storage_from(coeff, origin)
+    sout = G.storage_from(np.zeros_like(coeff), origin)
+    G.hdiff(sin, scf, sout)
+    G.device_status()
+    return region(sout.numpy(), origin, dom), region(orc.hdiff(inp, coeff), origin, dom)
+
+
+def test_fp64_nonfinite_tile_takes_binary64_phases(G, orc):
+    """An inf in one tile: that tile level runs the binary64 phases, every other tile
+    the fixed-point form; non-finite outputs and finite values match the oracle."""
+    inp, coeff = draw(150, 40, 3, 21)
+    inp[1, 12, 30] = np.inf
+    inp[2, 30, 100] = np.nan
+    got, ref = run_fields(G, orc, inp, coeff)
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(got))
+    assert (~fin).sum() > 0
+    assert rel_err(got[fin], ref[fin]) <= F64_TOL
+
+
+def test_fp64_tiny_magnitudes(G, orc):
+    """A field of magnitude 2^-1000 (exponents outside the fixed-point window)."""
+    inp, coeff = draw(70, 20, 2, 22)
+    got, ref = run_fields(G, orc, inp * 2.0 ** -1000, coeff)
+    assert rel_err(got, ref) <= F64_TOL
+
+
+def test_fp64_wide_dynamic_range(G, orc):
+    """Inputs spanning 60 binades in every tile: small values are truncated in the
+    fixed-point form, far below the bound relative to the field maximum."""
+    inp, coeff = draw(130, 33, 4, 23)
+    scale = 2.0 ** np.random.default_rng(24).integers(-60, 1, inp.shape)
+    got, ref = run_fields(G, orc, inp * scale, coeff)
+    assert rel_err(got, ref) <= F64_TOL
+
+
+def test_fp64_limiter_sign_of_tiny_differences(G, orc):
+    """Neighbours that differ only in their last bit, far below the fixed-point
+    resolution of their tile: the limiter still sees the exact sign of in[i+1]-in[i]."""
+    inp, coeff = draw(64, 16, 2, 25)
+    x0 = 1e-200
+    x1 = np.nextafter(x0, 1.0)
+    inp[:, 8:12, 20] = x0
+    inp[:, 8:12, 21] = x1
+    inp[:, 8:12, 22] = x0
+    got, ref = run_fields(G, orc, inp, coeff)
+    assert rel_err(got, ref) <= F64_TOL
