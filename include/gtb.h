@@ -35,6 +35,7 @@
 #ifndef GTB_H
 #define GTB_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -114,13 +115,27 @@ int gtb_hdiff(const gtb_field *in, const gtb_field *coeff, const gtb_field *out,
  * (binary64); for GTB_F32 storage NATIVE is all-binary32, F64 and DF keep the
  * whole column computation in binary64 / double-float.
  * A zero pivot (singular leading minor) yields non-finite values in that column,
- * as the unpivoted method does.  Limit: K <= 448 (the forward-sweep state of
- * a block of columns stays in shared memory); larger K is GTB_ERR_UNSUPPORTED.
+ * as the unpivoted method does.  Limit: K <= 448; larger K is GTB_ERR_UNSUPPORTED.
+ *
+ * workspace: optional caller-owned device scratch for the forward sweep's
+ * eliminated coefficients (c', and d' when it cannot be parked in the output),
+ * at least gtb_vadv_workspace_bytes() bytes, 16-byte aligned, overlapping no
+ * field; its contents on entry are ignored and on exit unspecified, and two
+ * calls that may run concurrently need distinct workspaces.  With it the
+ * kernel keeps no per-column state in shared memory and runs at full
+ * occupancy (the fast form on B300, whose FP64 pipe needs many resident warps);
+ * with NULL (or too small) the state stays in shared memory.
  */
 int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u_pos,
              const gtb_field *utens, const gtb_field *utens_stage,
              const gtb_field *utens_stage_out, double dtr_stage, double beta_v,
-             int prec, unsigned flags, const int64_t *domain, void *stream);
+             int prec, unsigned flags, const int64_t *domain,
+             void *workspace, size_t workspace_bytes, void *stream);
+
+/* Bytes of workspace gtb_vadv uses for this dtype, prec and domain (I,J,K):
+ * K*I*J*8 for GTB_F64 storage, K*I*J*4 for GTB_F32 with GTB_PREC_NATIVE,
+ * K*I*J*16 for GTB_F32 with GTB_PREC_F64 or GTB_PREC_DF; 0 for bad arguments. */
+size_t gtb_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain);
 
 /*
  * gtb_device_status -- synchronises `stream`, then returns and clears the

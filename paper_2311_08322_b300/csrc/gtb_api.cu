@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,7 @@
 #include "gtb.h"
 #include "gtb_device.cuh"
 #include "hdiff_kernels.cuh"
+#include "hdiff_rs.cuh"
 #include "vadv_kernels.cuh"
 
 namespace gtb {
@@ -178,38 +180,36 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // ------------------------------------------------------------------ hdiff
 template <typename T>
 struct HdiffCfg;
-template <> struct HdiffCfg<double> {
-    static constexpr int TI = 64, TJ = 16, NT = 256, STAGES = 3, VEC = 2;
+template <> struct HdiffCfg<double> {  // 64 x 64 tile, 4 warps of 16 rows, 2 columns per lane
+    static constexpr int CPL = 2, W = 4, R = 16, STAGES = 2;
 };
-template <> struct HdiffCfg<float> {
-    static constexpr int TI = 128, TJ = 16, NT = 256, STAGES = 4, VEC = 4;
+template <> struct HdiffCfg<float> {   // 128 x 64 tile, 4 warps of 16 rows, 4 columns per lane
+    static constexpr int CPL = 4, W = 4, R = 16, STAGES = 2;
 };
 
-template <typename T, bool TMA, int VEC>
+template <typename T, bool TMA>
 static int launch_hdiff_t(const CUtensorMap &map, const View<T> &in, const View<T> &cf, const View<T> &out,
-                          HdiffGeom g, cudaStream_t st) {
+                          HdiffGeom g, int vec_ok, cudaStream_t st) {
     using C = HdiffCfg<T>;
     constexpr int STG = TMA ? C::STAGES : 1;
-    // binary64: the exact fixed-point form (integer pipe); binary32: the definition in binary32
-    constexpr bool FX = sizeof(T) == 8;
-    constexpr int smem = hdiff_smem_bytes<T, C::TI, C::TJ, STG, FX>();
-    auto kern = [] {
-        if constexpr (FX) return hdiff_fx_kernel<C::TI, C::TJ, C::NT, STG, TMA, VEC>;
-        else return hdiff_kernel<T, C::TI, C::TJ, C::NT, STG, TMA, VEC>;
-    }();
+    // binary64: exact fixed-point lap/flux chain on the integer pipe; binary32: the definition
+    constexpr bool FIXED = sizeof(T) == 8;
+    constexpr int smem = hdiff_rs_smem_bytes<T, C::CPL, C::W, C::R, STG>();
+    constexpr int NT = 32 * C::W;
+    auto kern = hdiff_rs_kernel<T, C::CPL, C::W, C::R, STG, TMA, FIXED>;
     if (prepare_kernel(kern, smem) != cudaSuccess) return launch_status("hdiff: shared-memory attribute");
     static int slots_cache[64] = {0};
     const int dev = current_device();
     int slots = dev < 64 ? slots_cache[dev] : 0;
     if (!slots) {
-        slots = resident_blocks(kern, C::NT, smem) * sm_count();
+        slots = resident_blocks(kern, NT, smem) * sm_count();
         if (dev < 64) slots_cache[dev] = slots;
     }
     // one wave of work items: split K so that tiles x chunks fills the resident slots
     const int chunks = std::max(1, std::min(g.K, slots / std::max(1, g.n_tiles)));
     g.kc = (g.K + chunks - 1) / chunks;
     const int items = g.n_tiles * ((g.K + g.kc - 1) / g.kc);
-    kern<<<items, C::NT, smem, st>>>(map, in, cf, out, g);
+    kern<<<items, NT, smem, st>>>(map, in, cf, out, g, vec_ok);
     return launch_status("hdiff launch");
 }
 
@@ -217,11 +217,12 @@ template <typename T>
 static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field *fout, const int64_t dom[3],
                      cudaStream_t st) {
     using C = HdiffCfg<T>;
+    using Tile = RsTile<T, C::CPL, C::W, C::R>;
     const View<T> in = view_of<T>(fin), cf = view_of<T>(fcf), out = view_of<T>(fout);
     HdiffGeom g{};
     g.I = (int)dom[0], g.J = (int)dom[1], g.K = (int)dom[2];
-    g.tiles_i = (g.I + C::TI - 1) / C::TI;
-    g.tiles_j = (g.J + C::TJ - 1) / C::TJ;
+    g.tiles_i = (g.I + Tile::TI - 1) / Tile::TI;
+    g.tiles_j = (g.J + Tile::TJ - 1) / Tile::TJ;
     g.n_tiles = g.tiles_i * g.tiles_j;
 
     // TMA path: storage base rounded down to 16 B, pitches multiples of 16 B
@@ -242,7 +243,7 @@ static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field
         g.Z0 = (int)fin->origin[2];
         cuuint64_t gdim[3] = {(cuuint64_t)(fin->shape[0] + shift), (cuuint64_t)fin->shape[1], (cuuint64_t)fin->shape[2]};
         cuuint64_t gstride[2] = {(cuuint64_t)(fin->strides[1] * es), (cuuint64_t)(fin->strides[2] * es)};
-        cuuint32_t box[3] = {(cuuint32_t)HdiffTile<T, C::TI, C::TJ>::BX, (cuuint32_t)HdiffTile<T, C::TI, C::TJ>::BY, 1};
+        cuuint32_t box[3] = {(cuuint32_t)Tile::BX, (cuuint32_t)Tile::BY, 1};
         cuuint32_t estr[3] = {1, 1, 1};
         CUresult r = encode_fn()(&map, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                                  3, reinterpret_cast<void *>(abase), gdim, gstride, box, estr,
@@ -254,36 +255,50 @@ static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field
     auto aligned = [&](const View<T> &v) {
         return reinterpret_cast<uintptr_t>(v.p) % 16 == 0 && (v.sj * es) % 16 == 0 && (v.sk * es) % 16 == 0;
     };
-    const bool vec = aligned(cf) && aligned(out);
-    if (tma)
-        return vec ? launch_hdiff_t<T, true, C::VEC>(map, in, cf, out, g, st)
-                   : launch_hdiff_t<T, true, 1>(map, in, cf, out, g, st);
-    return vec ? launch_hdiff_t<T, false, C::VEC>(map, in, cf, out, g, st)
-               : launch_hdiff_t<T, false, 1>(map, in, cf, out, g, st);
+    const int vec = (aligned(cf) && aligned(out)) ? 1 : 0;
+    return tma ? launch_hdiff_t<T, true>(map, in, cf, out, g, vec, st)
+               : launch_hdiff_t<T, false>(map, in, cf, out, g, vec, st);
 }
 
 // ------------------------------------------------------------------ vadv
 constexpr int kVadvMaxK = 448;
 
-template <typename T, typename N, int BJ>
-static int launch_vadv_t(const gtb_field *const f[6], const VadvGeom &g, cudaStream_t st) {
+template <typename T, typename N, int BJ, bool WS>
+static int launch_vadv_t(const gtb_field *const f[6], const VadvGeom &g, void *ws, cudaStream_t st) {
     constexpr bool DPG = vadv_dp_global<T, N>();
-    auto kern = vadv_kernel<T, N, BJ, DPG>;
-    const int smem = (int)(vadv_smem_per_col_level<T, N>() * g.K * 32 * BJ);
-    if (prepare_kernel(kern, 227 * 1024) != cudaSuccess) return launch_status("vadv: shared-memory attribute");
+    auto kern = vadv_kernel<T, N, BJ, DPG, WS>;
+    const int smem = WS ? 0 : (int)(vadv_smem_per_col_level<T, N>() * g.K * 32 * BJ);
+    if (!WS && prepare_kernel(kern, 227 * 1024) != cudaSuccess)
+        return launch_status("vadv: shared-memory attribute");
     dim3 block(32, BJ), grid((g.I + 31) / 32, (g.J + BJ - 1) / BJ);
     kern<<<grid, block, smem, st>>>(view_of<const T>(f[0]), view_of<const T>(f[1]), view_of<const T>(f[2]),
-                                    view_of<const T>(f[3]), view_of<const T>(f[4]), view_of<T>(f[5]), g);
+                                    view_of<const T>(f[3]), view_of<const T>(f[4]), view_of<T>(f[5]), g,
+                                    static_cast<N *>(ws));
     return launch_status("vadv launch");
 }
 
-// Columns per block: two warps while a block's column state stays within
-// 48 KB (several blocks per SM), else one warp (K up to the 448 limit).
 template <typename T, typename N>
-static int run_vadv_n(const gtb_field *const f[6], const VadvGeom &g, cudaStream_t st) {
+static size_t vadv_ws_bytes(const int64_t dom[3]) {
+    return (size_t)(vadv_dp_global<T, N>() ? 1 : 2) * sizeof(N) * (size_t)dom[0] * (size_t)dom[1] * (size_t)dom[2];
+}
+
+// With a large enough workspace: column state in global memory (L2), two warps
+// per block.  Without: column state in shared memory, two warps per block while
+// it stays within 48 KB (several blocks per SM), else one.
+template <typename T, typename N>
+static int run_vadv_n(const gtb_field *const f[6], const VadvGeom &g, void *ws, size_t ws_bytes, cudaStream_t st) {
+    const int64_t dom[3] = {g.I, g.J, g.K};
+    if (ws && ws_bytes >= vadv_ws_bytes<T, N>(dom)) return launch_vadv_t<T, N, 2, true>(f, g, ws, st);
     const size_t per_col = vadv_smem_per_col_level<T, N>() * (size_t)g.K;
-    if (per_col * 64 <= 48 * 1024) return launch_vadv_t<T, N, 2>(f, g, st);
-    return launch_vadv_t<T, N, 1>(f, g, st);
+    if (per_col * 64 <= 48 * 1024) return launch_vadv_t<T, N, 2, false>(f, g, nullptr, st);
+    return launch_vadv_t<T, N, 1, false>(f, g, nullptr, st);
+}
+
+static size_t vadv_ws_bytes_for(int dt, int prec, const int64_t dom[3]) {
+    if (dt == GTB_F64) return vadv_ws_bytes<double, double>(dom);
+    if (prec == GTB_PREC_F64) return vadv_ws_bytes<float, double>(dom);
+    if (prec == GTB_PREC_DF) return vadv_ws_bytes<float, df>(dom);
+    return vadv_ws_bytes<float, float>(dom);
 }
 
 }  // namespace gtb
@@ -321,7 +336,7 @@ extern "C" int gtb_hdiff(const gtb_field *in, const gtb_field *coeff, const gtb_
 extern "C" int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u_pos,
                         const gtb_field *utens, const gtb_field *utens_stage, const gtb_field *utens_stage_out,
                         double dtr_stage, double beta_v, int prec, unsigned flags, const int64_t *domain,
-                        void *stream) {
+                        void *workspace, size_t workspace_bytes, void *stream) {
     const gtb_field *f[6] = {u_stage, wcon, u_pos, utens, utens_stage, utens_stage_out};
     static const char *names[6] = {"u_stage", "wcon", "u_pos", "utens", "utens_stage", "utens_stage_out"};
     for (int q = 0; q < 6; ++q)
@@ -362,11 +377,32 @@ extern "C" int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const g
     // a_k = bp * (-w_k/2): with w_k = s_k/2 (average) that is (-bp/4) s_k, else (-bp/2) s_k
     g.ka = (literal ? -0.5 : -0.25) * bp;
     g.kas = (literal ? -0.5 : -0.25) * bm;
+    {
+        int n = 0;
+        const double m = std::frexp(-g.ka, &n);  // -ka = m 2^n, m in [0.5, 1)
+        g.ka_pow2 = (m == 0.5 && n - 1 < 0 && n - 1 > -64) ? n - 1 : 0;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (dt == GTB_F64) return run_vadv_n<double, double>(f, g, st);
-    if (prec == GTB_PREC_F64) return run_vadv_n<float, double>(f, g, st);
-    if (prec == GTB_PREC_DF) return run_vadv_n<float, df>(f, g, st);
-    return run_vadv_n<float, float>(f, g, st);
+    if (workspace) {
+        if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
+            return fail(GTB_ERR_LAYOUT, "gtb_vadv: workspace must be 16-byte aligned");
+        const gtb_field wsf{workspace, dt, 0, {(int64_t)(workspace_bytes / dtype_size(dt)), 1, 1},
+                            {1, (int64_t)(workspace_bytes / dtype_size(dt)), (int64_t)(workspace_bytes / dtype_size(dt))},
+                            {0, 0, 0}};
+        for (int q = 0; q < 6; ++q)
+            if (overlaps(&wsf, f[q])) return fail(GTB_ERR_ALIAS, "gtb_vadv: workspace overlaps %s", names[q]);
+    }
+    if (dt == GTB_F64) return run_vadv_n<double, double>(f, g, workspace, workspace_bytes, st);
+    if (prec == GTB_PREC_F64) return run_vadv_n<float, double>(f, g, workspace, workspace_bytes, st);
+    if (prec == GTB_PREC_DF) return run_vadv_n<float, df>(f, g, workspace, workspace_bytes, st);
+    return run_vadv_n<float, float>(f, g, workspace, workspace_bytes, st);
+}
+
+extern "C" size_t gtb_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain) {
+    if (!domain || !dtype_size(dtype) || prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return 0;
+    for (int d = 0; d < 3; ++d)
+        if (domain[d] < 0) return 0;
+    return vadv_ws_bytes_for(dtype, dtype == GTB_F64 ? GTB_PREC_NATIVE : prec, domain);
 }
 
 extern "C" int gtb_device_status(void *stream) {

@@ -287,7 +287,7 @@ __device__ __forceinline__ int64_t to_fixed(double x, int E) {
     uint64_t m = b & 0x000FFFFFFFFFFFFFull;
     if (e) m |= 0x0010000000000000ull;
     else e = 1;  // subnormal: no implicit bit, exponent of the smallest normal
-    const int sh = e - E + 3;  // <= 3
+    const int sh = min(e - E + 3, 3);  // <= 3 for every value the scan covered
     uint64_t v;
     if (sh >= 0) v = m << sh;
     else v = (sh > -64) ? (m >> (-sh)) : 0ull;

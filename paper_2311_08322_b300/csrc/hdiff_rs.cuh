@@ -1,0 +1,286 @@
+// hdiff_rs.cuh -- register-streaming hdiff (GT4Py paper Sec. 3.1, horizontal
+// diffusion; one PARALLEL computation, Sec. 2.2):
+//   lap = 4 in - (((in[i+1] + in[i-1]) + in[j+1]) + in[j-1])
+//   fx  = lap[i+1] - lap[i], 0 where fx * (in[i+1] - in[i]) > 0;  fy likewise
+//   out = in - coeff ((fx[i] - fx[i-1]) + (fy[j] - fy[j-1]))
+//
+// CTA = W warps on a TI x TJ tile (TI = 32*CPL columns, TJ = W*R rows) for a
+// run of K levels.  Per level the tile box (+2 halo, left edge rounded down to
+// 16 bytes) arrives by one TMA tiled load into a STAGES-deep mbarrier ring.
+// Warp w owns rows [w*R, w*R+R) and all TI columns: lane l holds columns
+// l*CPL .. l*CPL+CPL-1 and rolls down j keeping in, lap and fy of its columns
+// in registers; the i-neighbours come from adjacent lanes by shuffles, and the
+// two columns just outside the warp (i = -1 and i = TI) are computed once per
+// strip by the warp itself (16 rows per side, one lane per row).  Temporaries
+// never leave registers (Sec. 2.2 temporaries); one CTA barrier per level
+// releases the stage.
+//
+// Arithmetic policies:
+//   Native<T>  the definition in binary32 / binary64;
+//   FixedF64   binary64 storage: the lap -> flux -> divergence chain in exact
+//              int64 fixed point (integer pipe), one FP64 FMA per point for
+//              out = in - coeff * D; a warp whose strip holds inf/NaN or
+//              exponents outside [64, 2040] switches to Native<double>.
+#pragma once
+
+#include "hdiff_kernels.cuh"
+
+namespace gtb {
+
+template <typename T>
+struct Native {
+    using V = T;  // value type of in, lap, flux
+    using Gd = T; // gradient in[i+1] - in[i]
+    __device__ __forceinline__ V conv(T x) const { return x; }
+    __device__ __forceinline__ V lap(V c, V e, V w, V n, V s) const { return T(4) * c - (((e + w) + n) + s); }
+    __device__ __forceinline__ Gd grad(V x1, V x0, const T *, const T *) const { return x1 - x0; }
+    __device__ __forceinline__ V limit(V f, Gd g) const { return (f * g > T(0)) ? T(0) : f; }
+    __device__ __forceinline__ T out(T in, T c, V D) const { return in - c * D; }
+};
+
+struct FixedF64 {
+    using V = int64_t;
+    using Gd = int;
+    int E;
+    __device__ __forceinline__ V conv(double x) const { return to_fixed(x, E); }
+    __device__ __forceinline__ V lap(V c, V e, V w, V n, V s) const { return 4 * c - (((e + w) + n) + s); }
+    // exact sign of in1 - in0; the binary64 values are read only when X1 == X0
+    __device__ __forceinline__ Gd grad(V x1, V x0, const double *p1, const double *p0) const {
+        if (x1 != x0) return x1 > x0 ? 1 : -1;
+        return exact_dir(x1, x0, *p1, *p0);
+    }
+    __device__ __forceinline__ V limit(V f, Gd g) const { return ((f > 0 && g > 0) || (f < 0 && g < 0)) ? 0 : f; }
+    __device__ __forceinline__ double out(double in, double c, V D) const { return fma(-c, from_fixed(D, E), in); }
+};
+
+template <typename T, int CPL, int W, int R>
+struct RsTile {
+    static constexpr int TI = 32 * CPL, TJ = W * R;
+    static constexpr int kAlign = 16 / (int)sizeof(T);
+    static constexpr int BX = ((TI + 4 + kAlign - 1 + kAlign - 1) / kAlign) * kAlign;
+    static constexpr int BY = TJ + 4;
+    static constexpr int box_elems = BX * BY;
+    static constexpr int box_bytes = box_elems * (int)sizeof(T);
+    static constexpr int stage_stride = ((box_bytes + 127) / 128) * 128;
+};
+
+template <typename T, int CPL, int W, int R, int STAGES>
+constexpr int hdiff_rs_smem_bytes() {
+    return STAGES * RsTile<T, CPL, W, R>::stage_stride + STAGES * 8 + 128;
+}
+
+// One warp's R-row strip of one level.  S: the level's box; bx(ci) = ci+2+xs,
+// by(cj) = cj+2 (tile-relative ci, cj).  cf: this lane's coeff rows.
+template <typename T, int CPL, int R, int BX, typename P>
+__device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int cj0, int ncols, int nrows,
+                                         const T *cfp, int64_t cf_sj, T *op, int64_t out_sj, bool vec_ok) {
+    using V = typename P::V;
+    using Gd = typename P::Gd;
+    const int lane = threadIdx.x & 31;
+    const int ci0 = lane * CPL;
+    auto at = [&](int ci, int cj) -> T { return S[(cj + 2) * BX + ci + 2 + xs]; };
+    auto ptr = [&](int ci, int cj) -> const T * { return S + (cj + 2) * BX + ci + 2 + xs; };
+
+    // ---- the two columns outside the warp: i = -1 (lanes 0-15) and i = TI (16-31)
+    const int side = lane >> 4, er = lane & 15;
+    const int eci = side ? 32 * CPL : -1;
+    const int ecj = cj0 + min(er, R - 1);
+    V ex_c = pol.conv(at(eci, ecj)), ex_u = pol.conv(at(eci, ecj - 1)), ex_d = pol.conv(at(eci, ecj + 1));
+    const V e_lap = pol.lap(ex_c, pol.conv(at(eci + 1, ecj)), pol.conv(at(eci - 1, ecj)), ex_d, ex_u);
+    // X of the outside column at strip row t (t in [-1, R]) for lane 0 (left) / lane 31 (right)
+    auto edge_x = [&](int t) -> V {
+        const V send = (t < 0) ? ex_u : (t >= R ? ex_d : ex_c);
+        const int src = (lane < 16 ? 0 : 16) + max(0, min(t, R - 1));
+        return __shfl_sync(0xffffffffu, send, src);
+    };
+    auto edge_lap = [&](int t) -> V { return __shfl_sync(0xffffffffu, e_lap, (lane < 16 ? 0 : 16) + t); };
+
+    // ---- rolling state; strip row t <-> tile row cj0 + t
+    V xa[CPL], xb[CPL], xc[CPL];  // X at rows t-1, t, t+1
+    V lp[CPL], fyp[CPL];          // lap(t-1), fy(t-2)
+    V nbL_prev = V(0), nbR_prev = V(0);  // X(c-1), X(c+1) at row t-1 for the outer columns
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        xa[q] = pol.conv(at(ci0 + q, cj0 - 2));
+        xb[q] = pol.conv(at(ci0 + q, cj0 - 1));
+        xc[q] = pol.conv(at(ci0 + q, cj0));
+        lp[q] = V(0), fyp[q] = V(0);
+    }
+    // coeff ring: at the top of iteration t, cf0/cf1/cf2 hold rows t-1, t, t+1
+    auto load_cf = [&](int row, T (&v)[CPL]) {
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) v[q] = (row >= 0 && row < nrows && q < ncols) ? cfp[(int64_t)(cj0 + row) * cf_sj + q] : T(0);
+    };
+    T cf0[CPL], cf1[CPL], cf2[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) cf0[q] = T(0), cf1[q] = T(0);
+    load_cf(0, cf2);
+    // iteration t computes lap(row t) for t = -1 .. R and emits out(row t-1) for t >= 1
+#pragma unroll 1
+    for (int t = -1; t <= R; ++t) {
+        // X neighbours in i at row t
+        V up = __shfl_up_sync(0xffffffffu, xb[CPL - 1], 1);
+        V dn = __shfl_down_sync(0xffffffffu, xb[0], 1);
+        const V ex = edge_x(t);
+        if (lane == 0) up = ex;
+        if (lane == 31) dn = ex;
+        V lc[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            const V w = (q == 0) ? up : xb[q - 1];
+            const V e = (q == CPL - 1) ? dn : xb[q + 1];
+            lc[q] = pol.lap(xb[q], e, w, xc[q], xa[q]);
+        }
+        if (t >= 0) {
+            // fy(row t-1) = lap(t) - lap(t-1), gradient in(t) - in(t-1)
+            V fyc[CPL];
+#pragma unroll
+            for (int q = 0; q < CPL; ++q)
+                fyc[q] = pol.limit(lc[q] - lp[q], pol.grad(xb[q], xa[q], ptr(ci0 + q, cj0 + t), ptr(ci0 + q, cj0 + t - 1)));
+            if (t >= 1) {
+                // output row j = t-1: fx(row j) from lap(t-1) (= lp) of this lane and its right neighbour
+                const int j = t - 1;
+                V lnext = __shfl_down_sync(0xffffffffu, lp[0], 1);
+                const V el = edge_lap(j);
+                if (lane == 31) lnext = el;
+                V fx[CPL];
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const V ln = (q == CPL - 1) ? lnext : lp[q + 1];
+                    const V xn = (q == CPL - 1) ? nbR_prev : xa[q + 1];
+                    fx[q] = pol.limit(ln - lp[q], pol.grad(xn, xa[q], ptr(ci0 + q + 1, cj0 + j), ptr(ci0 + q, cj0 + j)));
+                }
+                V fxw = __shfl_up_sync(0xffffffffu, fx[CPL - 1], 1);
+                if (lane == 0)  // fx(i = -1) = lap(0) - lap(-1)
+                    fxw = pol.limit(lp[0] - el, pol.grad(xa[0], nbL_prev, ptr(0, cj0 + j), ptr(-1, cj0 + j)));
+                T r[CPL];
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const V fwq = (q == 0) ? fxw : fx[q - 1];
+                    const V D = (fx[q] - fwq) + (fyc[q] - fyp[q]);
+                    r[q] = pol.out(at(ci0 + q, cj0 + j), cf0[q], D);
+                }
+                if (j < nrows) {
+                    T *o = op + (int64_t)(cj0 + j) * out_sj;
+                    if (vec_ok && ncols >= CPL) {
+                        store_vec<T, CPL>(o, r);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q)
+                            if (q < ncols) o[q] = r[q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) fyp[q] = fyc[q];
+        }
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            lp[q] = lc[q];
+            xa[q] = xb[q];
+            xb[q] = xc[q];
+            if (t + 2 <= R + 1) xc[q] = pol.conv(at(ci0 + q, cj0 + t + 2));
+        }
+        nbL_prev = up, nbR_prev = dn;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) cf0[q] = cf1[q], cf1[q] = cf2[q];
+        load_cf(t + 2, cf2);
+    }
+}
+
+template <typename T, int CPL, int W, int R, int STAGES, bool USE_TMA, bool FIXED>
+__global__ void __launch_bounds__(32 * W)
+    hdiff_rs_kernel(const __grid_constant__ CUtensorMap tmap, const View<T> in, const View<T> coeff,
+                    const View<T> out, const HdiffGeom g, const int vec_ok) {
+    using G = RsTile<T, CPL, W, R>;
+    constexpr int NT = 32 * W;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + STAGES * G::stage_stride);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x % g.n_tiles, kchunk = blockIdx.x / g.n_tiles;
+    const int ti0 = (tile % g.tiles_i) * G::TI, tj0 = (tile / g.tiles_i) * G::TJ;
+    const int k0 = kchunk * g.kc;
+    const int nk = min(g.kc, g.K - k0);
+    if (nk <= 0) return;
+    const int xs = g.xs;
+    const int cj0 = warp * R;
+    const int nrows = max(0, min(R, g.J - tj0 - cj0));  // rows of this strip inside the domain
+    const int ncols = max(0, min(CPL, g.I - ti0 - lane * CPL));
+
+    // TMA ring (same protocol as the tile kernels)
+    if (USE_TMA) {
+        if (tid == 0) {
+            prefetch_tensormap(&tmap);
+            for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0)
+            for (int p = 0; p < STAGES && p < nk; ++p) {
+                mbar_arrive_expect_tx(&bars[p], G::box_bytes);
+                tma_load_3d(base + p * G::stage_stride, &tmap, &bars[p], g.X0 + ti0, g.Y0 + tj0, g.Z0 + k0 + p);
+            }
+    }
+    bool failed = false;
+    for (int p = 0; p < nk; ++p) {
+        const int k = k0 + p;
+        const T *S = reinterpret_cast<const T *>(base + (USE_TMA ? (p % STAGES) : 0) * G::stage_stride);
+        if (USE_TMA) {
+            if (!mbar_wait(&bars[p % STAGES], (p / STAGES) & 1)) failed = true;
+        } else {
+            T *D = reinterpret_cast<T *>(base);
+            for (int idx = tid; idx < G::box_elems; idx += NT) {
+                const int bx = idx % G::BX, by = idx / G::BX;
+                const int i = ti0 - 2 - xs + bx, j = tj0 - 2 + by;
+                T v = T(0);
+                if (i >= -2 && i < g.I + 2 && j >= -2 && j < g.J + 2)
+                    v = in.p[(int64_t)i + (int64_t)j * in.sj + (int64_t)k * in.sk];
+                D[idx] = v;
+            }
+            __syncthreads();
+        }
+        if (__syncthreads_or(failed)) break;
+        if (nrows > 0) {
+            const T *cfp = coeff.p + (int64_t)(ti0 + lane * CPL) + (int64_t)tj0 * coeff.sj + (int64_t)k * coeff.sk;
+            T *op = out.p + (int64_t)(ti0 + lane * CPL) + (int64_t)tj0 * out.sj + (int64_t)k * out.sk;
+            if constexpr (FIXED) {
+                // largest biased exponent over the values the strip's stored outputs read:
+                // the domain part of rows cj0-2 .. cj0+nrows+1, columns -2 .. ntile+1 (never the
+                // storage padding beyond the halo, whose contents are arbitrary)
+                const int ntile = min(G::TI, g.I - ti0);
+                const int wx = ntile + 4, wy = nrows + 4;
+                unsigned emax = 0;
+                for (int idx = lane; idx < wx * wy; idx += 32) {
+                    const int bx = idx % wx + xs, by = idx / wx + cj0;
+                    emax = max(emax, ((unsigned)__double2hiint(S[by * G::BX + bx]) >> 20) & 0x7FFu);
+                }
+                const int E = (int)__reduce_max_sync(0xffffffffu, emax);
+                if (E >= 64 && E <= 2040)
+                    rs_strip<T, CPL, R, G::BX>(FixedF64{E}, S, xs, cj0, ncols, nrows, cfp, coeff.sj, op, out.sj,
+                                               vec_ok != 0);
+                else
+                    rs_strip<T, CPL, R, G::BX>(Native<T>{}, S, xs, cj0, ncols, nrows, cfp, coeff.sj, op, out.sj,
+                                               vec_ok != 0);
+            } else {
+                rs_strip<T, CPL, R, G::BX>(Native<T>{}, S, xs, cj0, ncols, nrows, cfp, coeff.sj, op, out.sj,
+                                           vec_ok != 0);
+            }
+        }
+        __syncthreads();  // every warp is done with this stage
+        if (USE_TMA && tid == 0 && p + STAGES < nk) {
+            const int s = p % STAGES;
+            mbar_arrive_expect_tx(&bars[s], G::box_bytes);
+            tma_load_3d(base + s * G::stage_stride, &tmap, &bars[s], g.X0 + ti0, g.Y0 + tj0, g.Z0 + k + STAGES);
+        }
+    }
+    if (USE_TMA && failed) {
+        if (tid == 0)
+            for (int s = 0; s < STAGES; ++s) mbar_wait(&bars[s], 0), mbar_wait(&bars[s], 1);
+        __syncthreads();
+    }
+}
+
+}  // namespace gtb

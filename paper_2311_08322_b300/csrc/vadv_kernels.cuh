@@ -26,6 +26,7 @@ struct VadvGeom {
     double dtr;   // dtr_stage
     double ka;    // a_k  = ka  * s_k  (s_k = wcon(i)+wcon(i+1), or wcon(i) when literal)
     double kas;   // as_k = kas * s_k;  c_{k-1} = -a_k, cs_{k-1} = -as_k
+    int ka_pow2;  // n < 0 when ka = -2^n exactly (a_k is then an exponent shift), else 0
 };
 
 template <typename N> __device__ __forceinline__ N num_const(double c);
@@ -83,17 +84,42 @@ __device__ __forceinline__ void load_level(Level<T> &L, int k, int K, const T *p
     }
 }
 
+// s * 2^n (n < 0) with a sign flip, exact for normal binary64 inputs: the
+// exponent field is adjusted on the integer pipe; inputs that would leave the
+// normal range take the FP64 multiply.
+__device__ __forceinline__ double scale_pow2(double s, double k, int n) {
+    const int hi = __double2hiint(s), lo = __double2loint(s);
+    const int e = (hi >> 20) & 0x7FF;
+    if (e + n >= 1 && e < 2047) return __hiloint2double((hi + (n << 20)) ^ 0x80000000, lo);
+    return k * s;
+}
+
+template <typename N>
+__device__ __forceinline__ N coef(N s, N k, int n) {
+    return k * s;
+}
+template <>
+__device__ __forceinline__ double coef<double>(double s, double k, int n) {
+    return n ? scale_pow2(s, k, n) : k * s;
+}
+
+// Where the forward sweep keeps its eliminated coefficients:
+//  * WS = false: c'_k (and d'_k unless parked) in shared memory, [K][block
+//    columns]; the K x 32 x BJ state caps the resident warps per SM.
+//  * WS = true: in a caller-provided global workspace, [K][I*J] (column id
+//    j*I + i, coalesced along i); it is written and read back within a few
+//    microseconds, so it lives in L2.  No shared memory is needed and the
+//    resident warps are bounded by registers only: on B300 the FP64
+//    recurrence runs at the pipe's rate only with many warps per SM (one
+//    warp keeps about one FP64 instruction in flight), so this is the fast form.
 // DPG: d'_k is parked in the output array (same element size as N) and read
-// back by the backward sweep from L2; only c'_k stays in shared memory.
-// Otherwise both live in shared memory.
-template <typename T, typename N, int BJ, bool DPG>
+// back by the backward sweep from L2.
+template <typename T, typename N, int BJ, bool DPG, bool WS>
 __global__ void __launch_bounds__(32 * BJ)
     vadv_kernel(const View<const T> us, const View<const T> wc, const View<const T> up, const View<const T> ut,
-                const View<const T> uts, const View<T> out, const VadvGeom g) {
+                const View<const T> uts, const View<T> out, const VadvGeom g, N *__restrict__ ws) {
     constexpr int NT = 32 * BJ;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    N *cpb = reinterpret_cast<N *>(smem_raw);  // [K][NT]
-    N *dpb = cpb + (size_t)g.K * NT;           // [K][NT] (unused when DPG)
 
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
     const int i = blockIdx.x * 32 + tx, j = blockIdx.y * BJ + ty;
@@ -101,6 +127,22 @@ __global__ void __launch_bounds__(32 * BJ)
     const int ic = min(i, g.I - 1), jc = min(j, g.J - 1);
     const int iw = min(i, g.I);  // wcon is valid up to i = I (staggered)
     const int K = g.K;
+
+    // c' / d' addressing: element k of this column at base[k * cstride + cidx]
+    N *cpb, *dpb;
+    size_t cstride, cidx;
+    if (WS) {
+        cstride = (size_t)g.I * g.J;
+        cidx = (size_t)jc * g.I + ic;
+        cpb = ws;
+        dpb = ws + (size_t)K * cstride;  // used only when d' is not parked in the output
+    } else {
+        cstride = NT;
+        cidx = t;
+        cpb = reinterpret_cast<N *>(smem_raw);
+        dpb = cpb + (size_t)K * NT;
+    }
+    const bool wr = WS ? active : true;  // inactive lanes alias a real column in the workspace
 
     const T *pus = us.p + ic + (int64_t)jc * us.sj;
     const T *pup = up.p + ic + (int64_t)jc * up.sj;
@@ -116,12 +158,12 @@ __global__ void __launch_bounds__(32 * BJ)
     const N ka = num_const<N>(g.ka);
     const N kas = num_const<N>(g.kas);
     const N zero = num_const<N>(0.0);
+    const int kexp = g.ka_pow2;  // a = ka * s as an exact exponent shift when ka = -2^kexp
 
 #define GTB_LOAD(L, k) load_level<T>(L, k, K, pup, put, puts, pus, pw, pw1, up.sk, ut.sk, uts.sk, us.sk, wc.sk, last_lane)
-    Level<T> L0, L1, L2;  // levels k, k+1, k+2
+    Level<T> L0, L1;  // levels k, k+1 (prefetch distance 2)
     GTB_LOAD(L0, 0);
     GTB_LOAD(L1, 1);
-    GTB_LOAD(L2, 2);
 
     N us_cur = to_num<N, T>(pus[0]);
     N dm = zero;                    // u_stage_{k-1} - u_stage_k
@@ -140,7 +182,7 @@ __global__ void __launch_bounds__(32 * BJ)
                 if (last_lane) hi = L0.w1;
                 s = to_num<N, T>(L0.w) + to_num<N, T>(hi);
             }
-            a_next = ka * s;
+            a_next = coef<N>(s, ka, kexp);
             as_next = g.sym ? a_next : kas * s;
             const N us_next = to_num<N, T>(L0.us1);
             dpl = us_next - us_cur;  // u_stage_{k+1} - u_stage_k
@@ -158,18 +200,17 @@ __global__ void __launch_bounds__(32 * BJ)
         }
         const N r = recip(p);
         const N cpk = (-a_next) * r, dpk = num * r;
-        cpb[(size_t)k * NT + t] = cpk;
+        if (wr) cpb[(size_t)k * cstride + cidx] = cpk;
         if (DPG) {
             if (active) po[(int64_t)k * out.sk] = to_store<T, N>(dpk);
-        } else {
-            dpb[(size_t)k * NT + t] = dpk;
+        } else if (wr) {
+            dpb[(size_t)k * cstride + cidx] = dpk;
         }
         cp_prev = cpk, dp_prev = dpk;
         dm = -dpl;
         a_cur = a_next, as_cur = as_next;
         L0 = L1;
-        L1 = L2;
-        GTB_LOAD(L2, k + 3);
+        GTB_LOAD(L1, k + 2);
     }
 #undef GTB_LOAD
 
@@ -178,10 +219,8 @@ __global__ void __launch_bounds__(32 * BJ)
     if (active) po[(int64_t)(K - 1) * out.sk] = to_store<T, N>(dtr * (x - to_num<N, T>(pup[(int64_t)(K - 1) * up.sk])));
 #pragma unroll 4
     for (int k = K - 2; k >= 0; --k) {
-        N dk;
-        if (DPG) dk = to_num<N, T>(po[(int64_t)k * out.sk]);
-        else dk = dpb[(size_t)k * NT + t];
-        x = dk - cpb[(size_t)k * NT + t] * x;
+        const N dk = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : dpb[(size_t)k * cstride + cidx];
+        x = dk - cpb[(size_t)k * cstride + cidx] * x;
         const N o = dtr * (x - to_num<N, T>(pup[(int64_t)k * up.sk]));
         if (active) po[(int64_t)k * out.sk] = to_store<T, N>(o);
     }

@@ -42,7 +42,8 @@ class GtbError(RuntimeError):
 
 
 _lib = None
-EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_device_status", "gtb_last_error", "gtb_version")
+EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_device_status", "gtb_last_error",
+           "gtb_version")
 
 
 def lib() -> ctypes.CDLL:
@@ -56,7 +57,9 @@ def lib() -> ctypes.CDLL:
         i64p, vp = ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p
         L.gtb_hdiff.argtypes = [P, P, P, i64p, vp]
         L.gtb_vadv.argtypes = [P, P, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint,
-                               i64p, vp]
+                               i64p, vp, ctypes.c_size_t, vp]
+        L.gtb_vadv_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, i64p]
+        L.gtb_vadv_workspace_bytes.restype = ctypes.c_size_t
         L.gtb_device_status.argtypes = [vp]
         L.gtb_last_error.restype = ctypes.c_char_p
         L.gtb_version.restype = ctypes.c_char_p
@@ -171,13 +174,54 @@ def hdiff(in_, coeff, out, *, domain=None, stream=None):
     return out
 
 
+def vadv_workspace_bytes(dtype, prec, domain) -> int:
+    """Workspace bytes gtb_vadv uses for this storage dtype, prec and domain (I, J, K)."""
+    dt = {torch.float64: GTB_F64, torch.float32: GTB_F32}.get(dtype, dtype)
+    return int(lib().gtb_vadv_workspace_bytes(dt, PREC[prec] if isinstance(prec, str) else int(prec), _dom(domain)))
+
+
+_ws_cache = {}
+
+
+def workspace(nbytes: int, stream=None) -> torch.Tensor:
+    """A cached device scratch buffer of at least ``nbytes`` bytes for one (device, stream):
+    calls that may run concurrently on different streams get different buffers."""
+    key = (torch.cuda.current_device(), _stream(stream).value)
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(nbytes, 16), dtype=torch.uint8, device="cuda")
+        _ws_cache[key] = buf
+    return buf
+
+
+def _vadv_domain(fs, literal):
+    """Deduced domain: the largest keeping every access inside its storage (paper Sec. 2.2)."""
+    dom = []
+    for d in range(3):
+        reach = [1 if (q == 1 and d == 0 and not literal) else 0 for q in range(6)]
+        dom.append(min(f.shape[d] - f.origin[d] - r for f, r in zip(fs, reach)))
+    return tuple(max(0, x) for x in dom)
+
+
 def vadv(u_stage, wcon, u_pos, utens, utens_stage, out=None, *, dtr_stage=3.0 / 20.0, beta_v=0.0,
-         prec="native", literal=False, domain=None, stream=None):
-    """utens_stage_out = vadv(...) (gtb_vadv); ``out=None`` updates utens_stage in place."""
+         prec="native", literal=False, domain=None, workspace="auto", stream=None):
+    """utens_stage_out = vadv(...) (gtb_vadv); ``out=None`` updates utens_stage in place.
+
+    ``workspace``: "auto" (a cached buffer from :func:`workspace`, the fast
+    form), a CUDA tensor, or None (column state in shared memory)."""
     out = utens_stage if out is None else out
     fs = [_as_field(x) for x in (u_stage, wcon, u_pos, utens, utens_stage, out)]
-    _check(lib().gtb_vadv(*[ctypes.byref(f) for f in fs], float(dtr_stage), float(beta_v), PREC[prec],
-                          GTB_WCON_LITERAL if literal else 0, _dom(domain), _stream(stream)))
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        if isinstance(workspace, str):
+            dom = tuple(domain) if domain is not None else _vadv_domain(fs, literal)
+            need = vadv_workspace_bytes(fs[0].dtype, prec, dom)
+            workspace = globals()["workspace"](need, stream) if need else None
+        if workspace is not None:
+            ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    _check(lib().gtb_vadv(*[ctypes.byref(f) for f in fs], float(dtr_stage), float(beta_v),
+                          PREC[prec] if isinstance(prec, str) else int(prec), GTB_WCON_LITERAL if literal else 0,
+                          _dom(domain), ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes, _stream(stream)))
     return out
 
 

@@ -26,7 +26,8 @@ def declared_symbols():
 
 def test_exports_every_declared_symbol(L):
     syms = declared_symbols()
-    assert {"gtb_hdiff", "gtb_vadv", "gtb_device_status", "gtb_last_error", "gtb_version"} <= set(syms)
+    assert {"gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_device_status", "gtb_last_error",
+            "gtb_version"} <= set(syms)
     lib = ctypes.CDLL(L.LIB_PATH)
     missing = [s for s in syms if not hasattr(lib, s)]
     assert not missing, missing
@@ -93,7 +94,7 @@ def test_vadv_validation(L):
     mk = lambda n, o=(1, 1, 0): fake(L, 10, 10, 6, origin=o, ptr=n * G)
     fs = [mk(n) for n in range(1, 7)]
     args = lambda fs, prec=0, flags=0, dom=(0, 8, 6): [*[ctypes.byref(f) for f in fs], 0.15, 0.0, prec, flags,
-                                                       (ctypes.c_int64 * 3)(*dom), None]
+                                                       (ctypes.c_int64 * 3)(*dom), None, 0, None]
     assert L.lib().gtb_vadv(*args(fs)) == 0
     assert L.lib().gtb_vadv(*args(fs, prec=1)) == -9       # FP64 storage: binary64 only
     assert L.lib().gtb_vadv(*args(fs, flags=4)) == -9
@@ -106,3 +107,22 @@ def test_vadv_validation(L):
     assert L.lib().gtb_vadv(*args(fs2)) == 0
     fs3 = [mk(n) for n in range(1, 6)] + [mk(5, o=(1, 2, 0))]
     assert L.lib().gtb_vadv(*args(fs3)) == -5
+
+
+def test_vadv_workspace_bytes(L):
+    """c' (and d' when it cannot be parked in the output) per domain point."""
+    dom = (10, 7, 5)
+    n = 10 * 7 * 5
+    assert L.vadv_workspace_bytes(2, 0, dom) == 8 * n
+    assert L.vadv_workspace_bytes(1, 0, dom) == 4 * n
+    assert L.vadv_workspace_bytes(1, 1, dom) == 16 * n
+    assert L.vadv_workspace_bytes(1, 2, dom) == 16 * n
+    assert L.vadv_workspace_bytes(3, 0, dom) == 0
+
+
+def test_vadv_workspace_alias_rejected(L):
+    G = 1 << 24
+    fs = [fake(L, 10, 10, 6, origin=(1, 1, 0), ptr=n * G) for n in range(1, 7)]
+    args = [*[ctypes.byref(f) for f in fs], 0.15, 0.0, 0, 0, (ctypes.c_int64 * 3)(8, 8, 6)]
+    assert L.lib().gtb_vadv(*args, ctypes.c_void_p(3 * G + 64), 4096, None) == -5
+    assert L.lib().gtb_vadv(*args, ctypes.c_void_p(40 * G + 8), 4096, None) == -4  # not 16-byte aligned

@@ -34,7 +34,7 @@ def draw(I, J, K, seed, wamp=0.5, pad=(0, 0, 0)):
 
 
 def run_case(G, orc, I, J, K, seed=0, dtype=np.float64, prec="native", pad=(0, 0, 0), inplace=False,
-             literal=False, beta_v=0.0, wamp=0.5, f=None):
+             literal=False, beta_v=0.0, wamp=0.5, f=None, workspace="auto"):
     f = draw(I, J, K, seed, wamp, pad) if f is None else f
     if dtype == np.float32:
         f = {k: v.astype(np.float32) for k, v in f.items()}
@@ -42,7 +42,7 @@ def run_case(G, orc, I, J, K, seed=0, dtype=np.float64, prec="native", pad=(0, 0
     dom = (I, J, K)
     st = {n: G.storage_from(f[n], o) for n in NAMES}
     out = st["utens_stage"] if inplace else G.storage_from(np.zeros_like(f["utens_stage"]), o)
-    G.vadv(*[st[n] for n in NAMES], out, prec=prec, literal=literal, beta_v=beta_v, domain=dom)
+    G.vadv(*[st[n] for n in NAMES], out, prec=prec, literal=literal, beta_v=beta_v, domain=dom, workspace=workspace)
     G.device_status()
     got = region(out.numpy(), o, dom)
     ref = orc.vadv(*[f[n].astype(np.float64) for n in NAMES], origin=o, domain=dom, beta_v=beta_v,
@@ -137,3 +137,22 @@ def test_zero_pivot_column(G, orc):
     bad_got = ~np.all(np.isfinite(got), axis=0)
     assert bad_ref[0, 2] and np.array_equal(bad_ref, bad_got)
     assert rel_err(got[:, ~bad_ref], ref[:, ~bad_ref]) <= F64_TOL
+
+
+@pytest.mark.parametrize("dtype,prec", [(np.float64, "native"), (np.float32, "df"), (np.float32, "f64"),
+                                        (np.float32, "native")])
+def test_shared_memory_form(G, orc, dtype, prec):
+    """Without a workspace the column state stays in shared memory; same results."""
+    tol = F64_TOL if dtype == np.float64 else (F32_TOL if prec != "native" else 1e-4)
+    for I, J, K in ((256, 64, 80), (45, 7, 137), (33, 3, 1)):
+        got, ref = run_case(G, orc, I, J, K, seed=K, dtype=dtype, prec=prec, wamp=0.15 if prec == "native" else 0.5,
+                            workspace=None)
+        assert rel_err(got, ref) <= tol, (I, J, K)
+
+
+def test_explicit_workspace_tensor_and_inplace(G, orc):
+    import torch
+    need = G.vadv_workspace_bytes(torch.float64, "native", (60, 20, 50))
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    got, ref = run_case(G, orc, 60, 20, 50, seed=77, inplace=True, workspace=ws)
+    assert rel_err(got, ref) <= F64_TOL
