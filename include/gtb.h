@@ -138,6 +138,33 @@ int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u
 size_t gtb_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain);
 
 /*
+ * gtb_vadv_noalloc -- gtb_vadv for callers that cannot allocate device memory.
+ * The paper has no counterpart: this exists for code that runs inside a host
+ * application that owns every device allocation (a fixed memory budget or a
+ * pool it will not hand buffers out of, e.g. a stencil library embedded in a
+ * model's time loop) and for latency-critical loops where cudaMalloc's
+ * implicit device-wide synchronisation is not acceptable.  Such a caller still
+ * passes its inputs and outputs, but no workspace: the forward-sweep state
+ * goes to a fixed 16 MiB array inside this library (a file-scope __device__
+ * array, held on every GPU that loads the library until the process exits).
+ * Same arguments, results and errors as gtb_vadv, plus:
+ *  - a domain whose workspace (gtb_vadv_workspace_bytes) exceeds 16 MiB
+ *    (2,097,152 points for GTB_F64 storage) is rejected with
+ *    GTB_ERR_UNSUPPORTED and nothing is enqueued;
+ *  - the first call on a device looks up the array's device address on that
+ *    device (make it before any stream capture);
+ *  - every call on a device shares the one array, and its contents carry
+ *    over between calls (nothing needs to start at zero): calls that may
+ *    overlap on the GPU (different streams, or other threads) race and must
+ *    be serialised by the caller.
+ * No call allocates or frees device memory.
+ */
+int gtb_vadv_noalloc(const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u_pos,
+                     const gtb_field *utens, const gtb_field *utens_stage,
+                     const gtb_field *utens_stage_out, double dtr_stage, double beta_v,
+                     int prec, unsigned flags, const int64_t *domain, void *stream);
+
+/*
  * gtb_device_status -- synchronises `stream`, then returns and clears the
  * device error word: GTB_OK, or GTB_ERR_DEVICE if a kernel's bounded wait
  * expired since the last call (the affected outputs are then unspecified).

@@ -422,3 +422,74 @@ extern "C" int gtb_device_status(void *stream) {
 extern "C" const char *gtb_last_error(void) { return t_err; }
 
 extern "C" const char *gtb_version(void) { return "gtb 0.1 sm_103a"; }
+
+// ====================================================================== allocation-free vadv
+// gtb_vadv_noalloc: gtb_vadv with its workspace in a fixed device array of this
+// library instead of caller memory (declared in include/gtb.h; the paper has no
+// counterpart).  The array is a file-scope __device__ variable, so it exists
+// on every GPU that loads the library, from load until exit, and no call ever
+// allocates.  Host code cannot use the array's name as a device address: the
+// address is looked up once per device with cudaGetSymbolAddress, with that
+// device current, on the first call made there.
+namespace gtb {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_vadv_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once).
+static int noalloc_scratch(void **ptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(GTB_ERR_LAUNCH, "gtb_vadv_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return fail(GTB_ERR_UNSUPPORTED, "gtb_vadv_noalloc: device ordinal %d >= 64", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_vadv_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(GTB_ERR_LAUNCH, "gtb_vadv_noalloc: cudaGetSymbolAddress of the scratch array failed: %s",
+                        cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return GTB_OK;
+}
+
+}  // namespace gtb
+
+extern "C" int gtb_vadv_noalloc(const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u_pos,
+                                const gtb_field *utens, const gtb_field *utens_stage,
+                                const gtb_field *utens_stage_out, double dtr_stage, double beta_v, int prec,
+                                unsigned flags, const int64_t *domain, void *stream) {
+    const gtb_field *f[6] = {u_stage, wcon, u_pos, utens, utens_stage, utens_stage_out};
+    for (int q = 0; q < 6; ++q)
+        if (!f[q]) return fail(GTB_ERR_NULL, "gtb_vadv_noalloc: NULL field");
+    // the domain the call will use: given, or deduced as gtb_vadv deduces it
+    int64_t dom[3];
+    if (domain) {
+        for (int d = 0; d < 3; ++d) dom[d] = domain[d];
+    } else {
+        const bool literal = flags & GTB_WCON_LITERAL;
+        for (int d = 0; d < 3; ++d) {
+            dom[d] = INT64_MAX;
+            for (int q = 0; q < 6; ++q)
+                dom[d] = std::min(dom[d], f[q]->shape[d] - f[q]->origin[d] - ((q == 1 && d == 0 && !literal) ? 1 : 0));
+            dom[d] = std::max<int64_t>(dom[d], 0);
+        }
+    }
+    const size_t need = gtb_vadv_workspace_bytes(u_stage->dtype, prec, dom);
+    if (need > kNoAllocScratchBytes)
+        return fail(GTB_ERR_UNSUPPORTED,
+                    "gtb_vadv_noalloc: domain %lldx%lldx%lld needs %zu bytes of scratch, above the fixed %zu-byte "
+                    "array; use gtb_vadv with a caller workspace",
+                    (long long)dom[0], (long long)dom[1], (long long)dom[2], need, kNoAllocScratchBytes);
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    // the workspace contents are never read before being written: nothing to clear
+    return gtb_vadv(u_stage, wcon, u_pos, utens, utens_stage, utens_stage_out, dtr_stage, beta_v, prec, flags,
+                    dom, scratch, kNoAllocScratchBytes, stream);
+}
