@@ -56,8 +56,10 @@ def _load():
                                            dp, dp, dp, dp]
         lib.oracle_thomas.argtypes = [dp, dp, dp, dp, i64, dp, dp, dp]
         lib.oracle_thomas_ld.argtypes = [dp, dp, dp, dp, i64, dp]
+        lib.oracle_hdiff_adj.argtypes = [P, P, P, P, P, i64, i64, i64]
+        lib.oracle_vadv_adj.argtypes = [P, P, P, P, P, P, i64, i64, i64, dbl, dbl, ctypes.c_int]
         for f in (lib.oracle_hdiff, lib.oracle_vadv, lib.oracle_vadv_system, lib.oracle_thomas,
-                  lib.oracle_thomas_ld):
+                  lib.oracle_thomas_ld, lib.oracle_hdiff_adj, lib.oracle_vadv_adj):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -173,3 +175,45 @@ def thomas(a, b, c, d, *, extended=False):
     _load().oracle_thomas(*ptrs, K, x.ctypes.data_as(dp), piv.ctypes.data_as(dp),
                           cpr.ctypes.data_as(dp))
     return x, piv, cpr
+
+
+def hdiff_adj(inp, coeff, out_bar, *, origin=(2, 2, 0), domain=None, coeff_bar=None):
+    """Reverse-mode hdiff: returns in_bar (same storage shape as ``inp``, written on
+    the domain plus its 2-point ring, zero elsewhere); ``coeff_bar`` (optional,
+    shaped like ``coeff``) is accumulated.  All fields share ``origin``."""
+    inp, coeff, out_bar = _f64(inp), _f64(coeff), _f64(out_bar)
+    if domain is None:
+        nk, nj, ni = inp.shape
+        domain = (ni - 2 * origin[0], nj - 2 * origin[1], nk - 2 * origin[2])
+    in_bar = np.zeros_like(inp)
+    _check_extent("in", inp, origin, domain, (2, 2, 0), (2, 2, 0))
+    for name, a in (("coeff", coeff), ("out_bar", out_bar)):
+        _check_extent(name, a, origin, domain)
+    I, J, K = domain
+    fs = [_ofield(a, origin) for a in (inp, coeff, out_bar, in_bar)]
+    cb = None if coeff_bar is None else ctypes.byref(_ofield(_f64(coeff_bar), origin))
+    if _load().oracle_hdiff_adj(*[ctypes.byref(f) for f in fs], cb, I, J, K) != 0:
+        raise MemoryError("oracle_hdiff_adj")
+    return in_bar
+
+
+def vadv_adj(wcon, y_bar, *, origin=(1, 1, 0), origin_wcon=None, domain=None, dtr_stage=3.0 / 20.0,
+             beta_v=0.0, wmode=0):
+    """Reverse-mode vadv: returns (u_stage_bar, u_pos_bar, utens_bar, utens_stage_bar),
+    shaped like ``y_bar``, written on the domain (wcon is held fixed)."""
+    wcon, y_bar = _f64(wcon), _f64(y_bar)
+    if domain is None:
+        nk, nj, ni = y_bar.shape
+        domain = (ni - 2 * origin[0], nj - 2 * origin[1], nk - 2 * origin[2])
+    origin_wcon = origin if origin_wcon is None else origin_wcon
+    _check_extent("wcon", wcon, origin_wcon, domain, (0, 0, 0), (1 if wmode == 0 else 0, 0, 0))
+    _check_extent("y_bar", y_bar, origin, domain)
+    outs = [np.zeros_like(y_bar) for _ in range(4)]
+    I, J, K = domain
+    fw = _ofield(wcon, origin_wcon)
+    fo = [_ofield(a, origin) for a in (y_bar, *outs)]
+    rc = _load().oracle_vadv_adj(ctypes.byref(fw), *[ctypes.byref(f) for f in fo], I, J, K, float(dtr_stage),
+                                 float(beta_v), int(wmode))
+    if rc != 0:
+        raise MemoryError("oracle_vadv_adj")
+    return tuple(outs)

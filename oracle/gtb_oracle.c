@@ -229,3 +229,179 @@ int oracle_vadv(const ofield *u_stage, const ofield *wcon, const ofield *u_pos,
     free(buf);
     return 0;
 }
+
+/* ------------------------------------------------------------------ adjoints
+ * Reverse-mode derivatives of the two stencils (the differentiation form of
+ * the hot path).  Both are written as the plain transpose of the forward
+ * steps above, in scatter form: walk the forward computation backwards and
+ * add each output cotangent into the cotangents of the values it was computed
+ * from.
+ *
+ * hdiff: out = in - coeff*D(in), D built from lap and the limited fluxes.  The
+ * limiter is piecewise: its keep/zero decision is frozen at the forward input
+ * (taken exactly as in oracle_hdiff), so on each piece the map is linear.
+ *   in_bar    (domain plus 2-point ring, overwritten): d<out_bar, out>/d in
+ *   coeff_bar (domain, accumulated when non-NULL): -D * out_bar
+ *
+ * vadv: y = dtr (x - u_pos), A x = d, d = dtr u_pos + utens + utens_stage
+ * + E u_stage with E the explicit correction operator; y is linear in
+ * (u_stage, u_pos, utens, utens_stage) for fixed wcon, so
+ *   dbar = A^-T (dtr y_bar)                 (transposed system, solved here by
+ *                                            Thomas elimination on A^T itself)
+ *   utens_bar = utens_stage_bar = dbar,  u_pos_bar = dtr (dbar - y_bar),
+ *   u_stage_bar = E^T dbar.
+ * wcon is not differentiated (it is held fixed).
+ */
+
+int oracle_hdiff_adj(const ofield *in, const ofield *coeff, const ofield *out_bar,
+                     ofield *in_bar, ofield *coeff_bar, int64_t I, int64_t J, int64_t K)
+{
+    int64_t LI = I + 2, LJ = J + 2;
+    double *lap = (double *)malloc(sizeof(double) * LI * LJ);
+    double *lapb = (double *)malloc(sizeof(double) * LI * LJ);
+    double *fx = (double *)malloc(sizeof(double) * (I + 1) * J);
+    double *fy = (double *)malloc(sizeof(double) * I * (J + 1));
+    char *kx = (char *)malloc((size_t)((I + 1) * J));      /* 1: flux kept */
+    char *ky = (char *)malloc((size_t)(I * (J + 1)));
+    if (!lap || !lapb || !fx || !fy || !kx || !ky) {
+        free(lap); free(lapb); free(fx); free(fy); free(kx); free(ky);
+        return -1;
+    }
+#define LAP(i, j) lap[((i) + 1) + ((j) + 1) * LI]
+#define LAPB(i, j) lapb[((i) + 1) + ((j) + 1) * LI]
+#define FX(i, j) fx[((i) + 1) + (j) * (I + 1)]
+#define FY(i, j) fy[(i) + ((j) + 1) * I]
+#define KX(i, j) kx[((i) + 1) + (j) * (I + 1)]
+#define KY(i, j) ky[(i) + ((j) + 1) * I]
+    for (int64_t k = 0; k < K; ++k) {
+        /* forward values of this level (same steps as oracle_hdiff) */
+        for (int64_t j = -1; j <= J; ++j)
+            for (int64_t i = -1; i <= I; ++i) {
+                double s = AT(in, i + 1, j, k) + AT(in, i - 1, j, k);
+                s = s + AT(in, i, j + 1, k);
+                s = s + AT(in, i, j - 1, k);
+                LAP(i, j) = 4.0 * AT(in, i, j, k) - s;
+            }
+        for (int64_t j = 0; j < J; ++j)
+            for (int64_t i = -1; i <= I - 1; ++i) {
+                double f = LAP(i + 1, j) - LAP(i, j);
+                double g = AT(in, i + 1, j, k) - AT(in, i, j, k);
+                KX(i, j) = (f * g > 0.0) ? 0 : 1;
+                FX(i, j) = KX(i, j) ? f : 0.0;
+            }
+        for (int64_t j = -1; j <= J - 1; ++j)
+            for (int64_t i = 0; i < I; ++i) {
+                double f = LAP(i, j + 1) - LAP(i, j);
+                double g = AT(in, i, j + 1, k) - AT(in, i, j, k);
+                KY(i, j) = (f * g > 0.0) ? 0 : 1;
+                FY(i, j) = KY(i, j) ? f : 0.0;
+            }
+        /* reverse pass */
+        for (int64_t j = -2; j < J + 2; ++j)
+            for (int64_t i = -2; i < I + 2; ++i) AT(in_bar, i, j, k) = 0.0;
+        for (int64_t n = 0; n < LI * LJ; ++n) lapb[n] = 0.0;
+        for (int64_t j = 0; j < J; ++j)
+            for (int64_t i = 0; i < I; ++i) {
+                double ob = AT(out_bar, i, j, k);
+                double div = (FX(i, j) - FX(i - 1, j)) + (FY(i, j) - FY(i, j - 1));
+                /* out = in - coeff * div */
+                AT(in_bar, i, j, k) += ob;
+                if (coeff_bar) AT(coeff_bar, i, j, k) += -div * ob;
+                double q = -AT(coeff, i, j, k) * ob;   /* cotangent of div */
+                /* div = fx(i) - fx(i-1) + fy(j) - fy(j-1); a limited flux passes nothing back */
+                if (KX(i, j))     { LAPB(i + 1, j) += q;  LAPB(i, j) -= q; }
+                if (KX(i - 1, j)) { LAPB(i, j) -= q;      LAPB(i - 1, j) += q; }
+                if (KY(i, j))     { LAPB(i, j + 1) += q;  LAPB(i, j) -= q; }
+                if (KY(i, j - 1)) { LAPB(i, j) -= q;      LAPB(i, j - 1) += q; }
+            }
+        for (int64_t j = -1; j <= J; ++j)
+            for (int64_t i = -1; i <= I; ++i) {
+                double lb = LAPB(i, j);
+                if (lb == 0.0) continue;
+                /* lap = 4 in(i,j) - in(i+1,j) - in(i-1,j) - in(i,j+1) - in(i,j-1) */
+                AT(in_bar, i, j, k) += 4.0 * lb;
+                AT(in_bar, i + 1, j, k) -= lb;
+                AT(in_bar, i - 1, j, k) -= lb;
+                AT(in_bar, i, j + 1, k) -= lb;
+                AT(in_bar, i, j - 1, k) -= lb;
+            }
+    }
+#undef LAP
+#undef LAPB
+#undef FX
+#undef FY
+#undef KX
+#undef KY
+    free(lap); free(lapb); free(fx); free(fy); free(kx); free(ky);
+    return 0;
+}
+
+/* Solve A^T z = r for the tridiagonal A = (a sub, b diag, c super): A^T has
+ * sub-diagonal c_{k-1}, diagonal b_k and super-diagonal a_{k+1}; eliminated
+ * top-down by the same Thomas recurrences as a forward solve. */
+static void thomas_transposed(const double *a, const double *b, const double *c, const double *r,
+                              int64_t K, double *cp, double *rp, double *z)
+{
+    for (int64_t k = 0; k < K; ++k) {
+        double sub = (k == 0) ? 0.0 : c[k - 1];
+        double sup = (k == K - 1) ? 0.0 : a[k + 1];
+        double p = (k == 0) ? b[0] : b[k] - sub * cp[k - 1];
+        double num = (k == 0) ? r[0] : r[k] - sub * rp[k - 1];
+        cp[k] = sup / p;
+        rp[k] = num / p;
+    }
+    z[K - 1] = rp[K - 1];
+    for (int64_t k = K - 2; k >= 0; --k) z[k] = rp[k] - cp[k] * z[k + 1];
+}
+
+int oracle_vadv_adj(const ofield *wcon, const ofield *y_bar, ofield *u_stage_bar, ofield *u_pos_bar,
+                    ofield *utens_bar, ofield *utens_stage_bar,
+                    int64_t I, int64_t J, int64_t K, double dtr, double beta, int wmode)
+{
+    if (K <= 0) return 0;
+    double *buf = (double *)malloc(sizeof(double) * K * 10);
+    if (!buf) return -1;
+    double *a = buf, *b = buf + K, *c = buf + 2 * K, *as = buf + 3 * K, *cs = buf + 4 * K;
+    double *r = buf + 5 * K, *cp = buf + 6 * K, *rp = buf + 7 * K, *z = buf + 8 * K;
+    double bp = 0.5 * (1.0 + beta), bm = 0.5 * (1.0 - beta);
+    for (int64_t j = 0; j < J; ++j)
+        for (int64_t i = 0; i < I; ++i) {
+            /* coefficients, exactly as oracle_vadv_system forms them */
+            for (int64_t k = 0; k < K; ++k) {
+                double ak = 0.0, ck = 0.0, ask = 0.0, csk = 0.0;
+                if (k >= 1) {
+                    double w = (wmode == 0) ? 0.5 * (AT(wcon, i, j, k) + AT(wcon, i + 1, j, k)) : AT(wcon, i, j, k);
+                    double g = -0.5 * w;
+                    ak = bp * g; ask = bm * g;
+                }
+                if (k <= K - 2) {
+                    double w = (wmode == 0) ? 0.5 * (AT(wcon, i, j, k + 1) + AT(wcon, i + 1, j, k + 1))
+                                            : AT(wcon, i, j, k + 1);
+                    double g = 0.5 * w;
+                    ck = bp * g; csk = bm * g;
+                }
+                a[k] = ak; c[k] = ck; as[k] = ask; cs[k] = csk;
+                b[k] = (dtr - ak) - ck;
+                r[k] = dtr * AT(y_bar, i, j, k);        /* x_bar = dtr y_bar */
+            }
+            thomas_transposed(a, b, c, r, K, cp, rp, z); /* z = d_bar */
+            for (int64_t k = 0; k < K; ++k) {
+                double yb = AT(y_bar, i, j, k);
+                if (utens_bar) AT(utens_bar, i, j, k) = z[k];
+                if (utens_stage_bar) AT(utens_stage_bar, i, j, k) = z[k];
+                /* d_k = dtr u_pos_k + ... ; y_k = dtr x_k - dtr u_pos_k */
+                if (u_pos_bar) AT(u_pos_bar, i, j, k) = dtr * z[k] - dtr * yb;
+                /* d_k -= as_k (us_{k-1} - us_k) + cs_k (us_{k+1} - us_k): transpose of E */
+                if (u_stage_bar) {
+                    double s = 0.0;
+                    if (k >= 1) s += as[k] * z[k];              /* from row k, +as_k us_k */
+                    if (k <= K - 2) s += cs[k] * z[k];          /* from row k, +cs_k us_k */
+                    if (k + 1 <= K - 1) s -= as[k + 1] * z[k + 1]; /* row k+1 reads us_k with -as_{k+1} */
+                    if (k - 1 >= 0) s -= cs[k - 1] * z[k - 1];     /* row k-1 reads us_k with -cs_{k-1} */
+                    AT(u_stage_bar, i, j, k) = s;
+                }
+            }
+        }
+    free(buf);
+    return 0;
+}
