@@ -74,8 +74,9 @@ typedef enum {
     GTB_PREC_DF = 2      /* double-float (pairs of binary32, ~48-bit) on the FP32 pipe */
 } gtb_prec;
 
-/* vadv flags */
-#define GTB_WCON_LITERAL 1u  /* use wcon(i) as the face velocity instead of the I-face average */
+/* flags */
+#define GTB_WCON_LITERAL 1u   /* vadv: use wcon(i) as the face velocity instead of the I-face average */
+#define GTB_ADJ_ACCUMULATE 2u /* adjoints: add into the cotangent outputs instead of overwriting them */
 
 /*
  * gtb_hdiff -- horizontal diffusion (paper Sec. 3.1; one PARALLEL computation,
@@ -136,6 +137,56 @@ int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u
  * K*I*J*8 for GTB_F64 storage, K*I*J*4 for GTB_F32 with GTB_PREC_NATIVE,
  * K*I*J*16 for GTB_F32 with GTB_PREC_F64 or GTB_PREC_DF; 0 for bad arguments. */
 size_t gtb_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain);
+
+/*
+ * gtb_hdiff_adj -- reverse mode of gtb_hdiff (the differentiation form of the
+ * paper's horizontal-diffusion benchmark, Sec. 3.1): a transposed stencil
+ * whose limiter keep/zero decisions are recomputed from `in` (the map is
+ * linear on each piece of the limiter).  Given out_bar on the domain:
+ *   in_bar    = out_bar - (dD/din)^T (coeff * out_bar)   written on the domain
+ *               plus its 2-point ring in I and J (overwritten; needs origin >= 2)
+ *   coeff_bar = -D * out_bar on the domain (optional, NULL to skip; added to
+ *               the existing values with GTB_ADJ_ACCUMULATE, else overwritten)
+ * D is the forward flux divergence.  in_bar and coeff_bar may not overlap any
+ * input or each other (GTB_ERR_ALIAS).  Limit: K <= 65535.
+ */
+int gtb_hdiff_adj(const gtb_field *in, const gtb_field *coeff, const gtb_field *out_bar,
+                  const gtb_field *in_bar, const gtb_field *coeff_bar, unsigned flags,
+                  const int64_t *domain, void *stream);
+
+/*
+ * gtb_vadv_adj -- reverse mode of gtb_vadv for fixed wcon (the transposed
+ * tridiagonal solve of the paper's implicit vertical solver, Sec. 3.1, run as
+ * a forward sweep with U^T and a backward sweep with L^T of A = LU).  The
+ * output utens_stage_out is linear in (u_stage, u_pos, utens, utens_stage):
+ *   z = A^-T (dtr_stage * y_bar),
+ *   utens_bar = utens_stage_bar = z,  u_pos_bar = dtr_stage (z - y_bar),
+ *   u_stage_bar = E^T z  (E: the explicit correction of the right-hand side).
+ * Every output is optional (NULL); outputs are overwritten, or added to with
+ * GTB_ADJ_ACCUMULATE.  u_stage_bar and u_pos_bar may be the very same view:
+ * it then receives their sum (the cotangent of a field passed as both
+ * u_stage and u_pos).  No other output may overlap an input or another output.
+ * flags: GTB_WCON_LITERAL, GTB_ADJ_ACCUMULATE.  workspace: as for gtb_vadv, of
+ * gtb_vadv_adj_workspace_bytes() bytes.  Limit: K <= 448.
+ */
+int gtb_vadv_adj(const gtb_field *wcon, const gtb_field *y_bar, const gtb_field *u_stage_bar,
+                 const gtb_field *u_pos_bar, const gtb_field *utens_bar, const gtb_field *utens_stage_bar,
+                 double dtr_stage, double beta_v, int prec, unsigned flags, const int64_t *domain,
+                 void *workspace, size_t workspace_bytes, void *stream);
+
+/* Workspace bytes of gtb_vadv_adj: 2*K*I*J times 8 (GTB_F64, or GTB_F32 with
+ * GTB_PREC_F64 / GTB_PREC_DF) or 4 (GTB_F32, GTB_PREC_NATIVE). */
+size_t gtb_vadv_adj_workspace_bytes(int dtype, int prec, const int64_t *domain);
+
+/*
+ * gtb_halo_periodic -- fill the hi-wide I halo and hj-wide J halo around the
+ * domain with the periodic continuation of the domain (corners included), the
+ * boundary condition of chained steps.  hi <= I and hj <= J.
+ * gtb_halo_periodic_adj -- its adjoint: every domain point adds the values
+ * held by the halo points that copy it; the halo itself is left unchanged.
+ */
+int gtb_halo_periodic(const gtb_field *f, int hi, int hj, const int64_t *domain, void *stream);
+int gtb_halo_periodic_adj(const gtb_field *f, int hi, int hj, const int64_t *domain, void *stream);
 
 /*
  * gtb_vadv_noalloc -- gtb_vadv for callers that cannot allocate device memory.

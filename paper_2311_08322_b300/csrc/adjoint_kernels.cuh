@@ -1,0 +1,325 @@
+// adjoint_kernels.cuh -- reverse-mode hdiff and vadv (the differentiation form
+// of the GT4Py paper's two benchmark stencils, Sec. 3.1), and the periodic
+// halo refresh used between chained steps together with its adjoint.
+//
+// vadv_adj: y = dtr (x - u_pos), A x = d, d = dtr u_pos + utens + utens_stage
+// + E u_stage.  With A = L U (Thomas: U = (p_k, c_k), l_k = a_k / p_{k-1}) the
+// transposed system A^T z = dtr y_bar is U^T v = dtr y_bar (forward sweep,
+// v_k = (x_k + a_k v_{k-1}) / p_k since c_{k-1} = -a_k) then L^T z = v
+// (backward sweep, z_k = v_k + c'_k z_{k+1} since l_{k+1} = -c'_k): the same
+// two sweeps as the forward solve, run on the transposed factors.  Then
+//   utens_bar = utens_stage_bar = z,  u_pos_bar = dtr (z - y_bar),
+//   u_stage_bar_m = as_m (z_{m-1} + z_m) - as_{m+1} (z_m + z_{m+1})
+// (E^T z with cs_{m-1} = -as_m; as_0 = as_K = 0).
+//
+// hdiff_adj (gather form, one output point of in_bar per thread item, over
+// the domain plus its 2-point ring): with q = coeff * out_bar on the domain
+// (0 elsewhere) and the limiter's keep/zero decision recomputed from in,
+//   gx(face) = keep * (q(i) - q(i+1)),  gy likewise,
+//   lb(cell) = gx(i-1) - gx(i) + gy(j-1) - gy(j),
+//   in_bar   = [domain] out_bar - (4 lb - lb(i+1) - lb(i-1) - lb(j+1) - lb(j-1)),
+//   coeff_bar = -D * out_bar with D the forward flux divergence.
+#pragma once
+
+#include "vadv_kernels.cuh"
+
+namespace gtb {
+
+// ------------------------------------------------------------------ vadv adjoint
+struct VadvAdjOut {
+    int64_t sj, sk;
+};
+
+template <typename T, typename N, int BJ, bool WS>
+__global__ void __launch_bounds__(32 * BJ)
+    vadv_adj_kernel(const View<const T> wc, const View<const T> yb, const View<T> usb, const View<T> upb,
+                    const View<T> utb, const View<T> utsb, const VadvGeom g, const int accumulate,
+                    const int merge_us_up, N *__restrict__ ws) {
+    constexpr int NT = 32 * BJ;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+    const int i = blockIdx.x * 32 + tx, j = blockIdx.y * BJ + ty;
+    const bool active = (i < g.I) && (j < g.J);
+    const int ic = min(i, g.I - 1), jc = min(j, g.J - 1);
+    const int iw = min(i, g.I);
+    const int K = g.K;
+
+    N *cpb, *vb;
+    size_t cstride, cidx;
+    if (WS) {
+        cstride = (size_t)g.I * g.J;
+        cidx = (size_t)jc * g.I + ic;
+        cpb = ws;
+        vb = ws + (size_t)K * cstride;
+    } else {
+        cstride = NT;
+        cidx = t;
+        cpb = reinterpret_cast<N *>(smem_raw);
+        vb = cpb + (size_t)K * NT;
+    }
+    const bool wr = WS ? active : true;
+
+    const T *pw = wc.p + iw + (int64_t)jc * wc.sj;
+    const T *pw1 = wc.p + min(i + 1, g.I) + (int64_t)jc * wc.sj;
+    const T *py = yb.p + ic + (int64_t)jc * yb.sj;
+    const bool last_lane = (tx == 31);
+    const bool lit = g.literal != 0;
+
+    const N dtr = num_const<N>(g.dtr);
+    const N ka = num_const<N>(g.ka);
+    const N kas = num_const<N>(g.kas);
+    const N zero = num_const<N>(0.0);
+    const int kexp = g.ka_pow2;
+
+    // face-velocity sum of level m (warp-uniform call)
+    auto face = [&](int m) -> N {
+        const T lo = pw[(int64_t)m * wc.sk];
+        if (lit) return to_num<N, T>(lo);
+        T hi = __shfl_down_sync(0xffffffffu, lo, 1);
+        if (last_lane) hi = pw1[(int64_t)m * wc.sk];
+        return to_num<N, T>(lo) + to_num<N, T>(hi);
+    };
+
+    // forward sweep: the pivots of A, c'_k, and v (U^T v = dtr y_bar)
+    N a_cur = zero, cp_prev = zero, v_prev = zero;
+    T ynext = py[0];
+    for (int k = 0; k < K; ++k) {
+        const T yk = ynext;
+        if (k + 1 < K) ynext = py[(int64_t)(k + 1) * yb.sk];
+        N a_next = zero;
+        if (k + 1 < K) a_next = coef<N>(face(k + 1), ka, kexp);
+        const N b = (dtr - a_cur) + a_next;
+        const N p = (k > 0) ? b - a_cur * cp_prev : b;
+        const N r = recip(p);
+        const N x = dtr * to_num<N, T>(yk);
+        const N v = (k > 0) ? (x + a_cur * v_prev) * r : x * r;
+        const N cpk = (-a_next) * r;
+        if (wr) {
+            cpb[(size_t)k * cstride + cidx] = cpk;
+            vb[(size_t)k * cstride + cidx] = v;
+        }
+        cp_prev = cpk, v_prev = v;
+        a_cur = a_next;
+    }
+
+    // backward sweep: z = L^-T v, outputs; u_stage_bar of level m is emitted once z_{m-1} is known
+    auto store = [&](const View<T> &o, int k, N val) {
+        if (!o.p || !active) return;
+        T *q = o.p + ic + (int64_t)jc * o.sj + (int64_t)k * o.sk;
+        *q = accumulate ? to_store<T, N>(to_num<N, T>(*q) + val) : to_store<T, N>(val);
+    };
+    N z1 = zero, z2 = zero;  // z_{k+1}, z_{k+2}
+    N as1 = zero, as2 = zero;  // as_{k+1}, as_{k+2} (as_K = 0)
+    for (int k = K - 1; k >= 0; --k) {
+        const N vk = vb[(size_t)k * cstride + cidx];
+        const N z = (k == K - 1) ? vk : vk + cpb[(size_t)k * cstride + cidx] * z1;
+        N ask = zero;
+        if (k > 0) {
+            const N s = face(k);
+            ask = g.sym ? coef<N>(s, ka, kexp) : kas * s;
+        }
+        const N yk = to_num<N, T>(py[(int64_t)k * yb.sk]);
+        store(utb, k, z);
+        store(utsb, k, z);
+        const N upbar = dtr * (z - yk);
+        if (!merge_us_up) store(upb, k, upbar);
+        if (k + 1 < K) {  // u_stage_bar of level k+1
+            const N usb1 = as1 * (z + z1) - as2 * (z1 + z2);
+            if (merge_us_up) {
+                // u_stage_bar and u_pos_bar are one field: level k+1 gets both (u_pos part stored earlier)
+                store(usb, k + 1, usb1 + dtr * (z1 - to_num<N, T>(py[(int64_t)(k + 1) * yb.sk])));
+            } else {
+                store(usb, k + 1, usb1);
+            }
+        }
+        z2 = z1, z1 = z;
+        as2 = as1, as1 = ask;
+    }
+    {  // level 0: as_0 = 0
+        const N usb0 = -as2 * (z1 + z2);
+        if (merge_us_up)
+            store(usb, 0, usb0 + dtr * (z1 - to_num<N, T>(py[0])));
+        else
+            store(usb, 0, usb0);
+    }
+}
+
+// ------------------------------------------------------------------ hdiff adjoint
+template <typename T, int TI, int TJ>
+struct HadjTile {
+    // regions (tile-relative offsets of their first element)
+    static constexpr int IX = TI + 6, IY = TJ + 6;  // in: tile +- 3
+    static constexpr int QX = TI + 4, QY = TJ + 4;  // q, lap: tile +- 2
+    static constexpr int GXX = TI + 3, GXY = TJ + 2; // x-faces: i in [-2, TI], rows tile +- 1
+    static constexpr int GYX = TI + 2, GYY = TJ + 3; // y-faces: cols tile +- 1, j in [-2, TJ]
+    static constexpr int LX = TI + 2, LY = TJ + 2;  // lb: tile +- 1
+    static constexpr int FXX = TI + 1, FYY = TJ + 1; // forward fluxes for coeff_bar
+    static constexpr int elems = IX * IY + 2 * QX * QY + GXX * GXY + GYX * GYY + LX * LY + FXX * TJ + TI * FYY;
+};
+
+template <typename T, int TI, int TJ>
+constexpr int hdiff_adj_smem_bytes() {
+    return HadjTile<T, TI, TJ>::elems * (int)sizeof(T) + 64;
+}
+
+struct HadjGeom {
+    int I, J, K;
+    int tiles_i, tiles_j;  // over the extended region [-2, I+2) x [-2, J+2)
+    int accumulate_coeff_bar;
+};
+
+template <typename T, int TI, int TJ, int NT>
+__global__ void __launch_bounds__(NT)
+    hdiff_adj_kernel(const View<const T> in, const View<const T> coeff, const View<const T> ob, const View<T> ib,
+                     const View<T> cb, const HadjGeom g) {
+    using H = HadjTile<T, TI, TJ>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *S_in = reinterpret_cast<T *>(smem_raw);  // in at (i, j) = tile (-3..TI+2, -3..TJ+2)
+    T *S_q = S_in + H::IX * H::IY;              // q at tile (-2..TI+1, -2..TJ+1)
+    T *S_lap = S_q + H::QX * H::QY;             // forward lap, same region as q
+    T *S_gx = S_lap + H::QX * H::QY;            // x-face cotangents, faces i in [-2, TI], rows [-1, TJ]
+    T *S_gy = S_gx + H::GXX * H::GXY;           // y-face cotangents, cols [-1, TI], faces j in [-2, TJ]
+    T *S_lb = S_gy + H::GYX * H::GYY;           // lap cotangents, tile +- 1
+    T *S_fx = S_lb + H::LX * H::LY;             // forward x-fluxes, faces [-1, TI-1], rows [0, TJ)
+    T *S_fy = S_fx + H::FXX * TJ;               // forward y-fluxes, cols [0, TI), faces [-1, TJ-1]
+
+    const int tid = threadIdx.x;
+    const int ti0 = (blockIdx.x % g.tiles_i) * TI - 2;  // domain-relative i of tile column 0
+    const int tj0 = (blockIdx.x / g.tiles_i) * TJ - 2;
+    const int k = blockIdx.y;
+    const int I = g.I, J = g.J;
+    auto in_dom = [&](int a, int b) { return a >= 0 && a < I && b >= 0 && b < J; };
+
+    // in (valid on the domain plus 2), q = coeff * out_bar (domain only)
+    for (int idx = tid; idx < H::IX * H::IY; idx += NT) {
+        const int a = ti0 - 3 + idx % H::IX, b = tj0 - 3 + idx / H::IX;
+        T v = T(0);
+        if (a >= -2 && a < I + 2 && b >= -2 && b < J + 2) v = in.p[a + (int64_t)b * in.sj + (int64_t)k * in.sk];
+        S_in[idx] = v;
+    }
+    for (int idx = tid; idx < H::QX * H::QY; idx += NT) {
+        const int a = ti0 - 2 + idx % H::QX, b = tj0 - 2 + idx / H::QX;
+        T v = T(0);
+        if (in_dom(a, b))
+            v = coeff.p[a + (int64_t)b * coeff.sj + (int64_t)k * coeff.sk] * ob.p[a + (int64_t)b * ob.sj + (int64_t)k * ob.sk];
+        S_q[idx] = v;
+    }
+    __syncthreads();
+    auto IN = [&](int a, int b) -> T { return S_in[(a + 3) + (b + 3) * H::IX]; };   // tile-relative
+    // forward Laplacian on tile +- 2 (needed only where -1 <= cell <= I, J)
+    for (int idx = tid; idx < H::QX * H::QY; idx += NT) {
+        const int a = idx % H::QX - 2, b = idx / H::QX - 2;
+        const T sum = ((IN(a + 1, b) + IN(a - 1, b)) + IN(a, b + 1)) + IN(a, b - 1);
+        S_lap[idx] = T(4) * IN(a, b) - sum;
+    }
+    __syncthreads();
+    auto LAP = [&](int a, int b) -> T { return S_lap[(a + 2) + (b + 2) * H::QX]; };
+    auto Q = [&](int a, int b) -> T { return S_q[(a + 2) + (b + 2) * H::QX]; };
+    // face cotangents (a face exists for domain-relative i in [-1, I-1], j in [0, J))
+    for (int idx = tid; idx < H::GXX * H::GXY; idx += NT) {
+        const int a = idx % H::GXX - 2, b = idx / H::GXX - 1;  // face between cells a and a+1, row b
+        const int da = ti0 + a, db = tj0 + b;
+        T v = T(0);
+        if (da >= -1 && da <= I - 1 && db >= 0 && db < J) {
+            const T f = LAP(a + 1, b) - LAP(a, b);
+            if (!(f * (IN(a + 1, b) - IN(a, b)) > T(0))) v = Q(a, b) - Q(a + 1, b);
+        }
+        S_gx[idx] = v;
+    }
+    for (int idx = tid; idx < H::GYX * H::GYY; idx += NT) {
+        const int a = idx % H::GYX - 1, b = idx / H::GYX - 2;  // face between rows b and b+1, column a
+        const int da = ti0 + a, db = tj0 + b;
+        T v = T(0);
+        if (da >= 0 && da < I && db >= -1 && db <= J - 1) {
+            const T f = LAP(a, b + 1) - LAP(a, b);
+            if (!(f * (IN(a, b + 1) - IN(a, b)) > T(0))) v = Q(a, b) - Q(a, b + 1);
+        }
+        S_gy[idx] = v;
+    }
+    // forward fluxes around the tile's domain cells (for coeff_bar)
+    if (cb.p) {
+        for (int idx = tid; idx < H::FXX * TJ; idx += NT) {
+            const int a = idx % H::FXX - 1, b = idx / H::FXX;
+            const int da = ti0 + a, db = tj0 + b;
+            T v = T(0);
+            if (da >= -1 && da <= I - 1 && db >= 0 && db < J) {
+                const T f = LAP(a + 1, b) - LAP(a, b);
+                v = (f * (IN(a + 1, b) - IN(a, b)) > T(0)) ? T(0) : f;
+            }
+            S_fx[idx] = v;
+        }
+        for (int idx = tid; idx < TI * H::FYY; idx += NT) {
+            const int a = idx % TI, b = idx / TI - 1;
+            const int da = ti0 + a, db = tj0 + b;
+            T v = T(0);
+            if (da >= 0 && da < I && db >= -1 && db <= J - 1) {
+                const T f = LAP(a, b + 1) - LAP(a, b);
+                v = (f * (IN(a, b + 1) - IN(a, b)) > T(0)) ? T(0) : f;
+            }
+            S_fy[idx] = v;
+        }
+    }
+    __syncthreads();
+    auto GX = [&](int a, int b) -> T { return S_gx[(a + 2) + (b + 1) * H::GXX]; };
+    auto GY = [&](int a, int b) -> T { return S_gy[(a + 1) + (b + 2) * H::GYX]; };
+    for (int idx = tid; idx < H::LX * H::LY; idx += NT) {
+        const int a = idx % H::LX - 1, b = idx / H::LX - 1;
+        S_lb[idx] = (GX(a - 1, b) - GX(a, b)) + (GY(a, b - 1) - GY(a, b));
+    }
+    __syncthreads();
+    auto LB = [&](int a, int b) -> T { return S_lb[(a + 1) + (b + 1) * H::LX]; };
+    for (int idx = tid; idx < TI * TJ; idx += NT) {
+        const int a = idx % TI, b = idx / TI;
+        const int da = ti0 + a, db = tj0 + b;
+        if (da < -2 || da >= I + 2 || db < -2 || db >= J + 2) continue;
+        const T tr = T(4) * LB(a, b) - (((LB(a + 1, b) + LB(a - 1, b)) + LB(a, b + 1)) + LB(a, b - 1));
+        const bool dom = in_dom(da, db);
+        const int64_t off_ob = da + (int64_t)db * ob.sj + (int64_t)k * ob.sk;
+        const T o = dom ? ob.p[off_ob] : T(0);
+        ib.p[da + (int64_t)db * ib.sj + (int64_t)k * ib.sk] = o - tr;
+        if (cb.p && dom) {
+            const T D = (S_fx[(a + 1) + b * H::FXX] - S_fx[a + b * H::FXX]) + (S_fy[a + (b + 1) * TI] - S_fy[a + b * TI]);
+            T *c = cb.p + da + (int64_t)db * cb.sj + (int64_t)k * cb.sk;
+            *c = g.accumulate_coeff_bar ? *c - D * o : -D * o;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ periodic halo
+// Fill the hi-wide I halo and hj-wide J halo around the domain with the
+// periodic continuation of the domain (corners included).
+template <typename T>
+__global__ void halo_periodic_kernel(const View<T> f, int I, int J, int K, int hi, int hj) {
+    const int W = I + 2 * hi, H = J + 2 * hj;
+    const int64_t n = (int64_t)W * H * K;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(idx % W) - hi, b = (int)((idx / W) % H) - hj, k = (int)(idx / ((int64_t)W * H));
+        if (a >= 0 && a < I && b >= 0 && b < J) continue;
+        const int sa = (a + I) % I, sb = (b + J) % J;
+        f.p[a + (int64_t)b * f.sj + (int64_t)k * f.sk] = f.p[sa + (int64_t)sb * f.sj + (int64_t)k * f.sk];
+    }
+}
+
+// Adjoint of the refresh: every domain point gathers the cotangents of the halo
+// points that copied it (halo widths <= I, J, so each halo point maps to one
+// domain point); the halo itself is left unchanged.
+template <typename T>
+__global__ void halo_periodic_adj_kernel(const View<T> f, int I, int J, int K, int hi, int hj) {
+    const int64_t n = (int64_t)I * J * K;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(idx % I), b = (int)((idx / I) % J), k = (int)(idx / ((int64_t)I * J));
+        T acc = T(0);
+#pragma unroll
+        for (int sa = -1; sa <= 1; ++sa)
+#pragma unroll
+            for (int sb = -1; sb <= 1; ++sb) {
+                if (sa == 0 && sb == 0) continue;
+                const int x = a + sa * I, y = b + sb * J;
+                if (x >= -hi && x < I + hi && y >= -hj && y < J + hj && !(x >= 0 && x < I && y >= 0 && y < J))
+                    acc += f.p[x + (int64_t)y * f.sj + (int64_t)k * f.sk];
+            }
+        f.p[a + (int64_t)b * f.sj + (int64_t)k * f.sk] += acc;
+    }
+}
+
+}  // namespace gtb

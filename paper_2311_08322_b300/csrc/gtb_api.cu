@@ -18,6 +18,7 @@
 #include "hdiff_kernels.cuh"
 #include "hdiff_rs.cuh"
 #include "vadv_kernels.cuh"
+#include "adjoint_kernels.cuh"
 
 namespace gtb {
 
@@ -301,6 +302,74 @@ static size_t vadv_ws_bytes_for(int dt, int prec, const int64_t dom[3]) {
     return vadv_ws_bytes<float, float>(dom);
 }
 
+// ------------------------------------------------------------------ adjoints
+template <typename T, typename N, int BJ, bool WS>
+static int launch_vadv_adj_t(const gtb_field *const f[6], const VadvGeom &g, int accumulate, int merge, void *ws,
+                             cudaStream_t st) {
+    auto kern = vadv_adj_kernel<T, N, BJ, WS>;
+    const int smem = WS ? 0 : (int)(2 * sizeof(N) * g.K * 32 * BJ);
+    if (!WS && prepare_kernel(kern, 227 * 1024) != cudaSuccess)
+        return launch_status("vadv_adj: shared-memory attribute");
+    auto ov = [&](const gtb_field *x) { return x ? view_of<T>(x) : View<T>{nullptr, 0, 0}; };
+    dim3 block(32, BJ), grid((g.I + 31) / 32, (g.J + BJ - 1) / BJ);
+    kern<<<grid, block, smem, st>>>(view_of<const T>(f[0]), view_of<const T>(f[1]), ov(f[2]), ov(f[3]), ov(f[4]),
+                                    ov(f[5]), g, accumulate, merge, static_cast<N *>(ws));
+    return launch_status("vadv_adj launch");
+}
+
+template <typename T, typename N>
+static size_t vadv_adj_ws_bytes(const int64_t dom[3]) {
+    return 2 * sizeof(N) * (size_t)dom[0] * (size_t)dom[1] * (size_t)dom[2];
+}
+
+template <typename T, typename N>
+static int run_vadv_adj_n(const gtb_field *const f[6], const VadvGeom &g, int accumulate, int merge, void *ws,
+                          size_t ws_bytes, cudaStream_t st) {
+    const int64_t dom[3] = {g.I, g.J, g.K};
+    if (ws && ws_bytes >= vadv_adj_ws_bytes<T, N>(dom)) return launch_vadv_adj_t<T, N, 2, true>(f, g, accumulate, merge, ws, st);
+    const size_t per_col = 2 * sizeof(N) * (size_t)g.K;
+    if (per_col * 64 <= 48 * 1024) return launch_vadv_adj_t<T, N, 2, false>(f, g, accumulate, merge, nullptr, st);
+    return launch_vadv_adj_t<T, N, 1, false>(f, g, accumulate, merge, nullptr, st);
+}
+
+static size_t vadv_adj_ws_bytes_for(int dt, int prec, const int64_t dom[3]) {
+    if (dt == GTB_F64) return vadv_adj_ws_bytes<double, double>(dom);
+    if (prec == GTB_PREC_F64) return vadv_adj_ws_bytes<float, double>(dom);
+    if (prec == GTB_PREC_DF) return vadv_adj_ws_bytes<float, df>(dom);
+    return vadv_adj_ws_bytes<float, float>(dom);
+}
+
+template <typename T>
+static int run_hdiff_adj(const gtb_field *fin, const gtb_field *fcf, const gtb_field *fob, const gtb_field *fib,
+                         const gtb_field *fcb, int accumulate, const int64_t dom[3], cudaStream_t st) {
+    constexpr int TI = 64, TJ = 16, NT = 256;
+    auto kern = hdiff_adj_kernel<T, TI, TJ, NT>;
+    constexpr int smem = hdiff_adj_smem_bytes<T, TI, TJ>();
+    if (prepare_kernel(kern, smem) != cudaSuccess) return launch_status("hdiff_adj: shared-memory attribute");
+    HadjGeom g{};
+    g.I = (int)dom[0], g.J = (int)dom[1], g.K = (int)dom[2];
+    g.tiles_i = (g.I + 4 + TI - 1) / TI;
+    g.tiles_j = (g.J + 4 + TJ - 1) / TJ;
+    g.accumulate_coeff_bar = accumulate;
+    dim3 grid(g.tiles_i * g.tiles_j, g.K);
+    kern<<<grid, NT, smem, st>>>(view_of<const T>(fin), view_of<const T>(fcf), view_of<const T>(fob), view_of<T>(fib),
+                                 fcb ? view_of<T>(fcb) : View<T>{nullptr, 0, 0}, g);
+    return launch_status("hdiff_adj launch");
+}
+
+template <typename T>
+static int run_halo(const gtb_field *f, int hi, int hj, const int64_t dom[3], bool adjoint, cudaStream_t st) {
+    const View<T> v = view_of<T>(f);
+    const int64_t n = adjoint ? dom[0] * dom[1] * dom[2] : (dom[0] + 2 * hi) * (dom[1] + 2 * hj) * dom[2];
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)sm_count() * 16);
+    if (adjoint)
+        halo_periodic_adj_kernel<T><<<blocks, threads, 0, st>>>(v, (int)dom[0], (int)dom[1], (int)dom[2], hi, hj);
+    else
+        halo_periodic_kernel<T><<<blocks, threads, 0, st>>>(v, (int)dom[0], (int)dom[1], (int)dom[2], hi, hj);
+    return launch_status(adjoint ? "halo_periodic_adj launch" : "halo_periodic launch");
+}
+
 }  // namespace gtb
 
 // ====================================================================== C ABI
@@ -492,4 +561,149 @@ extern "C" int gtb_vadv_noalloc(const gtb_field *u_stage, const gtb_field *wcon,
     // the workspace contents are never read before being written: nothing to clear
     return gtb_vadv(u_stage, wcon, u_pos, utens, utens_stage, utens_stage_out, dtr_stage, beta_v, prec, flags,
                     dom, scratch, kNoAllocScratchBytes, stream);
+}
+
+// ====================================================================== adjoints and halos
+extern "C" int gtb_hdiff_adj(const gtb_field *in, const gtb_field *coeff, const gtb_field *out_bar,
+                             const gtb_field *in_bar, const gtb_field *coeff_bar, unsigned flags,
+                             const int64_t *domain, void *stream) {
+    if (!in || !coeff || !out_bar || !in_bar) return fail(GTB_ERR_NULL, "gtb_hdiff_adj: NULL field");
+    const int dt = in->dtype;
+    if (!dtype_size(dt)) return fail(GTB_ERR_DTYPE, "gtb_hdiff_adj: unknown dtype %d", dt);
+    int rc;
+    if ((rc = check_field("in", in, dt)) || (rc = check_field("coeff", coeff, dt)) ||
+        (rc = check_field("out_bar", out_bar, dt)) || (rc = check_field("in_bar", in_bar, dt)) ||
+        (coeff_bar && (rc = check_field("coeff_bar", coeff_bar, dt))))
+        return rc;
+    if (flags & ~GTB_ADJ_ACCUMULATE) return fail(GTB_ERR_ARG, "gtb_hdiff_adj: unknown flags 0x%x", flags);
+    const Reach r2{{2, 2, 0}, {2, 2, 0}}, r0{{0, 0, 0}, {0, 0, 0}};
+    int64_t dom[3] = {INT64_MAX, INT64_MAX, INT64_MAX};
+    if (!domain) {
+        shrink_domain(in, r2, dom);
+        shrink_domain(coeff, r0, dom);
+        shrink_domain(out_bar, r0, dom);
+        shrink_domain(in_bar, r2, dom);
+        if (coeff_bar) shrink_domain(coeff_bar, r0, dom);
+    }
+    if ((rc = resolve_domain(domain, dom))) return rc;
+    if ((rc = check_extent("in", in, r2, dom)) || (rc = check_extent("coeff", coeff, r0, dom)) ||
+        (rc = check_extent("out_bar", out_bar, r0, dom)) || (rc = check_extent("in_bar", in_bar, r2, dom)) ||
+        (coeff_bar && (rc = check_extent("coeff_bar", coeff_bar, r0, dom))))
+        return rc;
+    const gtb_field *ins[3] = {in, coeff, out_bar};
+    static const char *inames[3] = {"in", "coeff", "out_bar"};
+    for (int q = 0; q < 3; ++q) {
+        if (overlaps(in_bar, ins[q])) return fail(GTB_ERR_ALIAS, "gtb_hdiff_adj: in_bar overlaps %s", inames[q]);
+        if (coeff_bar && overlaps(coeff_bar, ins[q]))
+            return fail(GTB_ERR_ALIAS, "gtb_hdiff_adj: coeff_bar overlaps %s", inames[q]);
+    }
+    if (coeff_bar && overlaps(coeff_bar, in_bar)) return fail(GTB_ERR_ALIAS, "gtb_hdiff_adj: coeff_bar overlaps in_bar");
+    if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
+    if (dom[2] > 65535) return fail(GTB_ERR_UNSUPPORTED, "gtb_hdiff_adj: K above 65535");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int acc = (flags & GTB_ADJ_ACCUMULATE) ? 1 : 0;
+    return dt == GTB_F64 ? run_hdiff_adj<double>(in, coeff, out_bar, in_bar, coeff_bar, acc, dom, st)
+                         : run_hdiff_adj<float>(in, coeff, out_bar, in_bar, coeff_bar, acc, dom, st);
+}
+
+extern "C" size_t gtb_vadv_adj_workspace_bytes(int dtype, int prec, const int64_t *domain) {
+    if (!domain || !dtype_size(dtype) || prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return 0;
+    for (int d = 0; d < 3; ++d)
+        if (domain[d] < 0) return 0;
+    return vadv_adj_ws_bytes_for(dtype, dtype == GTB_F64 ? GTB_PREC_NATIVE : prec, domain);
+}
+
+extern "C" int gtb_vadv_adj(const gtb_field *wcon, const gtb_field *y_bar, const gtb_field *u_stage_bar,
+                            const gtb_field *u_pos_bar, const gtb_field *utens_bar, const gtb_field *utens_stage_bar,
+                            double dtr_stage, double beta_v, int prec, unsigned flags, const int64_t *domain,
+                            void *workspace, size_t workspace_bytes, void *stream) {
+    const gtb_field *f[6] = {wcon, y_bar, u_stage_bar, u_pos_bar, utens_bar, utens_stage_bar};
+    static const char *names[6] = {"wcon", "y_bar", "u_stage_bar", "u_pos_bar", "utens_bar", "utens_stage_bar"};
+    if (!wcon || !y_bar) return fail(GTB_ERR_NULL, "gtb_vadv_adj: NULL wcon or y_bar");
+    const int dt = y_bar->dtype;
+    if (!dtype_size(dt)) return fail(GTB_ERR_DTYPE, "gtb_vadv_adj: unknown dtype %d", dt);
+    int rc;
+    for (int q = 0; q < 6; ++q)
+        if (f[q] && (rc = check_field(names[q], f[q], dt))) return rc;
+    if (flags & ~(GTB_WCON_LITERAL | GTB_ADJ_ACCUMULATE)) return fail(GTB_ERR_ARG, "gtb_vadv_adj: unknown flags 0x%x", flags);
+    if (prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return fail(GTB_ERR_ARG, "gtb_vadv_adj: unknown prec %d", prec);
+    if (dt == GTB_F64 && prec != GTB_PREC_NATIVE)
+        return fail(GTB_ERR_ARG, "gtb_vadv_adj: FP64 storage computes in binary64 (prec must be GTB_PREC_NATIVE)");
+    if (!(dtr_stage == dtr_stage) || !(beta_v == beta_v)) return fail(GTB_ERR_ARG, "gtb_vadv_adj: NaN scalar");
+    const bool literal = flags & GTB_WCON_LITERAL;
+    const Reach r0{{0, 0, 0}, {0, 0, 0}}, rw{{0, 0, 0}, {literal ? 0 : 1, 0, 0}};
+    int64_t dom[3] = {INT64_MAX, INT64_MAX, INT64_MAX};
+    if (!domain)
+        for (int q = 0; q < 6; ++q)
+            if (f[q]) shrink_domain(f[q], q == 0 ? rw : r0, dom);
+    if ((rc = resolve_domain(domain, dom))) return rc;
+    for (int q = 0; q < 6; ++q)
+        if (f[q] && (rc = check_extent(names[q], f[q], q == 0 ? rw : r0, dom))) return rc;
+    const bool merge = u_stage_bar && u_pos_bar && same_view(u_stage_bar, u_pos_bar);
+    for (int q = 2; q < 6; ++q) {
+        if (!f[q]) continue;
+        for (int r = 0; r < 6; ++r) {
+            if (r == q || !f[r]) continue;
+            if (merge && ((q == 2 && r == 3) || (q == 3 && r == 2))) continue;
+            if (overlaps(f[q], f[r])) return fail(GTB_ERR_ALIAS, "gtb_vadv_adj: %s overlaps %s", names[q], names[r]);
+        }
+    }
+    if (dom[2] > kVadvMaxK)
+        return fail(GTB_ERR_UNSUPPORTED, "gtb_vadv_adj: K = %lld exceeds the limit %d", (long long)dom[2], kVadvMaxK);
+    if (workspace && reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
+        return fail(GTB_ERR_LAYOUT, "gtb_vadv_adj: workspace must be 16-byte aligned");
+    if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
+    VadvGeom g{};
+    g.I = (int)dom[0], g.J = (int)dom[1], g.K = (int)dom[2];
+    g.literal = literal ? 1 : 0;
+    const double bp = 0.5 * (1.0 + beta_v), bm = 0.5 * (1.0 - beta_v);
+    g.sym = (bp == bm) ? 1 : 0;
+    g.dtr = dtr_stage;
+    g.ka = (literal ? -0.5 : -0.25) * bp;
+    g.kas = (literal ? -0.5 : -0.25) * bm;
+    {
+        int n = 0;
+        const double m = std::frexp(-g.ka, &n);
+        g.ka_pow2 = (m == 0.5 && n - 1 < 0 && n - 1 > -64) ? n - 1 : 0;
+    }
+    const int acc = (flags & GTB_ADJ_ACCUMULATE) ? 1 : 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (dt == GTB_F64) return run_vadv_adj_n<double, double>(f, g, acc, merge, workspace, workspace_bytes, st);
+    if (prec == GTB_PREC_F64) return run_vadv_adj_n<float, double>(f, g, acc, merge, workspace, workspace_bytes, st);
+    if (prec == GTB_PREC_DF) return run_vadv_adj_n<float, df>(f, g, acc, merge, workspace, workspace_bytes, st);
+    return run_vadv_adj_n<float, float>(f, g, acc, merge, workspace, workspace_bytes, st);
+}
+
+static int halo_common(const char *fn, const gtb_field *f, int hi, int hj, const int64_t *domain, int64_t dom[3]) {
+    if (!f) return fail(GTB_ERR_NULL, "%s: NULL field", fn);
+    int rc;
+    if (!dtype_size(f->dtype)) return fail(GTB_ERR_DTYPE, "%s: unknown dtype %d", fn, f->dtype);
+    if ((rc = check_field("field", f, f->dtype))) return rc;
+    if (hi < 0 || hj < 0) return fail(GTB_ERR_ARG, "%s: negative halo width", fn);
+    const Reach r{{hi, hj, 0}, {hi, hj, 0}};
+    for (int d = 0; d < 3; ++d) dom[d] = INT64_MAX;
+    if (!domain) shrink_domain(f, r, dom);
+    if ((rc = resolve_domain(domain, dom))) return rc;
+    if ((rc = check_extent("field", f, r, dom))) return rc;
+    if ((dom[0] > 0 && hi > dom[0]) || (dom[1] > 0 && hj > dom[1]))
+        return fail(GTB_ERR_UNSUPPORTED, "%s: halo wider than the domain", fn);
+    return GTB_OK;
+}
+
+extern "C" int gtb_halo_periodic(const gtb_field *f, int hi, int hj, const int64_t *domain, void *stream) {
+    int64_t dom[3];
+    int rc = halo_common("gtb_halo_periodic", f, hi, hj, domain, dom);
+    if (rc) return rc;
+    if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return f->dtype == GTB_F64 ? run_halo<double>(f, hi, hj, dom, false, st) : run_halo<float>(f, hi, hj, dom, false, st);
+}
+
+extern "C" int gtb_halo_periodic_adj(const gtb_field *f, int hi, int hj, const int64_t *domain, void *stream) {
+    int64_t dom[3];
+    int rc = halo_common("gtb_halo_periodic_adj", f, hi, hj, domain, dom);
+    if (rc) return rc;
+    if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return f->dtype == GTB_F64 ? run_halo<double>(f, hi, hj, dom, true, st) : run_halo<float>(f, hi, hj, dom, true, st);
 }

@@ -42,8 +42,10 @@ class GtbError(RuntimeError):
 
 
 _lib = None
-EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_device_status", "gtb_last_error",
-           "gtb_version")
+EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_hdiff_adj", "gtb_vadv_adj",
+           "gtb_vadv_adj_workspace_bytes", "gtb_halo_periodic", "gtb_halo_periodic_adj", "gtb_device_status",
+           "gtb_last_error", "gtb_version")
+GTB_ADJ_ACCUMULATE = 2
 
 
 def lib() -> ctypes.CDLL:
@@ -60,6 +62,15 @@ def lib() -> ctypes.CDLL:
                                i64p, vp, ctypes.c_size_t, vp]
         L.gtb_vadv_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, i64p]
         L.gtb_vadv_workspace_bytes.restype = ctypes.c_size_t
+        L.gtb_hdiff_adj.argtypes = [P, P, P, P, P, ctypes.c_uint, i64p, vp]
+        L.gtb_vadv_adj.argtypes = [P, P, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_uint,
+                                   i64p, vp, ctypes.c_size_t, vp]
+        L.gtb_vadv_adj_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, i64p]
+        L.gtb_vadv_adj_workspace_bytes.restype = ctypes.c_size_t
+        L.gtb_halo_periodic.argtypes = [P, ctypes.c_int, ctypes.c_int, i64p, vp]
+        L.gtb_halo_periodic_adj.argtypes = [P, ctypes.c_int, ctypes.c_int, i64p, vp]
+        for n in ("gtb_hdiff_adj", "gtb_vadv_adj", "gtb_halo_periodic", "gtb_halo_periodic_adj"):
+            getattr(L, n).restype = ctypes.c_int
         L.gtb_device_status.argtypes = [vp]
         L.gtb_last_error.restype = ctypes.c_char_p
         L.gtb_version.restype = ctypes.c_char_p
@@ -223,6 +234,51 @@ def vadv(u_stage, wcon, u_pos, utens, utens_stage, out=None, *, dtr_stage=3.0 / 
                           PREC[prec] if isinstance(prec, str) else int(prec), GTB_WCON_LITERAL if literal else 0,
                           _dom(domain), ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes, _stream(stream)))
     return out
+
+
+def _ptr(x):
+    return None if x is None else ctypes.byref(_as_field(x))
+
+
+def hdiff_adj(in_, coeff, out_bar, in_bar, coeff_bar=None, *, accumulate=False, domain=None, stream=None):
+    """Reverse-mode hdiff (gtb_hdiff_adj): in_bar on the domain plus its 2-ring,
+    coeff_bar (optional) on the domain."""
+    _check(lib().gtb_hdiff_adj(_ptr(in_), _ptr(coeff), _ptr(out_bar), _ptr(in_bar), _ptr(coeff_bar),
+                               GTB_ADJ_ACCUMULATE if accumulate else 0, _dom(domain), _stream(stream)))
+    return in_bar
+
+
+def vadv_adj(wcon, y_bar, u_stage_bar=None, u_pos_bar=None, utens_bar=None, utens_stage_bar=None, *,
+             dtr_stage=3.0 / 20.0, beta_v=0.0, prec="native", literal=False, accumulate=False, domain=None,
+             workspace="auto", stream=None):
+    """Reverse-mode vadv for fixed wcon (gtb_vadv_adj).  Passing one storage as both
+    u_stage_bar and u_pos_bar stores their sum there."""
+    fw, fy = _as_field(wcon), _as_field(y_bar)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        if isinstance(workspace, str):
+            dom = tuple(domain) if domain is not None else tuple(fy.shape[d] - fy.origin[d] for d in range(3))
+            need = int(lib().gtb_vadv_adj_workspace_bytes(fy.dtype, PREC[prec], _dom(dom)))
+            workspace = globals()["workspace"](need, stream) if need else None
+        if workspace is not None:
+            ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    flags = (1 if literal else 0) | (GTB_ADJ_ACCUMULATE if accumulate else 0)
+    _check(lib().gtb_vadv_adj(ctypes.byref(fw), ctypes.byref(fy), _ptr(u_stage_bar), _ptr(u_pos_bar),
+                              _ptr(utens_bar), _ptr(utens_stage_bar), float(dtr_stage), float(beta_v), PREC[prec],
+                              flags, _dom(domain), ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes,
+                              _stream(stream)))
+
+
+def halo_periodic(f, hi=2, hj=2, *, domain=None, stream=None):
+    """Periodic refresh of the hi x hj halo around the domain (gtb_halo_periodic)."""
+    _check(lib().gtb_halo_periodic(_ptr(f), int(hi), int(hj), _dom(domain), _stream(stream)))
+    return f
+
+
+def halo_periodic_adj(f, hi=2, hj=2, *, domain=None, stream=None):
+    """Adjoint of the refresh: fold the halo's values into the domain (gtb_halo_periodic_adj)."""
+    _check(lib().gtb_halo_periodic_adj(_ptr(f), int(hi), int(hj), _dom(domain), _stream(stream)))
+    return f
 
 
 def device_status(stream=None):

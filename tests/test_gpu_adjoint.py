@@ -1,0 +1,214 @@
+"""GPU parity of the differentiation form: gtb_hdiff_adj, gtb_vadv_adj and the
+periodic halo pair against the oracle adjoints, and the 10-step chained
+torch.autograd gradient against (a) the oracle-side reference gradient (oracle
+forward + oracle adjoints + numpy's periodic padding) and (b) central finite
+differences on random directions."""
+import numpy as np
+import pytest
+
+from helpers import region, rel_err
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+F32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    from paper_2311_08322_b300 import build, gtb
+    assert torch.cuda.is_available()
+    build.build()
+    return gtb
+
+
+def rnd(shape, seed, lo=-1.0, hi=1.0):
+    return np.random.default_rng(seed).uniform(lo, hi, shape)
+
+
+# ------------------------------------------------------------------ hdiff_adj
+@pytest.mark.parametrize("I,J,K,dtype", [(256, 256, 80, np.float64), (67, 19, 5, np.float64), (1, 1, 1, np.float64),
+                                         (130, 40, 3, np.float32), (64, 16, 2, np.float32)])
+def test_hdiff_adj(G, orc, I, J, K, dtype):
+    o = (2, 2, 0)
+    shp = (K, J + 4, I + 4)
+    inp, coeff, ob = rnd(shp, 1), rnd(shp, 2, 0, 0.025), rnd(shp, 3)
+    inp, coeff, ob = (x.astype(dtype) for x in (inp, coeff, ob))
+    cb0 = rnd(shp, 4).astype(dtype)
+    s_in, s_cf, s_ob = (G.storage_from(x, o) for x in (inp, coeff, ob))
+    s_ib = G.storage_from(np.full(shp, np.nan, dtype), o)
+    s_cb = G.storage_from(cb0, o)
+    G.hdiff_adj(s_in, s_cf, s_ob, s_ib, s_cb, accumulate=True)
+    G.device_status()
+    ref_cb = cb0.astype(np.float64).copy()
+    ref_ib = orc.hdiff_adj(inp.astype(np.float64), coeff.astype(np.float64), ob.astype(np.float64), coeff_bar=ref_cb)
+    tol = F64_TOL if dtype == np.float64 else F32_TOL
+    ring = (slice(None), slice(0, J + 4), slice(0, I + 4))
+    assert rel_err(s_ib.numpy()[ring], ref_ib[ring]) <= tol
+    assert rel_err(region(s_cb.numpy(), o, (I, J, K)), region(ref_cb, o, (I, J, K))) <= tol
+
+
+def test_hdiff_adj_overwrite_and_closed_form(G, orc):
+    """Checkerboard: every flux limited, so in_bar = out_bar (0 on the ring) and coeff_bar = 0."""
+    I, J, K = 40, 24, 2
+    _, y, x = np.meshgrid(np.arange(K), np.arange(J + 4), np.arange(I + 4), indexing="ij")
+    inp = np.where((x + y) % 2 == 0, 1.0, -1.0)
+    ob = rnd(inp.shape, 5)
+    o = (2, 2, 0)
+    s_ib = G.storage_from(np.full(inp.shape, 7.0), o)
+    s_cb = G.storage_from(np.full(inp.shape, 7.0), o)
+    G.hdiff_adj(G.storage_from(inp, o), G.storage_from(rnd(inp.shape, 6, 0, 0.025), o), G.storage_from(ob, o), s_ib, s_cb)
+    expect = np.zeros_like(ob)
+    expect[:, 2:-2, 2:-2] = ob[:, 2:-2, 2:-2]
+    assert np.array_equal(s_ib.numpy(), expect)
+    assert np.all(region(s_cb.numpy(), o, (I, J, K)) == 0.0)
+
+
+# ------------------------------------------------------------------ vadv_adj
+@pytest.mark.parametrize("I,J,K,dtype,prec,workspace", [
+    (256, 256, 80, np.float64, "native", "auto"), (70, 9, 137, np.float64, "native", None),
+    (33, 7, 1, np.float64, "native", "auto"), (31, 5, 2, np.float64, "native", None),
+    (200, 64, 80, np.float32, "df", "auto"), (45, 7, 30, np.float32, "f64", None)])
+def test_vadv_adj(G, orc, I, J, K, dtype, prec, workspace):
+    o = (1, 1, 0)
+    shp = (K, J + 2, I + 2)
+    wamp = 0.5 if dtype == np.float64 else 0.3
+    wcon, yb = rnd(shp, 7, -wamp, wamp).astype(dtype), rnd(shp, 8).astype(dtype)
+    outs = [G.storage_from(np.full(shp, np.nan, dtype), o) for _ in range(4)]
+    G.vadv_adj(G.storage_from(wcon, o), G.storage_from(yb, o), *outs, prec=prec, workspace=workspace)
+    G.device_status()
+    refs = orc.vadv_adj(wcon.astype(np.float64), yb.astype(np.float64))
+    tol = F64_TOL if dtype == np.float64 else F32_TOL
+    for name, s, r in zip(("u_stage_bar", "u_pos_bar", "utens_bar", "utens_stage_bar"), outs, refs):
+        assert rel_err(region(s.numpy(), o, (I, J, K)), region(r, o, (I, J, K))) <= tol, name
+
+
+def test_vadv_adj_merged_and_accumulated(G, orc):
+    """One storage as u_stage_bar and u_pos_bar receives their sum; GTB_ADJ_ACCUMULATE adds."""
+    I, J, K = 96, 20, 40
+    o = (1, 1, 0)
+    shp = (K, J + 2, I + 2)
+    wcon, yb, base = rnd(shp, 9, -0.5, 0.5), rnd(shp, 10), rnd(shp, 11)
+    s = G.storage_from(base, o)
+    G.vadv_adj(G.storage_from(wcon, o), G.storage_from(yb, o), s, s, accumulate=True)
+    G.device_status()
+    us, up, _, _ = orc.vadv_adj(wcon, yb)
+    assert rel_err(region(s.numpy(), o, (I, J, K)), region(base + us + up, o, (I, J, K))) <= F64_TOL
+
+
+# ------------------------------------------------------------------ halos
+def test_halo_periodic_pair(G):
+    I, J, K = 37, 21, 3
+    inner = rnd((K, J, I), 12)
+    s = G.storage_from(np.pad(inner, ((0, 0), (2, 2), (2, 2))), (2, 2, 0))
+    G.halo_periodic(s, 2, 2)
+    G.device_status()
+    assert np.array_equal(s.numpy(), np.pad(inner, ((0, 0), (2, 2), (2, 2)), mode="wrap"))
+    # adjoint: <P x, y> = <x, P^T y> with P the refresh
+    y = rnd((K, J + 4, I + 4), 13)
+    t = G.storage_from(y, (2, 2, 0))
+    G.halo_periodic_adj(t, 2, 2)
+    G.device_status()
+    lhs = np.sum(np.pad(inner, ((0, 0), (2, 2), (2, 2)), mode="wrap") * y)
+    rhs = np.sum(inner * t.numpy()[:, 2:-2, 2:-2])
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+# ------------------------------------------------------------------ chain
+def oracle_chain_grad(orc, field, coeff, wcon, utens, utens_stage, steps):
+    """Loss 1/2 |final|^2 and its gradient in (field, coeff) from the oracle alone."""
+    K, J, I = field.shape
+    wrap2 = lambda a: np.pad(a, ((0, 0), (2, 2), (2, 2)), mode="wrap")
+    pad1 = lambda a: np.pad(a, ((0, 0), (1, 1), (1, 1)))
+    pad2 = lambda a: np.pad(a, ((0, 0), (2, 2), (2, 2)))
+    cst = pad2(coeff)
+    saved, x = [], field
+    for _ in range(steps):
+        st = wrap2(x)
+        saved.append(st)
+        h = orc.hdiff(st, cst)[:, 2:-2, 2:-2]
+        x = orc.vadv(pad1(h), wcon, pad1(h), pad1(utens), pad1(utens_stage))[:, 1:-1, 1:-1]
+    loss = 0.5 * np.sum(x * x)
+    yb, cbar = x.copy(), np.zeros_like(coeff)
+    jj, ii = np.meshgrid((np.arange(J + 4) - 2) % J, (np.arange(I + 4) - 2) % I, indexing="ij")
+    for st in reversed(saved):
+        us, up, _, _ = orc.vadv_adj(wcon, pad1(yb))
+        hb = (us + up)[:, 1:-1, 1:-1]
+        cb = np.zeros_like(cst)
+        ib = orc.hdiff_adj(st, cst, pad2(hb), coeff_bar=cb)
+        folded = np.zeros_like(field)
+        for k in range(K):
+            np.add.at(folded[k], (jj, ii), ib[k])
+        yb = folded
+        cbar += cb[:, 2:-2, 2:-2]
+    return loss, yb, cbar
+
+
+def gpu_chain(G, field, coeff, fixed, steps):
+    import torch
+    from paper_2311_08322_b300.autograd import chain
+    f = field.clone().requires_grad_(True)
+    c = coeff.clone().requires_grad_(True)
+    y = chain(f, c, fixed, steps)
+    loss = 0.5 * (y.double() ** 2).sum()
+    loss.backward()
+    return float(loss), f.grad, c.grad
+
+
+@pytest.mark.parametrize("I,J,K", [(64, 48, 40), (256, 256, 80)])
+def test_chain_gradient_vs_oracle(G, orc, I, J, K):
+    import torch
+    from paper_2311_08322_b300.autograd import chain_inputs
+    field, coeff, fixed, f = chain_inputs(I, J, K, seed=3, dtype=torch.float64)
+    loss, gf, gc = gpu_chain(G, field, coeff, fixed, 10)
+    rl, rf, rc = oracle_chain_grad(orc, field.cpu().numpy(), coeff.cpu().numpy(), f["wcon"],
+                                   f["utens"][:, 1:-1, 1:-1], f["utens_stage"][:, 1:-1, 1:-1], 10)
+    assert abs(loss - rl) <= 1e-11 * abs(rl)
+    assert rel_err(gf.cpu().numpy(), rf) <= 1e-10
+    assert rel_err(gc.cpu().numpy(), rc) <= 1e-10
+
+
+def test_chain_gradient_fp32_vs_oracle(G, orc):
+    import torch
+    from paper_2311_08322_b300.autograd import chain_inputs
+    I, J, K = 128, 96, 80
+    field, coeff, fixed, f = chain_inputs(I, J, K, seed=4, dtype=torch.float32)
+    loss, gf, gc = gpu_chain(G, field, coeff, fixed, 10)
+    f32 = {k: v.astype(np.float32).astype(np.float64) for k, v in f.items()}
+    rl, rf, rc = oracle_chain_grad(orc, field.double().cpu().numpy(), coeff.double().cpu().numpy(), f32["wcon"],
+                                   f32["utens"][:, 1:-1, 1:-1], f32["utens_stage"][:, 1:-1, 1:-1], 10)
+    assert abs(loss - rl) <= 1e-5 * abs(rl)
+    assert rel_err(gf.cpu().numpy(), rf) <= 1e-4
+    assert rel_err(gc.cpu().numpy(), rc) <= 1e-4
+
+
+def test_chain_gradient_central_differences(G):
+    """32 random unit directions in (field, coeff), h = 1e-6: the loss is piecewise
+    quadratic in the inputs, so central differences are exact up to rounding unless a
+    limiter switch lies within the step; such directions are detected (h vs h/2) and
+    set aside, and at least 28 of 32 must be smooth and agree."""
+    import torch
+    from paper_2311_08322_b300.autograd import chain, chain_inputs
+    field, coeff, fixed, _ = chain_inputs(64, 48, 40, seed=5, dtype=torch.float64)
+    _, gf, gc = gpu_chain(G, field, coeff, fixed, 10)
+    rng = np.random.default_rng(6)
+
+    def loss_at(df, dc):
+        with torch.no_grad():
+            y = chain(field + df, coeff + dc, fixed, 10)
+            return float(0.5 * (y ** 2).sum())
+
+    good = 0
+    for d in range(32):
+        vf = torch.from_numpy(rng.standard_normal(field.shape)).cuda()
+        vc = torch.from_numpy(rng.standard_normal(coeff.shape)).cuda() * 1e-2
+        nrm = torch.sqrt((vf ** 2).sum() + (vc ** 2).sum())
+        vf, vc = vf / nrm, vc / nrm
+        fd = [(loss_at(h * vf, h * vc) - loss_at(-h * vf, -h * vc)) / (2 * h) for h in (1e-6, 5e-7)]
+        exact = float((gf * vf).sum() + (gc * vc).sum())
+        if abs(fd[0] - fd[1]) > 1e-5 * max(1.0, abs(fd[0])):
+            continue  # a limiter switch inside the step
+        assert abs(fd[0] - exact) <= 1e-5 * max(1.0, abs(exact)), (d, fd[0], exact)
+        good += 1
+    assert good >= 28, good
