@@ -15,7 +15,10 @@ elimination, back substitution) on another.  Prints ONE JSON line (rank 0).
   (from pinned host memory) and of its two outputs inside the timed region.
 * roofline: the dominant kernel's achieved rate against its binding peak.
 * cpu_baseline: the FP64 CPU oracle (single thread) on a bounded sample.
+* adjoint_forward_ratio: backward / forward time of one chained step
+  (periodic halo + hdiff + vadv) through the adjoint kernels.
 * --impl reference: the oracle itself as the reference arm.
+Per-kernel times come from a second pass with an event around each kernel.
 Under torchrun every rank runs its own replica (independent problems, no
 collective): weak scaling.
 """
@@ -247,14 +250,13 @@ def run_gtb(args):
         uuid = str(dev)
     clocks = ClockSampler(uuid)
     clocks.start()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for q in range(args.steps):
-        step(sets[q % len(sets)], evs[q])
+        step(sets[q % len(sets)])
     t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -262,8 +264,17 @@ def run_gtb(args):
     clk = clocks.stop()
     gtb.device_status()
     el_ms = t_start.elapsed_time(t_end)
+    # the same steps again with an event around each kernel (per-kernel rooflines)
+    nser = max(20, min(args.steps, 500))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nser)]
+    torch.cuda.synchronize()
+    for q in range(nser):
+        step(sets[q % len(sets)], evs[q])
+    torch.cuda.synchronize()
+    gtb.device_status()
     h_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     v_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    adj = adjoint_ratio(gtb, f, sets) if rank == 0 and not args.no_adjoint else None
     if world > 1:
         t = torch.tensor([el_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -288,6 +299,7 @@ def run_gtb(args):
 
     for _ in range(2):
         e2e_step()
+    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -336,6 +348,7 @@ def run_gtb(args):
                        "l2": f"{args.sets} rotating input sets of "
                              f"{(hdiff_bytes(I, J, K, 8) + vadv_bytes(I, J, K, 8)) / 1e6:.0f} MB each (> 126 MB L2)"},
             "kernels": kern, "roofline": roof, "clocks": clk, "gpu_launches": 2 * args.steps,
+            "adjoint_forward_ratio": None if adj is None else adj["ratio"], "adjoint": adj,
             "e2e": {"value": round(e2e_value, 1), "unit": "Mpoints/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -349,6 +362,62 @@ def run_gtb(args):
     return 0
 
 
+def adjoint_ratio(gtb, f, sets, reps=50):
+    """Time of one chained step's backward over its forward at 256x256x80 FP64 (C ABI,
+    preallocated storages): forward = periodic halo refresh + hdiff + vadv, backward =
+    vadv_adj (merged u_stage/u_pos cotangent) + hdiff_adj (with coeff_bar) + halo fold."""
+    import torch
+    o2, o1 = (HDIFF_HALO, HDIFF_HALO, 0), (VADV_HALO, VADV_HALO, 0)
+    dom = (I, J, K)
+    bufs = []
+    for s in sets:
+        h = gtb.storage_from(np.zeros((K, J, I)), (0, 0, 0))
+        bufs.append({"fs": s["in"], "cs": s["coeff"], "h": h, "y": gtb.storage_from(np.zeros((K, J, I)), (0, 0, 0)),
+                     "wcon": s["wcon"], "ut": s["utens"], "uts": s["utens_stage"],
+                     "yb": gtb.storage_from(f["u_pos"][:, 1:-1, 1:-1].copy(), (0, 0, 0)),
+                     "hb": gtb.storage_from(np.zeros((K, J, I)), (0, 0, 0)),
+                     "ib": gtb.storage_from(np.zeros_like(f["in"]), o2),
+                     "cb": gtb.storage_from(np.zeros_like(f["coeff"]), o2)})
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def fwd(b):
+        gtb.halo_periodic(b["fs"], 2, 2, domain=dom)
+        gtb.hdiff(b["fs"], b["cs"], b["h"], domain=dom)
+        gtb.vadv(b["h"], b["wcon"], b["h"], b["ut"], b["uts"], b["y"], domain=dom)
+
+    def bwd(b, e=None):
+        if e: e[0].record(stream)
+        gtb.vadv_adj(b["wcon"], b["yb"], b["hb"], b["hb"], domain=dom)
+        if e: e[1].record(stream)
+        gtb.hdiff_adj(b["fs"], b["cs"], b["hb"], b["ib"], b["cb"], accumulate=True, domain=dom)
+        if e: e[2].record(stream)
+        gtb.halo_periodic_adj(b["ib"], 2, 2, domain=dom)
+        if e: e[3].record(stream)
+
+    for q in range(5):
+        fwd(bufs[q % len(bufs)])
+        bwd(bufs[q % len(bufs)])
+    torch.cuda.synchronize()
+    t = [ev() for _ in range(4)]
+    t[0].record(stream)
+    for q in range(reps):
+        fwd(bufs[q % len(bufs)])
+    t[1].record(stream)
+    es = [[ev() for _ in range(4)] for _ in range(reps)]
+    for q in range(reps):
+        bwd(bufs[q % len(bufs)], es[q])
+    t[2].record(stream)
+    torch.cuda.synchronize()
+    gtb.device_status()
+    f_ms, b_ms = t[0].elapsed_time(t[1]) / reps, t[1].elapsed_time(t[2]) / reps
+    return {"ratio": round(b_ms / f_ms, 3), "forward_ms": round(f_ms, 4), "backward_ms": round(b_ms, 4),
+            "vadv_adj_ms": round(float(np.mean([e[0].elapsed_time(e[1]) for e in es])), 4),
+            "hdiff_adj_ms": round(float(np.mean([e[1].elapsed_time(e[2]) for e in es])), 4),
+            "halo_adj_ms": round(float(np.mean([e[2].elapsed_time(e[3]) for e in es])), 4),
+            "workload": "one chained step at 256x256x80 FP64 (halo refresh + hdiff + vadv vs their adjoints)"}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,6 +427,7 @@ def main():
     ap.add_argument("--sets", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

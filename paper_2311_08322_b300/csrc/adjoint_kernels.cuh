@@ -148,13 +148,13 @@ __global__ void __launch_bounds__(32 * BJ)
 template <typename T, int TI, int TJ>
 struct HadjTile {
     // regions (tile-relative offsets of their first element)
-    static constexpr int IX = TI + 6, IY = TJ + 6;  // in: tile +- 3
-    static constexpr int QX = TI + 4, QY = TJ + 4;  // q, lap: tile +- 2
+    static constexpr int IX = TI + 6, IY = TJ + 6;   // in: tile +- 3
+    static constexpr int QX = TI + 4, QY = TJ + 4;   // q, lap: tile +- 2
     static constexpr int GXX = TI + 3, GXY = TJ + 2; // x-faces: i in [-2, TI], rows tile +- 1
     static constexpr int GYX = TI + 2, GYY = TJ + 3; // y-faces: cols tile +- 1, j in [-2, TJ]
-    static constexpr int LX = TI + 2, LY = TJ + 2;  // lb: tile +- 1
-    static constexpr int FXX = TI + 1, FYY = TJ + 1; // forward fluxes for coeff_bar
-    static constexpr int elems = IX * IY + 2 * QX * QY + GXX * GXY + GYX * GYY + LX * LY + FXX * TJ + TI * FYY;
+    static constexpr int LX = TI + 2, LY = TJ + 2;   // lb: tile +- 1
+    // per face: its cotangent g and its forward (limited) value f
+    static constexpr int elems = IX * IY + 2 * QX * QY + 2 * (GXX * GXY + GYX * GYY) + LX * LY;
 };
 
 template <typename T, int TI, int TJ>
@@ -168,20 +168,34 @@ struct HadjGeom {
     int accumulate_coeff_bar;
 };
 
+// Limiter decision of the definition, f * g > 0 (strict), taken from the signs:
+// the product of two finite values is positive iff both are nonzero with equal
+// signs (barring underflow of the product).
+template <typename T>
+__device__ __forceinline__ bool limited(T f, T g) {
+    if constexpr (sizeof(T) == 8) {
+        const int fh = __double2hiint(f), gh = __double2hiint(g);
+        const bool fz = ((fh & 0x7FFFFFFF) | __double2loint(f)) == 0, gz = ((gh & 0x7FFFFFFF) | __double2loint(g)) == 0;
+        return !fz && !gz && ((fh ^ gh) >= 0);
+    } else {
+        return f * g > T(0);
+    }
+}
+
 template <typename T, int TI, int TJ, int NT>
 __global__ void __launch_bounds__(NT)
     hdiff_adj_kernel(const View<const T> in, const View<const T> coeff, const View<const T> ob, const View<T> ib,
                      const View<T> cb, const HadjGeom g) {
     using H = HadjTile<T, TI, TJ>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *S_in = reinterpret_cast<T *>(smem_raw);  // in at (i, j) = tile (-3..TI+2, -3..TJ+2)
+    T *S_in = reinterpret_cast<T *>(smem_raw);  // in at tile (-3..TI+2, -3..TJ+2)
     T *S_q = S_in + H::IX * H::IY;              // q at tile (-2..TI+1, -2..TJ+1)
     T *S_lap = S_q + H::QX * H::QY;             // forward lap, same region as q
     T *S_gx = S_lap + H::QX * H::QY;            // x-face cotangents, faces i in [-2, TI], rows [-1, TJ]
-    T *S_gy = S_gx + H::GXX * H::GXY;           // y-face cotangents, cols [-1, TI], faces j in [-2, TJ]
-    T *S_lb = S_gy + H::GYX * H::GYY;           // lap cotangents, tile +- 1
-    T *S_fx = S_lb + H::LX * H::LY;             // forward x-fluxes, faces [-1, TI-1], rows [0, TJ)
-    T *S_fy = S_fx + H::FXX * TJ;               // forward y-fluxes, cols [0, TI), faces [-1, TJ-1]
+    T *S_fx = S_gx + H::GXX * H::GXY;           // x-face forward values (0 when limited), same region
+    T *S_gy = S_fx + H::GXX * H::GXY;           // y-face cotangents, cols [-1, TI], faces j in [-2, TJ]
+    T *S_fy = S_gy + H::GYX * H::GYY;           // y-face forward values, same region
+    T *S_lb = S_fy + H::GYX * H::GYY;           // lap cotangents, tile +- 1
 
     const int tid = threadIdx.x;
     const int ti0 = (blockIdx.x % g.tiles_i) * TI - 2;  // domain-relative i of tile column 0
@@ -205,7 +219,7 @@ __global__ void __launch_bounds__(NT)
         S_q[idx] = v;
     }
     __syncthreads();
-    auto IN = [&](int a, int b) -> T { return S_in[(a + 3) + (b + 3) * H::IX]; };   // tile-relative
+    auto IN = [&](int a, int b) -> T { return S_in[(a + 3) + (b + 3) * H::IX]; };  // tile-relative
     // forward Laplacian on tile +- 2 (needed only where -1 <= cell <= I, J)
     for (int idx = tid; idx < H::QX * H::QY; idx += NT) {
         const int a = idx % H::QX - 2, b = idx / H::QX - 2;
@@ -215,53 +229,41 @@ __global__ void __launch_bounds__(NT)
     __syncthreads();
     auto LAP = [&](int a, int b) -> T { return S_lap[(a + 2) + (b + 2) * H::QX]; };
     auto Q = [&](int a, int b) -> T { return S_q[(a + 2) + (b + 2) * H::QX]; };
-    // face cotangents (a face exists for domain-relative i in [-1, I-1], j in [0, J))
+    // every face once: keep/zero from the forward values, its forward flux and its cotangent
+    // (a face exists for domain-relative i in [-1, I-1], j in [0, J) in x, and likewise in y)
     for (int idx = tid; idx < H::GXX * H::GXY; idx += NT) {
         const int a = idx % H::GXX - 2, b = idx / H::GXX - 1;  // face between cells a and a+1, row b
         const int da = ti0 + a, db = tj0 + b;
-        T v = T(0);
+        T gv = T(0), fv = T(0);
         if (da >= -1 && da <= I - 1 && db >= 0 && db < J) {
             const T f = LAP(a + 1, b) - LAP(a, b);
-            if (!(f * (IN(a + 1, b) - IN(a, b)) > T(0))) v = Q(a, b) - Q(a + 1, b);
+            if (!limited(f, IN(a + 1, b) - IN(a, b))) {
+                gv = Q(a, b) - Q(a + 1, b);
+                fv = f;
+            }
         }
-        S_gx[idx] = v;
+        S_gx[idx] = gv;
+        S_fx[idx] = fv;
     }
     for (int idx = tid; idx < H::GYX * H::GYY; idx += NT) {
         const int a = idx % H::GYX - 1, b = idx / H::GYX - 2;  // face between rows b and b+1, column a
         const int da = ti0 + a, db = tj0 + b;
-        T v = T(0);
+        T gv = T(0), fv = T(0);
         if (da >= 0 && da < I && db >= -1 && db <= J - 1) {
             const T f = LAP(a, b + 1) - LAP(a, b);
-            if (!(f * (IN(a, b + 1) - IN(a, b)) > T(0))) v = Q(a, b) - Q(a, b + 1);
-        }
-        S_gy[idx] = v;
-    }
-    // forward fluxes around the tile's domain cells (for coeff_bar)
-    if (cb.p) {
-        for (int idx = tid; idx < H::FXX * TJ; idx += NT) {
-            const int a = idx % H::FXX - 1, b = idx / H::FXX;
-            const int da = ti0 + a, db = tj0 + b;
-            T v = T(0);
-            if (da >= -1 && da <= I - 1 && db >= 0 && db < J) {
-                const T f = LAP(a + 1, b) - LAP(a, b);
-                v = (f * (IN(a + 1, b) - IN(a, b)) > T(0)) ? T(0) : f;
+            if (!limited(f, IN(a, b + 1) - IN(a, b))) {
+                gv = Q(a, b) - Q(a, b + 1);
+                fv = f;
             }
-            S_fx[idx] = v;
         }
-        for (int idx = tid; idx < TI * H::FYY; idx += NT) {
-            const int a = idx % TI, b = idx / TI - 1;
-            const int da = ti0 + a, db = tj0 + b;
-            T v = T(0);
-            if (da >= 0 && da < I && db >= -1 && db <= J - 1) {
-                const T f = LAP(a, b + 1) - LAP(a, b);
-                v = (f * (IN(a, b + 1) - IN(a, b)) > T(0)) ? T(0) : f;
-            }
-            S_fy[idx] = v;
-        }
+        S_gy[idx] = gv;
+        S_fy[idx] = fv;
     }
     __syncthreads();
     auto GX = [&](int a, int b) -> T { return S_gx[(a + 2) + (b + 1) * H::GXX]; };
     auto GY = [&](int a, int b) -> T { return S_gy[(a + 1) + (b + 2) * H::GYX]; };
+    auto FX = [&](int a, int b) -> T { return S_fx[(a + 2) + (b + 1) * H::GXX]; };
+    auto FY = [&](int a, int b) -> T { return S_fy[(a + 1) + (b + 2) * H::GYX]; };
     for (int idx = tid; idx < H::LX * H::LY; idx += NT) {
         const int a = idx % H::LX - 1, b = idx / H::LX - 1;
         S_lb[idx] = (GX(a - 1, b) - GX(a, b)) + (GY(a, b - 1) - GY(a, b));
@@ -274,11 +276,10 @@ __global__ void __launch_bounds__(NT)
         if (da < -2 || da >= I + 2 || db < -2 || db >= J + 2) continue;
         const T tr = T(4) * LB(a, b) - (((LB(a + 1, b) + LB(a - 1, b)) + LB(a, b + 1)) + LB(a, b - 1));
         const bool dom = in_dom(da, db);
-        const int64_t off_ob = da + (int64_t)db * ob.sj + (int64_t)k * ob.sk;
-        const T o = dom ? ob.p[off_ob] : T(0);
+        const T o = dom ? ob.p[da + (int64_t)db * ob.sj + (int64_t)k * ob.sk] : T(0);
         ib.p[da + (int64_t)db * ib.sj + (int64_t)k * ib.sk] = o - tr;
         if (cb.p && dom) {
-            const T D = (S_fx[(a + 1) + b * H::FXX] - S_fx[a + b * H::FXX]) + (S_fy[a + (b + 1) * TI] - S_fy[a + b * TI]);
+            const T D = (FX(a, b) - FX(a - 1, b)) + (FY(a, b) - FY(a, b - 1));
             T *c = cb.p + da + (int64_t)db * cb.sj + (int64_t)k * cb.sk;
             *c = g.accumulate_coeff_bar ? *c - D * o : -D * o;
         }
@@ -302,12 +303,33 @@ __global__ void halo_periodic_kernel(const View<T> f, int I, int J, int K, int h
 
 // Adjoint of the refresh: every domain point gathers the cotangents of the halo
 // points that copied it (halo widths <= I, J, so each halo point maps to one
-// domain point); the halo itself is left unchanged.
+// domain point); the halo itself is left unchanged.  Only the band of domain
+// points within hi (hj) of an edge receives anything, so the launch covers
+// that band: its rows j < hj or j >= J-hj in full, and the first and last hi
+// columns of the other rows.
 template <typename T>
 __global__ void halo_periodic_adj_kernel(const View<T> f, int I, int J, int K, int hi, int hj) {
-    const int64_t n = (int64_t)I * J * K;
+    const int rows_full = min(J, 2 * hj);             // rows taken in full
+    const int mid_rows = J - rows_full;               // rows of which only 2*hi edge columns count
+    const int cols_edge = min(I, 2 * hi);
+    const int64_t per_level = (int64_t)rows_full * I + (int64_t)mid_rows * cols_edge;
+    const int64_t n = per_level * K;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int a = (int)(idx % I), b = (int)((idx / I) % J), k = (int)(idx / ((int64_t)I * J));
+        const int k = (int)(idx / per_level);
+        int64_t r = idx % per_level;
+        int a, b;
+        if (r < (int64_t)rows_full * I) {
+            const int rr = (int)(r / I);
+            a = (int)(r % I);
+            b = rr < hj ? rr : J - rows_full + rr;  // top hj rows, then the bottom ones
+            if (rows_full < 2 * hj) b = rr;         // J < 2 hj: every row is full
+        } else {
+            r -= (int64_t)rows_full * I;
+            const int cc = (int)(r % cols_edge);
+            b = hj + (int)(r / cols_edge);
+            a = cc < hi ? cc : I - cols_edge + cc;
+            if (cols_edge < 2 * hi) a = cc;
+        }
         T acc = T(0);
 #pragma unroll
         for (int sa = -1; sa <= 1; ++sa)

@@ -360,7 +360,10 @@ static int run_hdiff_adj(const gtb_field *fin, const gtb_field *fcf, const gtb_f
 template <typename T>
 static int run_halo(const gtb_field *f, int hi, int hj, const int64_t dom[3], bool adjoint, cudaStream_t st) {
     const View<T> v = view_of<T>(f);
-    const int64_t n = adjoint ? dom[0] * dom[1] * dom[2] : (dom[0] + 2 * hi) * (dom[1] + 2 * hj) * dom[2];
+    const int64_t rows_full = std::min<int64_t>(dom[1], 2 * hj);
+    const int64_t band = rows_full * dom[0] + (dom[1] - rows_full) * std::min<int64_t>(dom[0], 2 * hi);
+    const int64_t n = adjoint ? band * dom[2] : (dom[0] + 2 * hi) * (dom[1] + 2 * hj) * dom[2];
+    if (n == 0) return ok();
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)sm_count() * 16);
     if (adjoint)
