@@ -189,6 +189,44 @@ int gtb_halo_periodic(const gtb_field *f, int hi, int hj, const int64_t *domain,
 int gtb_halo_periodic_adj(const gtb_field *f, int hi, int hj, const int64_t *domain, void *stream);
 
 /*
+ * Batched ensembles of uneven domains (the paper's stencils over many
+ * independent members, e.g. an ensemble forecast).  Each member runs
+ *   h   = hdiff(in, coeff)                         (gtb_hdiff on its domain)
+ *   out = vadv(u_stage = h, wcon, u_pos = h, utens, utens_stage)   (gtb_vadv)
+ * A plan validates every member once (the checks of gtb_hdiff and gtb_vadv,
+ * plus: h and out may overlap no field of any member, except out being its
+ * own member's utens_stage view; in needs 16-byte pitches), builds device
+ * tables (one TMA descriptor per member), allocates its scratch and captures
+ * a CUDA graph of two persistent kernels (hdiff stage, then vadv stage) that
+ * pull work items from atomic queues.  gtb_batch_run replays that graph: it
+ * allocates nothing and never synchronises.  A batched member's results equal
+ * those of gtb_hdiff + gtb_vadv with the same hdiff tile, bit for bit.  A plan
+ * belongs to the device current at creation and holds its members' pointers;
+ * runs of one plan must not overlap on the GPU (they share the queues).
+ */
+typedef struct gtb_member {
+    gtb_field in, coeff, h;                   /* hdiff: h = hdiff(in, coeff) */
+    gtb_field wcon, utens, utens_stage, out;  /* vadv: out = vadv(h, wcon, h, utens, utens_stage) */
+    int64_t domain[3];                        /* (I, J, K), all > 0; K <= 448 */
+} gtb_member;
+
+typedef struct gtb_batch_config {
+    int32_t hdiff_tile;    /* 0: 4 warps x 16 rows per tile, 1: 2 warps x 16 rows */
+    int32_t hdiff_levels;  /* K levels per hdiff work item (the K-blocking); <= 0: whole columns */
+    int32_t vadv_warps;    /* warps (32 columns each) per vadv work item: 1, 2 or 4 */
+    int32_t ctas_per_sm;   /* resident persistent CTAs per SM per stage; <= 0: as many as fit */
+} gtb_batch_config;
+
+typedef struct gtb_plan gtb_plan;
+
+int gtb_batch_plan(const gtb_member *members, int n, double dtr_stage, double beta_v, int prec,
+                   unsigned flags, const gtb_batch_config *config, gtb_plan **plan);
+int gtb_batch_run(const gtb_plan *plan, void *stream);
+/* info: hdiff items, vadv items, hdiff grid, vadv grid, total points, members */
+int gtb_plan_info(const gtb_plan *plan, int64_t info[6]);
+int gtb_plan_destroy(gtb_plan *plan);
+
+/*
  * gtb_vadv_noalloc -- gtb_vadv for callers that cannot allocate device memory.
  * The paper has no counterpart: this exists for code that runs inside a host
  * application that owns every device allocation (a fixed memory budget or a

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "gtb.h"
 #include "gtb_device.cuh"
@@ -19,6 +20,7 @@
 #include "hdiff_rs.cuh"
 #include "vadv_kernels.cuh"
 #include "adjoint_kernels.cuh"
+#include "batch_kernels.cuh"
 
 namespace gtb {
 
@@ -709,4 +711,275 @@ extern "C" int gtb_halo_periodic_adj(const gtb_field *f, int hi, int hj, const i
     if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return f->dtype == GTB_F64 ? run_halo<double>(f, hi, hj, dom, true, st) : run_halo<float>(f, hi, hj, dom, true, st);
+}
+
+// ====================================================================== batched ensembles
+struct gtb_plan {
+    int device = 0, dtype = 0, prec = 0, n = 0;
+    gtb_batch_config cfg{};
+    int h_items = 0, v_items = 0, h_grid = 0, v_grid = 0;
+    void *d_maps = nullptr, *d_hmem = nullptr, *d_vmem = nullptr, *d_scratch = nullptr;
+    int *d_counters = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double points = 0;
+};
+
+namespace gtb {
+
+static void plan_free(gtb_plan *p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    cudaFree(p->d_maps);
+    cudaFree(p->d_hmem);
+    cudaFree(p->d_vmem);
+    cudaFree(p->d_scratch);
+    cudaFree(p->d_counters);
+    delete p;
+}
+
+// hdiff tile variants of the batched form: 0 = 4 warps x 16 rows, 1 = 2 warps x 16 rows
+template <typename T>
+struct BatchHCfg {
+    static constexpr int CPL = sizeof(T) == 8 ? 2 : 4, R = 16, STAGES = 2;
+};
+
+template <typename T, int W>
+static int batch_hdiff_launch_info(int ctas_per_sm, int *slots, void (**kern)(const CUtensorMap *, const BatchHdiffMember<T> *, int, int, int *), int *smem) {
+    using C = BatchHCfg<T>;
+    constexpr bool FIXED = sizeof(T) == 8;
+    auto k = hdiff_batch_kernel<T, C::CPL, W, C::R, C::STAGES, FIXED>;
+    *smem = hdiff_rs_smem_bytes<T, C::CPL, W, C::R, C::STAGES>();
+    if (prepare_kernel(k, *smem) != cudaSuccess) return launch_status("batch: hdiff shared-memory attribute");
+    int rb = resident_blocks(k, 32 * W, *smem);
+    if (ctas_per_sm > 0) rb = std::min(rb, ctas_per_sm);
+    *slots = rb * sm_count();
+    *kern = k;
+    return GTB_OK;
+}
+
+template <typename T, typename N, int BJ>
+static int batch_vadv_launch_info(int ctas_per_sm, int *slots, void (**kern)(const BatchVadvMember<T> *, int, int, int *, N *, size_t, int)) {
+    auto k = vadv_batch_kernel<T, N, BJ>;
+    int rb = resident_blocks(k, 32 * BJ, 0);
+    if (ctas_per_sm > 0) rb = std::min(rb, ctas_per_sm);
+    *slots = rb * sm_count();
+    *kern = k;
+    return GTB_OK;
+}
+
+template <typename T, typename N, int W, int BJ>
+static int build_plan(const gtb_member *mem, int n, double dtr, double beta, unsigned flags, gtb_plan *P) {
+    using C = BatchHCfg<T>;
+    using Tile = RsTile<T, C::CPL, W, C::R>;
+    const size_t es = sizeof(T);
+    constexpr int kAlign = 16 / (int)sizeof(T);
+    std::vector<CUtensorMap> maps(n);
+    std::vector<BatchHdiffMember<T>> hm(n);
+    std::vector<BatchVadvMember<T>> vm(n);
+    std::vector<int> vorder(n);
+    int k_max = 1;
+    double pts = 0;
+    // hdiff members in the given order
+    int hitems = 0;
+    for (int q = 0; q < n; ++q) {
+        const gtb_member &M = mem[q];
+        const int64_t *d = M.domain;
+        HdiffGeom g{};
+        g.I = (int)d[0], g.J = (int)d[1], g.K = (int)d[2];
+        g.tiles_i = (g.I + Tile::TI - 1) / Tile::TI;
+        g.tiles_j = (g.J + Tile::TJ - 1) / Tile::TJ;
+        g.n_tiles = g.tiles_i * g.tiles_j;
+        g.kc = P->cfg.hdiff_levels > 0 ? std::min(P->cfg.hdiff_levels, g.K) : g.K;
+        const uintptr_t base = reinterpret_cast<uintptr_t>(M.in.ptr), abase = base & ~uintptr_t(15);
+        const int shift = (int)((base - abase) / es);
+        const int xraw = (int)M.in.origin[0] - 2 + shift;
+        g.xs = xraw % kAlign;
+        g.X0 = xraw - g.xs;
+        g.Y0 = (int)M.in.origin[1] - 2;
+        g.Z0 = (int)M.in.origin[2];
+        cuuint64_t gdim[3] = {(cuuint64_t)(M.in.shape[0] + shift), (cuuint64_t)M.in.shape[1], (cuuint64_t)M.in.shape[2]};
+        cuuint64_t gstride[2] = {(cuuint64_t)(M.in.strides[1] * es), (cuuint64_t)(M.in.strides[2] * es)};
+        cuuint32_t box[3] = {(cuuint32_t)Tile::BX, (cuuint32_t)Tile::BY, 1};
+        cuuint32_t estr[3] = {1, 1, 1};
+        memset(&maps[q], 0, sizeof(CUtensorMap));
+        CUresult r = encode_fn()(&maps[q], sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                 3, reinterpret_cast<void *>(abase), gdim, gstride, box, estr,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(GTB_ERR_LAYOUT, "gtb_batch_plan: member %d: tensor-map encoding failed (%d)", q, (int)r);
+        const View<T> cf = view_of<T>(&M.coeff), out = view_of<T>(&M.h);
+        auto aligned = [&](const View<T> &v) {
+            return reinterpret_cast<uintptr_t>(v.p) % 16 == 0 && (v.sj * es) % 16 == 0 && (v.sk * es) % 16 == 0;
+        };
+        hm[q] = BatchHdiffMember<T>{view_of<T>(&M.in), cf, out, g, (aligned(cf) && aligned(out)) ? 1 : 0, hitems};
+        hitems += g.n_tiles * ((g.K + g.kc - 1) / g.kc);
+        k_max = std::max(k_max, g.K);
+        pts += (double)g.I * g.J * g.K;
+    }
+    // vadv members longest column first (largest K), so the queue ends with short items
+    for (int q = 0; q < n; ++q) vorder[q] = q;
+    std::stable_sort(vorder.begin(), vorder.end(), [&](int a, int b) { return mem[a].domain[2] > mem[b].domain[2]; });
+    const bool literal = flags & GTB_WCON_LITERAL;
+    int vitems = 0;
+    for (int r = 0; r < n; ++r) {
+        const gtb_member &M = mem[vorder[r]];
+        VadvGeom g{};
+        g.I = (int)M.domain[0], g.J = (int)M.domain[1], g.K = (int)M.domain[2];
+        g.literal = literal ? 1 : 0;
+        const double bp = 0.5 * (1.0 + beta), bm = 0.5 * (1.0 - beta);
+        g.sym = (bp == bm) ? 1 : 0;
+        g.dtr = dtr;
+        g.ka = (literal ? -0.5 : -0.25) * bp;
+        g.kas = (literal ? -0.5 : -0.25) * bm;
+        int e2 = 0;
+        const double mant = std::frexp(-g.ka, &e2);
+        g.ka_pow2 = (mant == 0.5 && e2 - 1 < 0 && e2 - 1 > -64) ? e2 - 1 : 0;
+        const int bx = (g.I + 31) / 32, by = (g.J + BJ - 1) / BJ;
+        const View<const T> h = view_of<const T>(&M.h);
+        vm[r] = BatchVadvMember<T>{h, view_of<const T>(&M.wcon), h, view_of<const T>(&M.utens),
+                                   view_of<const T>(&M.utens_stage), view_of<T>(&M.out), g, bx, vitems};
+        vitems += bx * by;
+    }
+    void (*hk)(const CUtensorMap *, const BatchHdiffMember<T> *, int, int, int *);
+    void (*vk)(const BatchVadvMember<T> *, int, int, int *, N *, size_t, int);
+    int hslots, vslots, hsmem, rc;
+    if ((rc = batch_hdiff_launch_info<T, W>(P->cfg.ctas_per_sm, &hslots, &hk, &hsmem))) return rc;
+    if ((rc = batch_vadv_launch_info<T, N, BJ>(P->cfg.ctas_per_sm, &vslots, &vk))) return rc;
+    P->h_items = hitems, P->v_items = vitems;
+    P->h_grid = std::max(1, std::min(hitems, hslots));
+    P->v_grid = std::max(1, std::min(vitems, vslots));
+    P->points = pts;
+    const size_t slice = (size_t)(vadv_dp_global<T, N>() ? 1 : 2) * k_max * 32 * BJ;
+    cudaError_t e;
+    if ((e = cudaMalloc(&P->d_maps, sizeof(CUtensorMap) * n)) || (e = cudaMalloc(&P->d_hmem, sizeof(BatchHdiffMember<T>) * n)) ||
+        (e = cudaMalloc(&P->d_vmem, sizeof(BatchVadvMember<T>) * n)) || (e = cudaMalloc(&P->d_counters, 2 * sizeof(int))) ||
+        (e = cudaMalloc(&P->d_scratch, sizeof(N) * slice * P->v_grid)))
+        return fail(GTB_ERR_LAUNCH, "gtb_batch_plan: device tables: %s", cudaGetErrorString(e));
+    if ((e = cudaMemcpy(P->d_maps, maps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(P->d_hmem, hm.data(), sizeof(BatchHdiffMember<T>) * n, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(P->d_vmem, vm.data(), sizeof(BatchVadvMember<T>) * n, cudaMemcpyHostToDevice)))
+        return fail(GTB_ERR_LAUNCH, "gtb_batch_plan: table upload: %s", cudaGetErrorString(e));
+    // capture: reset the two queues, hdiff stage, vadv stage
+    cudaStream_t cs;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)))
+        return fail(GTB_ERR_LAUNCH, "gtb_batch_plan: stream: %s", cudaGetErrorString(e));
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(P->d_counters, 0, 2 * sizeof(int), cs);
+        hk<<<P->h_grid, 32 * W, hsmem, cs>>>(static_cast<const CUtensorMap *>(P->d_maps),
+                                             static_cast<const BatchHdiffMember<T> *>(P->d_hmem), n, hitems, P->d_counters);
+        vk<<<P->v_grid, dim3(32, BJ), 0, cs>>>(static_cast<const BatchVadvMember<T> *>(P->d_vmem), n, vitems,
+                                               P->d_counters + 1, static_cast<N *>(P->d_scratch), slice, k_max);
+        e = cudaStreamEndCapture(cs, &P->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, P->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return fail(GTB_ERR_LAUNCH, "gtb_batch_plan: graph capture: %s", cudaGetErrorString(e));
+    return GTB_OK;
+}
+
+template <typename T, typename N, int W>
+static int build_plan_bj(const gtb_member *mem, int n, double dtr, double beta, unsigned flags, gtb_plan *P) {
+    switch (P->cfg.vadv_warps) {
+    case 1: return build_plan<T, N, W, 1>(mem, n, dtr, beta, flags, P);
+    case 4: return build_plan<T, N, W, 4>(mem, n, dtr, beta, flags, P);
+    default: return build_plan<T, N, W, 2>(mem, n, dtr, beta, flags, P);
+    }
+}
+
+template <typename T, typename N>
+static int build_plan_w(const gtb_member *mem, int n, double dtr, double beta, unsigned flags, gtb_plan *P) {
+    return P->cfg.hdiff_tile == 1 ? build_plan_bj<T, N, 2>(mem, n, dtr, beta, flags, P)
+                                  : build_plan_bj<T, N, 4>(mem, n, dtr, beta, flags, P);
+}
+
+}  // namespace gtb
+
+extern "C" int gtb_batch_plan(const gtb_member *members, int n, double dtr_stage, double beta_v, int prec,
+                              unsigned flags, const gtb_batch_config *config, gtb_plan **plan) {
+    if (!plan) return fail(GTB_ERR_NULL, "gtb_batch_plan: NULL plan");
+    *plan = nullptr;
+    if (!members || n <= 0) return fail(GTB_ERR_ARG, "gtb_batch_plan: no members");
+    if (flags & ~GTB_WCON_LITERAL) return fail(GTB_ERR_ARG, "gtb_batch_plan: unknown flags 0x%x", flags);
+    if (encode_fn() == nullptr) return fail(GTB_ERR_LAUNCH, "gtb_batch_plan: cuTensorMapEncodeTiled unavailable");
+    const int dt = members[0].in.dtype;
+    if (!dtype_size(dt)) return fail(GTB_ERR_DTYPE, "gtb_batch_plan: unknown dtype %d", dt);
+    if (prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF || (dt == GTB_F64 && prec != GTB_PREC_NATIVE))
+        return fail(GTB_ERR_ARG, "gtb_batch_plan: bad prec %d for this dtype", prec);
+    if (!(dtr_stage == dtr_stage) || !(beta_v == beta_v)) return fail(GTB_ERR_ARG, "gtb_batch_plan: NaN scalar");
+    const bool literal = flags & GTB_WCON_LITERAL;
+    const Reach r2{{2, 2, 0}, {2, 2, 0}}, r0{{0, 0, 0}, {0, 0, 0}}, rw{{0, 0, 0}, {literal ? 0 : 1, 0, 0}};
+    int rc;
+    for (int q = 0; q < n; ++q) {
+        const gtb_member &M = members[q];
+        const gtb_field *f[7] = {&M.in, &M.coeff, &M.h, &M.wcon, &M.utens, &M.utens_stage, &M.out};
+        static const char *nm[7] = {"in", "coeff", "h", "wcon", "utens", "utens_stage", "out"};
+        const Reach *rr[7] = {&r2, &r0, &r0, &rw, &r0, &r0, &r0};
+        for (int d = 0; d < 3; ++d)
+            if (M.domain[d] <= 0) return fail(GTB_ERR_EXTENT, "gtb_batch_plan: member %d: empty domain", q);
+        if (M.domain[2] > kVadvMaxK) return fail(GTB_ERR_UNSUPPORTED, "gtb_batch_plan: member %d: K above %d", q, kVadvMaxK);
+        for (int a = 0; a < 7; ++a) {
+            if ((rc = check_field(nm[a], f[a], dt)) || (rc = check_extent(nm[a], f[a], *rr[a], M.domain))) {
+                char msg[512];
+                snprintf(msg, sizeof msg, "gtb_batch_plan: member %d: %s", q, gtb_last_error());
+                return fail(rc, "%s", msg);
+            }
+        }
+        const size_t es = dtype_size(dt);
+        if ((M.in.strides[1] * es) % 16 || (M.in.strides[2] * es) % 16)
+            return fail(GTB_ERR_LAYOUT, "gtb_batch_plan: member %d: in needs 16-byte pitches (TMA)", q);
+        // outputs: h and out may not overlap any field of any member (out == utens_stage of its own member allowed)
+        for (int b = 0; b < n; ++b) {
+            const gtb_member &B = members[b];
+            const gtb_field *g[7] = {&B.in, &B.coeff, &B.h, &B.wcon, &B.utens, &B.utens_stage, &B.out};
+            for (int a = 0; a < 7; ++a) {
+                if (b == q && (a == 2)) continue;  // h itself
+                if (overlaps(&M.h, g[a])) return fail(GTB_ERR_ALIAS, "gtb_batch_plan: member %d: h overlaps a field of member %d", q, b);
+            }
+            for (int a = 0; a < 7; ++a) {
+                if (b == q && (a == 6 || (a == 5 && same_view(&M.out, &M.utens_stage)))) continue;
+                if (overlaps(&M.out, g[a])) return fail(GTB_ERR_ALIAS, "gtb_batch_plan: member %d: out overlaps a field of member %d", q, b);
+            }
+        }
+    }
+    gtb_plan *P = new gtb_plan();
+    P->n = n, P->dtype = dt, P->prec = prec;
+    cudaGetDevice(&P->device);
+    if (config) P->cfg = *config;
+    if (P->cfg.vadv_warps != 1 && P->cfg.vadv_warps != 2 && P->cfg.vadv_warps != 4) P->cfg.vadv_warps = 2;
+    if (P->cfg.hdiff_tile != 1) P->cfg.hdiff_tile = 0;
+    if (dt == GTB_F64) rc = build_plan_w<double, double>(members, n, dtr_stage, beta_v, flags, P);
+    else if (prec == GTB_PREC_F64) rc = build_plan_w<float, double>(members, n, dtr_stage, beta_v, flags, P);
+    else if (prec == GTB_PREC_DF) rc = build_plan_w<float, df>(members, n, dtr_stage, beta_v, flags, P);
+    else rc = build_plan_w<float, float>(members, n, dtr_stage, beta_v, flags, P);
+    if (rc) {
+        plan_free(P);
+        return rc;
+    }
+    *plan = P;
+    return ok();
+}
+
+extern "C" int gtb_batch_run(const gtb_plan *plan, void *stream) {
+    if (!plan || !plan->exec) return fail(GTB_ERR_NULL, "gtb_batch_run: NULL plan");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != plan->device) return fail(GTB_ERR_ARG, "gtb_batch_run: the plan belongs to device %d", plan->device);
+    cudaError_t e = cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(GTB_ERR_LAUNCH, "gtb_batch_run: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+extern "C" int gtb_plan_info(const gtb_plan *plan, int64_t info[6]) {
+    if (!plan || !info) return fail(GTB_ERR_NULL, "gtb_plan_info: NULL argument");
+    info[0] = plan->h_items, info[1] = plan->v_items, info[2] = plan->h_grid, info[3] = plan->v_grid;
+    info[4] = (int64_t)plan->points, info[5] = plan->n;
+    return ok();
+}
+
+extern "C" int gtb_plan_destroy(gtb_plan *plan) {
+    plan_free(plan);
+    return GTB_OK;
 }

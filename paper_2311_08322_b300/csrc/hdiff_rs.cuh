@@ -188,19 +188,15 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
     }
 }
 
+// One work item: tile `tile` of the launch geometry g, K-chunk `kchunk`.
+// Block-uniform; the caller provides the shared-memory stages and barriers.
 template <typename T, int CPL, int W, int R, int STAGES, bool USE_TMA, bool FIXED>
-__global__ void __launch_bounds__(32 * W)
-    hdiff_rs_kernel(const __grid_constant__ CUtensorMap tmap, const View<T> in, const View<T> coeff,
-                    const View<T> out, const HdiffGeom g, const int vec_ok) {
+__device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const View<T> &in, const View<T> &coeff,
+                                              const View<T> &out, const HdiffGeom &g, int vec_ok, int tile,
+                                              int kchunk, unsigned char *base, uint64_t *bars) {
     using G = RsTile<T, CPL, W, R>;
     constexpr int NT = 32 * W;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char *base =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(base + STAGES * G::stage_stride);
-
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x % g.n_tiles, kchunk = blockIdx.x / g.n_tiles;
     const int ti0 = (tile % g.tiles_i) * G::TI, tj0 = (tile / g.tiles_i) * G::TJ;
     const int k0 = kchunk * g.kc;
     const int nk = min(g.kc, g.K - k0);
@@ -210,10 +206,10 @@ __global__ void __launch_bounds__(32 * W)
     const int nrows = max(0, min(R, g.J - tj0 - cj0));  // rows of this strip inside the domain
     const int ncols = max(0, min(CPL, g.I - ti0 - lane * CPL));
 
-    // TMA ring (same protocol as the tile kernels)
+    // TMA ring: (re)initialised per item; no load is in flight between items
     if (USE_TMA) {
         if (tid == 0) {
-            prefetch_tensormap(&tmap);
+            prefetch_tensormap(tmap);
             for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
             fence_mbar_init();
         }
@@ -221,7 +217,7 @@ __global__ void __launch_bounds__(32 * W)
         if (tid == 0)
             for (int p = 0; p < STAGES && p < nk; ++p) {
                 mbar_arrive_expect_tx(&bars[p], G::box_bytes);
-                tma_load_3d(base + p * G::stage_stride, &tmap, &bars[p], g.X0 + ti0, g.Y0 + tj0, g.Z0 + k0 + p);
+                tma_load_3d(base + p * G::stage_stride, tmap, &bars[p], g.X0 + ti0, g.Y0 + tj0, g.Z0 + k0 + p);
             }
     }
     bool failed = false;
@@ -273,7 +269,7 @@ __global__ void __launch_bounds__(32 * W)
         if (USE_TMA && tid == 0 && p + STAGES < nk) {
             const int s = p % STAGES;
             mbar_arrive_expect_tx(&bars[s], G::box_bytes);
-            tma_load_3d(base + s * G::stage_stride, &tmap, &bars[s], g.X0 + ti0, g.Y0 + tj0, g.Z0 + k + STAGES);
+            tma_load_3d(base + s * G::stage_stride, tmap, &bars[s], g.X0 + ti0, g.Y0 + tj0, g.Z0 + k + STAGES);
         }
     }
     if (USE_TMA && failed) {
@@ -281,6 +277,26 @@ __global__ void __launch_bounds__(32 * W)
             for (int s = 0; s < STAGES; ++s) mbar_wait(&bars[s], 0), mbar_wait(&bars[s], 1);
         __syncthreads();
     }
+}
+
+template <typename T, int CPL, int W, int R, int STAGES>
+__device__ __forceinline__ unsigned char *hdiff_rs_smem(uint64_t **bars) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    *bars = reinterpret_cast<uint64_t *>(base + STAGES * RsTile<T, CPL, W, R>::stage_stride);
+    return base;
+}
+
+// Single domain: one CTA per (tile, K-chunk) item.
+template <typename T, int CPL, int W, int R, int STAGES, bool USE_TMA, bool FIXED>
+__global__ void __launch_bounds__(32 * W)
+    hdiff_rs_kernel(const __grid_constant__ CUtensorMap tmap, const View<T> in, const View<T> coeff,
+                    const View<T> out, const HdiffGeom g, const int vec_ok) {
+    uint64_t *bars;
+    unsigned char *base = hdiff_rs_smem<T, CPL, W, R, STAGES>(&bars);
+    hdiff_rs_item<T, CPL, W, R, STAGES, USE_TMA, FIXED>(&tmap, in, coeff, out, g, vec_ok, blockIdx.x % g.n_tiles,
+                                                         blockIdx.x / g.n_tiles, base, bars);
 }
 
 }  // namespace gtb

@@ -104,45 +104,33 @@ __device__ __forceinline__ double coef<double>(double s, double k, int n) {
 }
 
 // Where the forward sweep keeps its eliminated coefficients:
-//  * WS = false: c'_k (and d'_k unless parked) in shared memory, [K][block
-//    columns]; the K x 32 x BJ state caps the resident warps per SM.
-//  * WS = true: in a caller-provided global workspace, [K][I*J] (column id
-//    j*I + i, coalesced along i); it is written and read back within a few
-//    microseconds, so it lives in L2.  No shared memory is needed and the
-//    resident warps are bounded by registers only: on B300 the FP64
-//    recurrence runs at the pipe's rate only with many warps per SM (one
-//    warp keeps about one FP64 instruction in flight), so this is the fast form.
+//  * shared memory, [K][block columns]: the K x 32 x BJ state caps the
+//    resident warps per SM;
+//  * a caller-provided global workspace, [K][I*J] (column id j*I + i,
+//    coalesced along i), written and read back within a few microseconds, so
+//    it lives in L2.  No shared memory is needed and the resident warps are
+//    bounded by registers only: on B300 the FP64 recurrence runs at the
+//    pipe's rate only with many warps per SM (one warp keeps about one FP64
+//    instruction in flight), so this is the fast form;
+//  * a per-CTA slice of global scratch, [K][block columns] (batched form).
+// The caller passes the base, the stride between levels and this thread's
+// column index; `wr` says whether this thread may write its slot (inactive
+// threads alias a real column in a domain-indexed workspace).
 // DPG: d'_k is parked in the output array (same element size as N) and read
 // back by the backward sweep from L2.
-template <typename T, typename N, int BJ, bool DPG, bool WS>
-__global__ void __launch_bounds__(32 * BJ)
-    vadv_kernel(const View<const T> us, const View<const T> wc, const View<const T> up, const View<const T> ut,
-                const View<const T> uts, const View<T> out, const VadvGeom g, N *__restrict__ ws) {
-    constexpr int NT = 32 * BJ;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-
-    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
-    const int i = blockIdx.x * 32 + tx, j = blockIdx.y * BJ + ty;
+template <typename T, typename N, int BJ, bool DPG>
+__device__ __forceinline__ void vadv_columns(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
+                                             const View<const T> &ut, const View<const T> &uts, const View<T> &out,
+                                             const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
+                                             size_t cidx_ws, bool ws_domain) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = bx * 32 + tx, j = by * BJ + ty;
     const bool active = (i < g.I) && (j < g.J);
     const int ic = min(i, g.I - 1), jc = min(j, g.J - 1);
     const int iw = min(i, g.I);  // wcon is valid up to i = I (staggered)
     const int K = g.K;
-
-    // c' / d' addressing: element k of this column at base[k * cstride + cidx]
-    N *cpb, *dpb;
-    size_t cstride, cidx;
-    if (WS) {
-        cstride = (size_t)g.I * g.J;
-        cidx = (size_t)jc * g.I + ic;
-        cpb = ws;
-        dpb = ws + (size_t)K * cstride;  // used only when d' is not parked in the output
-    } else {
-        cstride = NT;
-        cidx = t;
-        cpb = reinterpret_cast<N *>(smem_raw);
-        dpb = cpb + (size_t)K * NT;
-    }
-    const bool wr = WS ? active : true;  // inactive lanes alias a real column in the workspace
+    const size_t cidx = ws_domain ? (size_t)jc * g.I + ic : cidx_ws;
+    const bool wr = ws_domain ? active : true;
 
     const T *pus = us.p + ic + (int64_t)jc * us.sj;
     const T *pup = up.p + ic + (int64_t)jc * up.sj;
@@ -226,13 +214,33 @@ __global__ void __launch_bounds__(32 * BJ)
     }
 }
 
+// Single domain: one CTA per 32 x BJ block of columns; WS selects a
+// domain-indexed global workspace over shared memory.
+template <typename T, typename N, int BJ, bool DPG, bool WS>
+__global__ void __launch_bounds__(32 * BJ)
+    vadv_kernel(const View<const T> us, const View<const T> wc, const View<const T> up, const View<const T> ut,
+                const View<const T> uts, const View<T> out, const VadvGeom g, N *__restrict__ ws) {
+    constexpr int NT = 32 * BJ;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    if (WS) {
+        const size_t cstride = (size_t)g.I * g.J;
+        vadv_columns<T, N, BJ, DPG>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws, ws + (size_t)g.K * cstride,
+                                    cstride, 0, true);
+    } else {
+        N *cpb = reinterpret_cast<N *>(smem_raw);
+        vadv_columns<T, N, BJ, DPG>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, cpb, cpb + (size_t)g.K * NT,
+                                    NT, t, false);
+    }
+}
+
 template <typename T, typename N>
-constexpr bool vadv_dp_global() {
+__host__ __device__ constexpr bool vadv_dp_global() {
     return sizeof(T) == sizeof(N);
 }
 
 template <typename T, typename N>
-constexpr size_t vadv_smem_per_col_level() {
+__host__ __device__ constexpr size_t vadv_smem_per_col_level() {
     return (vadv_dp_global<T, N>() ? 1 : 2) * sizeof(N);
 }
 

@@ -35,6 +35,16 @@ class GtbField(ctypes.Structure):
                 ("shape", ctypes.c_int64 * 3), ("strides", ctypes.c_int64 * 3), ("origin", ctypes.c_int64 * 3)]
 
 
+class GtbMember(ctypes.Structure):
+    _fields_ = [("in_", GtbField), ("coeff", GtbField), ("h", GtbField), ("wcon", GtbField), ("utens", GtbField),
+                ("utens_stage", GtbField), ("out", GtbField), ("domain", ctypes.c_int64 * 3)]
+
+
+class GtbBatchConfig(ctypes.Structure):
+    _fields_ = [("hdiff_tile", ctypes.c_int32), ("hdiff_levels", ctypes.c_int32), ("vadv_warps", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
 class GtbError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -44,7 +54,7 @@ class GtbError(RuntimeError):
 _lib = None
 EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_hdiff_adj", "gtb_vadv_adj",
            "gtb_vadv_adj_workspace_bytes", "gtb_halo_periodic", "gtb_halo_periodic_adj", "gtb_device_status",
-           "gtb_last_error", "gtb_version")
+           "gtb_batch_plan", "gtb_batch_run", "gtb_plan_info", "gtb_plan_destroy", "gtb_last_error", "gtb_version")
 GTB_ADJ_ACCUMULATE = 2
 
 
@@ -70,6 +80,14 @@ def lib() -> ctypes.CDLL:
         L.gtb_halo_periodic.argtypes = [P, ctypes.c_int, ctypes.c_int, i64p, vp]
         L.gtb_halo_periodic_adj.argtypes = [P, ctypes.c_int, ctypes.c_int, i64p, vp]
         for n in ("gtb_hdiff_adj", "gtb_vadv_adj", "gtb_halo_periodic", "gtb_halo_periodic_adj"):
+            getattr(L, n).restype = ctypes.c_int
+        L.gtb_batch_plan.argtypes = [ctypes.POINTER(GtbMember), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_uint, ctypes.POINTER(GtbBatchConfig),
+                                     ctypes.POINTER(ctypes.c_void_p)]
+        L.gtb_batch_run.argtypes = [ctypes.c_void_p, vp]
+        L.gtb_plan_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+        L.gtb_plan_destroy.argtypes = [ctypes.c_void_p]
+        for n in ("gtb_batch_plan", "gtb_batch_run", "gtb_plan_info", "gtb_plan_destroy"):
             getattr(L, n).restype = ctypes.c_int
         L.gtb_device_status.argtypes = [vp]
         L.gtb_last_error.restype = ctypes.c_char_p
@@ -294,3 +312,71 @@ def _as_field(x) -> GtbField:
     if isinstance(x, tuple) and len(x) == 2:
         return field(x[0], x[1])
     raise TypeError("expected a Storage, a (tensor, origin) pair or a GtbField")
+
+
+# ----------------------------------------------------------------- batched ensembles
+DEFAULT_BATCH_CONFIG = {"hdiff_tile": 0, "hdiff_levels": 8, "vadv_warps": 2, "ctas_per_sm": 0}
+MEMBER_FIELDS = ("in", "coeff", "h", "wcon", "utens", "utens_stage", "out")
+
+
+class BatchPlan:
+    """A validated ensemble captured into a CUDA graph (gtb_batch_plan).
+
+    ``members``: dicts with Storages under MEMBER_FIELDS and ``domain`` (I, J, K).
+    Each member runs h = hdiff(in, coeff) then out = vadv(h, wcon, h, utens,
+    utens_stage).  ``run()`` replays the graph on a stream; the plan keeps its
+    members' storages alive."""
+
+    def __init__(self, members, *, dtr_stage=3.0 / 20.0, beta_v=0.0, prec="native", literal=False, config=None):
+        self.members = members
+        arr = (GtbMember * len(members))()
+        for q, m in enumerate(members):
+            for name in MEMBER_FIELDS:
+                setattr(arr[q], "in_" if name == "in" else name, field(m[name]))
+            arr[q].domain[:] = [int(x) for x in m["domain"]]
+        self.config = dict(DEFAULT_BATCH_CONFIG, **(config or {}))
+        cfg = GtbBatchConfig(**self.config)
+        h = ctypes.c_void_p()
+        _check(lib().gtb_batch_plan(arr, len(members), float(dtr_stage), float(beta_v), PREC[prec],
+                                    1 if literal else 0, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib().gtb_batch_run(self._h, _stream(stream)))
+
+    def info(self) -> dict:
+        v = (ctypes.c_int64 * 6)()
+        _check(lib().gtb_plan_info(self._h, v))
+        return dict(zip(("hdiff_items", "vadv_items", "hdiff_grid", "vadv_grid", "points", "members"), list(v)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().gtb_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def member_storages(fields: dict, I: int, J: int, K: int, device="cuda") -> dict:
+    """Device storages of one ensemble member from its seeded draws (hdiff halo 2,
+    vadv halo 1, h interior, out with halo 1)."""
+    o2, o1 = (2, 2, 0), (1, 1, 0)
+    m = {"in": storage_from(fields["in"], o2, device=device), "coeff": storage_from(fields["coeff"], o2, device=device)}
+    for n in ("wcon", "utens", "utens_stage"):
+        m[n] = storage_from(fields[n], o1, device=device)
+    dt = torch.float32 if fields["in"].dtype == np.float32 else torch.float64
+    m["h"] = Storage(empty_storage(I, J, K, dtype=dt, device=device), (0, 0, 0))
+    m["out"] = Storage(empty_storage(I + 2, J + 2, K, dtype=dt, device=device, halo_i=1), o1)
+    m["domain"] = (I, J, K)
+    return m
+
+
+def run_member_single(m, *, dtr_stage=3.0 / 20.0, beta_v=0.0, prec="native", stream=None):
+    """The same member with the single-domain entry points (gtb_hdiff, gtb_vadv)."""
+    hdiff(m["in"], m["coeff"], m["h"], domain=m["domain"], stream=stream)
+    vadv(m["h"], m["wcon"], m["h"], m["utens"], m["utens_stage"], m["out"], dtr_stage=dtr_stage, beta_v=beta_v,
+         prec=prec, domain=m["domain"], stream=stream)
