@@ -15,6 +15,8 @@ elimination, back substitution) on another.  Prints ONE JSON line (rank 0).
   (from pinned host memory) and of its two outputs inside the timed region.
 * roofline: the dominant kernel's achieved rate against its binding peak.
 * cpu_baseline: the FP64 CPU oracle (single thread) on a bounded sample.
+* batched: the 48-member ensemble of uneven domains, autotuned plan replayed
+  from a CUDA graph vs the loop of single-domain launches.
 * adjoint_forward_ratio: backward / forward time of one chained step
   (periodic halo + hdiff + vadv) through the adjoint kernels.
 * --impl reference: the oracle itself as the reference arm.
@@ -351,6 +353,8 @@ def run_gtb(args):
             "adjoint_forward_ratio": None if adj is None else adj["ratio"], "adjoint": adj,
             "e2e": {"value": round(e2e_value, 1), "unit": "Mpoints/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}}
+    if rank == 0 and not args.no_batched:
+        line["batched"] = batched_compare()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -418,6 +422,50 @@ def adjoint_ratio(gtb, f, sets, reps=50):
             "workload": "one chained step at 256x256x80 FP64 (halo refresh + hdiff + vadv vs their adjoints)"}
 
 
+def batched_compare(reps=20):
+    """The batched form: a 48-member ensemble of uneven domains (I=J in
+    {48..384}, K in {40, 60, 80, 137}, seed-fixed), FP32 storage with
+    double-float vadv, each member hdiff then vadv (h fed to vadv as u_stage and
+    u_pos).  Graph replay of the autotuned plan vs a loop of the 96
+    single-domain launches, both timed with CUDA events after warm-up."""
+    import torch
+    from paper_2311_08322_b300 import autotune, gtb, inputs
+    shapes = inputs.ensemble_shapes(48, 0)
+    members = []
+    for q, (I_, J_, K_) in enumerate(shapes):
+        f = inputs.hdiff_vadv(I_, J_, K_, seed=1 + q)
+        f = {k: v.astype(np.float32) for k, v in f.items()}
+        members.append(gtb.member_storages(f, I_, J_, K_))
+        del f
+    cfg, log = autotune.tune(members, prec="df", reps=3)
+    plan = gtb.BatchPlan(members, prec="df", config=cfg)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    g_ms = timed(lambda: plan.run(stream))
+    l_ms = timed(lambda: [gtb.run_member_single(m, prec="df", stream=stream) for m in members])
+    gtb.device_status()
+    info = plan.info()
+    pts = info["points"]
+    plan.close()
+    return {"workload": "48-member ensemble, I=J in {48,96,128,192,256,384}, K in {40,60,80,137}, FP32 storage, "
+                        "double-float vadv", "points": pts, "graph_ms": round(g_ms, 4), "loop_ms": round(l_ms, 4),
+            "speedup_vs_loop": round(l_ms / g_ms, 3), "mpoints_s": round(pts / (g_ms / 1e3) / 1e6, 1),
+            "config": cfg, "autotune_cached": log.get("cached"), "launches_graph": 2,
+            "launches_loop": 2 * len(members)}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,6 +476,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
