@@ -15,6 +15,8 @@ elimination, back substitution) on another.  Prints ONE JSON line (rank 0).
   (from pinned host memory) and of its two outputs inside the timed region.
 * roofline: the dominant kernel's achieved rate against its binding peak.
 * cpu_baseline: the FP64 CPU oracle (single thread) on a bounded sample.
+* precision: FP32 storage at 512x512x80 (binary32 hdiff; vadv in binary32,
+  binary64 and double-float column arithmetic) beside the FP64 path there.
 * batched: the 48-member ensemble of uneven domains, autotuned plan replayed
   from a CUDA graph vs the loop of single-domain launches.
 * adjoint_forward_ratio: backward / forward time of one chained step
@@ -353,6 +355,8 @@ def run_gtb(args):
             "adjoint_forward_ratio": None if adj is None else adj["ratio"], "adjoint": adj,
             "e2e": {"value": round(e2e_value, 1), "unit": "Mpoints/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}}
+    if rank == 0 and not args.no_precision:
+        line["precision"] = precision_compare()
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_compare()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -466,6 +470,67 @@ def batched_compare(reps=20):
             "launches_loop": 2 * len(members)}
 
 
+def precision_compare(reps=20):
+    """The precision form at 512x512x80 (same generators): FP32 storage with binary32
+    hdiff and vadv in its three column-arithmetic forms (binary32, binary64 on the
+    FP64 pipe, double-float on the FP32 pipe), beside the FP64 path at the same size
+    on the same GPU.  Two input sets alternate (each larger than L2).  The error of
+    each form against the FP64 oracle is measured by tests/test_gpu_precision.py."""
+    import torch
+    from paper_2311_08322_b300 import gtb, inputs
+    I3, J3, K3 = 512, 512, 80
+    f = inputs.hdiff_vadv(I3, J3, K3, seed=0)
+    o2, o1 = (2, 2, 0), (1, 1, 0)
+
+    def make(dt):
+        sets = []
+        for _ in range(2):
+            st = {"in": gtb.storage_from(f["in"].astype(dt), o2), "coeff": gtb.storage_from(f["coeff"].astype(dt), o2),
+                  "hout": gtb.storage_from(np.zeros(f["coeff"].shape, dt), o2),
+                  "vout": gtb.storage_from(np.zeros(f["utens"].shape, dt), o1)}
+            for n in VADV_NAMES:
+                st[n] = gtb.storage_from(f[n].astype(dt), o1)
+            sets.append(st)
+        return sets
+
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for q in range(4):
+            fn(q)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for q in range(reps):
+            fn(q)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    pts = I3 * J3 * K3
+    res = {"workload": "hdiff + vadv at 512x512x80 (same generators as the FP64 path)"}
+    for name, dt in (("fp64", np.float64), ("fp32", np.float32)):
+        sets = make(dt)
+        es = 8 if dt == np.float64 else 4
+        r = {"hdiff_ms": timed(lambda q: gtb.hdiff(sets[q % 2]["in"], sets[q % 2]["coeff"], sets[q % 2]["hout"]))}
+        precs = ("native",) if dt == np.float64 else ("native", "f64", "df")
+        for pr in precs:
+            r[f"vadv_{pr}_ms"] = timed(lambda q: gtb.vadv(*[sets[q % 2][n] for n in VADV_NAMES], sets[q % 2]["vout"],
+                                                          prec=pr))
+        r["hdiff_gbs"] = round(hdiff_bytes(I3, J3, K3, es) / (r["hdiff_ms"] / 1e3) / 1e9, 1)
+        for pr in precs:
+            r[f"vadv_{pr}_gbs"] = round(vadv_bytes(I3, J3, K3, es) / (r[f"vadv_{pr}_ms"] / 1e3) / 1e9, 1)
+        best_v = min(r[f"vadv_{pr}_ms"] for pr in precs if pr != "native" or dt == np.float64)
+        r["step_mpoints_s"] = round(pts / ((r["hdiff_ms"] + best_v) / 1e3) / 1e6, 1)
+        res[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+        del sets
+        torch.cuda.empty_cache()
+    gtb.device_status()
+    res["note"] = ("fp32 step uses the fastest vadv form that meets the 1e-5 bound (f64 or df); all-binary32 vadv "
+                   "does not meet it on ill-conditioned columns")
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,6 +542,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
