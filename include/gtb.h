@@ -211,7 +211,8 @@ typedef struct gtb_member {
 } gtb_member;
 
 typedef struct gtb_batch_config {
-    int32_t hdiff_tile;    /* 0: 4 warps x 16 rows per tile, 1: 2 warps x 16 rows */
+    int32_t hdiff_tile;    /* 0: the single-domain tile (binary64: 4 warps x 16 rows, binary32:
+                              8 warps x 8 rows), 1: the other of the two splits */
     int32_t hdiff_levels;  /* K levels per hdiff work item (the K-blocking); <= 0: whole columns */
     int32_t vadv_warps;    /* warps (32 columns each) per vadv work item: 1, 2 or 4 */
     int32_t ctas_per_sm;   /* resident persistent CTAs per SM per stage; <= 0: as many as fit */

@@ -183,11 +183,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // ------------------------------------------------------------------ hdiff
 template <typename T>
 struct HdiffCfg;
+// Measured on B300 (row loop fully unrolled): binary64 fixed point runs best
+// with 4 warps of 16 rows, binary32 with 8 warps of 8 rows (more resident
+// warps to cover the latency chain of each row).
 template <> struct HdiffCfg<double> {  // 64 x 64 tile, 4 warps of 16 rows, 2 columns per lane
     static constexpr int CPL = 2, W = 4, R = 16, STAGES = 2;
 };
-template <> struct HdiffCfg<float> {   // 128 x 64 tile, 4 warps of 16 rows, 4 columns per lane
-    static constexpr int CPL = 4, W = 4, R = 16, STAGES = 2;
+template <> struct HdiffCfg<float> {   // 128 x 64 tile, 8 warps of 8 rows, 4 columns per lane
+    static constexpr int CPL = 4, W = 8, R = 8, STAGES = 2;
 };
 
 template <typename T, bool TMA>
@@ -739,16 +742,21 @@ static void plan_free(gtb_plan *p) {
     delete p;
 }
 
-// hdiff tile variants of the batched form: 0 = 4 warps x 16 rows, 1 = 2 warps x 16 rows
-template <typename T>
+// hdiff tile variants of the batched form: variant 0 is the single-domain
+// configuration (so batched and single results agree bit for bit), variant 1
+// the other warp/row split.
+template <typename T, int V>
 struct BatchHCfg {
-    static constexpr int CPL = sizeof(T) == 8 ? 2 : 4, R = 16, STAGES = 2;
+    static constexpr int CPL = HdiffCfg<T>::CPL, STAGES = 2;
+    static constexpr int W = V == 0 ? HdiffCfg<T>::W : (HdiffCfg<T>::W == 4 ? 8 : 4);
+    static constexpr int R = V == 0 ? HdiffCfg<T>::R : (HdiffCfg<T>::R == 16 ? 8 : 16);
 };
 
-template <typename T, int W>
+template <typename T, int V>
 static int batch_hdiff_launch_info(int ctas_per_sm, int *slots, void (**kern)(const CUtensorMap *, const BatchHdiffMember<T> *, int, int, int *), int *smem) {
-    using C = BatchHCfg<T>;
+    using C = BatchHCfg<T, V>;
     constexpr bool FIXED = sizeof(T) == 8;
+    constexpr int W = C::W;
     auto k = hdiff_batch_kernel<T, C::CPL, W, C::R, C::STAGES, FIXED>;
     *smem = hdiff_rs_smem_bytes<T, C::CPL, W, C::R, C::STAGES>();
     if (prepare_kernel(k, *smem) != cudaSuccess) return launch_status("batch: hdiff shared-memory attribute");
@@ -769,9 +777,10 @@ static int batch_vadv_launch_info(int ctas_per_sm, int *slots, void (**kern)(con
     return GTB_OK;
 }
 
-template <typename T, typename N, int W, int BJ>
+template <typename T, typename N, int V, int BJ>
 static int build_plan(const gtb_member *mem, int n, double dtr, double beta, unsigned flags, gtb_plan *P) {
-    using C = BatchHCfg<T>;
+    using C = BatchHCfg<T, V>;
+    constexpr int W = C::W;
     using Tile = RsTile<T, C::CPL, W, C::R>;
     const size_t es = sizeof(T);
     constexpr int kAlign = 16 / (int)sizeof(T);
@@ -845,7 +854,7 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
     void (*hk)(const CUtensorMap *, const BatchHdiffMember<T> *, int, int, int *);
     void (*vk)(const BatchVadvMember<T> *, int, int, int *, N *, size_t, int);
     int hslots, vslots, hsmem, rc;
-    if ((rc = batch_hdiff_launch_info<T, W>(P->cfg.ctas_per_sm, &hslots, &hk, &hsmem))) return rc;
+    if ((rc = batch_hdiff_launch_info<T, V>(P->cfg.ctas_per_sm, &hslots, &hk, &hsmem))) return rc;
     if ((rc = batch_vadv_launch_info<T, N, BJ>(P->cfg.ctas_per_sm, &vslots, &vk))) return rc;
     P->h_items = hitems, P->v_items = vitems;
     P->h_grid = std::max(1, std::min(hitems, hslots));
@@ -880,19 +889,19 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
     return GTB_OK;
 }
 
-template <typename T, typename N, int W>
+template <typename T, typename N, int V>
 static int build_plan_bj(const gtb_member *mem, int n, double dtr, double beta, unsigned flags, gtb_plan *P) {
     switch (P->cfg.vadv_warps) {
-    case 1: return build_plan<T, N, W, 1>(mem, n, dtr, beta, flags, P);
-    case 4: return build_plan<T, N, W, 4>(mem, n, dtr, beta, flags, P);
-    default: return build_plan<T, N, W, 2>(mem, n, dtr, beta, flags, P);
+    case 1: return build_plan<T, N, V, 1>(mem, n, dtr, beta, flags, P);
+    case 4: return build_plan<T, N, V, 4>(mem, n, dtr, beta, flags, P);
+    default: return build_plan<T, N, V, 2>(mem, n, dtr, beta, flags, P);
     }
 }
 
 template <typename T, typename N>
 static int build_plan_w(const gtb_member *mem, int n, double dtr, double beta, unsigned flags, gtb_plan *P) {
-    return P->cfg.hdiff_tile == 1 ? build_plan_bj<T, N, 2>(mem, n, dtr, beta, flags, P)
-                                  : build_plan_bj<T, N, 4>(mem, n, dtr, beta, flags, P);
+    return P->cfg.hdiff_tile == 1 ? build_plan_bj<T, N, 1>(mem, n, dtr, beta, flags, P)
+                                  : build_plan_bj<T, N, 0>(mem, n, dtr, beta, flags, P);
 }
 
 }  // namespace gtb

@@ -132,14 +132,16 @@ __device__ __forceinline__ df two_prod(float a, float b) {
     return {p, __fmaf_rn(a, b, -p)};
 }
 
-// Accurate double-word addition (JMP17 Alg. 6): relative error <= 3u^2 + 13u^3.
+// Double-word addition in the "sloppy" form (JMP17 Alg. 5): TwoSum of the high
+// parts, the low parts added, one renormalisation.  Its absolute error is
+// about 2u^2 (|x| + |y|) (u = 2^-24): like a binary64-style operation on the
+// operands' magnitude, ample for the FP32-storage bound it serves (the
+// column solve needs ~34 significant bits there), at 11 flops instead of 20.
 __device__ __forceinline__ df operator+(df x, df y) {
-    df s = two_sum(x.hi, y.hi);
-    const df t = two_sum(x.lo, y.lo);
-    float c = __fadd_rn(s.lo, t.hi);
-    df v = fast_two_sum(s.hi, c);
-    const float w = __fadd_rn(t.lo, v.lo);
-    return fast_two_sum(v.hi, w);
+    const df s = two_sum(x.hi, y.hi);
+    const float v = __fadd_rn(x.lo, y.lo);
+    const float w = __fadd_rn(s.lo, v);
+    return fast_two_sum(s.hi, w);
 }
 
 __device__ __forceinline__ df operator-(df x) { return {-x.hi, -x.lo}; }
@@ -169,13 +171,18 @@ __device__ __forceinline__ df operator*(df x, df y) {
     return fast_two_sum(c.hi, cl3);
 }
 
-// Reciprocal of a double-word: a binary32 reciprocal th of y.hi refined by one
-// double-word Newton step, q = th + th (1 - y th); relative error ~2^-46.
+// Reciprocal of a double-word: th = 1/y.hi in binary32, refined by one Newton
+// step whose residual e = (1 - y.hi*th) - y.lo*th is formed with FMAs (the
+// first product-difference is exact to within one rounding of a value of
+// size ~2^-24); result th + th*e as a double-word, relative error ~2^-46.
 __device__ __forceinline__ df recip(df y) {
     const float th = __frcp_rn(y.hi);
-    const df yt = y * th;
-    const df r = df{1.0f, 0.0f} - yt;
-    return df_from(th) + r * th;
+    float e = __fmaf_rn(-y.hi, th, 1.0f);
+    e = __fmaf_rn(-y.lo, th, e);
+    return fast_two_sum(th, __fmul_rn(th, e));
 }
+
+// Exact sum / difference of two binary32 values as a double-word (TwoSum).
+__device__ __forceinline__ df df_add2(float a, float b) { return two_sum(a, b); }
 
 }  // namespace gtb

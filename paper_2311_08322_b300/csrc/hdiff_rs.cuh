@@ -80,6 +80,16 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
     const int ci0 = lane * CPL;
     auto at = [&](int ci, int cj) -> T { return S[(cj + 2) * BX + ci + 2 + xs]; };
     auto ptr = [&](int ci, int cj) -> const T * { return S + (cj + 2) * BX + ci + 2 + xs; };
+    // this lane's CPL values of row cj: one 16-byte shared load when the box column is aligned
+    const bool vsm = ((2 + xs) % CPL) == 0;
+    auto row = [&](int cj, T (&v)[CPL]) {
+        if (vsm) {
+            load_vec<T, CPL>(ptr(ci0, cj), v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) v[q] = at(ci0 + q, cj);
+        }
+    };
 
     // ---- the two columns outside the warp: i = -1 (lanes 0-15) and i = TI (16-31)
     const int side = lane >> 4, er = lane & 15;
@@ -99,24 +109,43 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
     V xa[CPL], xb[CPL], xc[CPL];  // X at rows t-1, t, t+1
     V lp[CPL], fyp[CPL];          // lap(t-1), fy(t-2)
     V nbL_prev = V(0), nbR_prev = V(0);  // X(c-1), X(c+1) at row t-1 for the outer columns
+    {
+        T ra[CPL], rb[CPL], rc[CPL];
+        row(cj0 - 2, ra);
+        row(cj0 - 1, rb);
+        row(cj0, rc);
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) {
-        xa[q] = pol.conv(at(ci0 + q, cj0 - 2));
-        xb[q] = pol.conv(at(ci0 + q, cj0 - 1));
-        xc[q] = pol.conv(at(ci0 + q, cj0));
-        lp[q] = V(0), fyp[q] = V(0);
+        for (int q = 0; q < CPL; ++q) {
+            xa[q] = pol.conv(ra[q]);
+            xb[q] = pol.conv(rb[q]);
+            xc[q] = pol.conv(rc[q]);
+            lp[q] = V(0), fyp[q] = V(0);
+        }
     }
-    // coeff ring: at the top of iteration t, cf0/cf1/cf2 hold rows t-1, t, t+1
-    auto load_cf = [&](int row, T (&v)[CPL]) {
+    // coeff ring: at the top of iteration t, cf0 .. cf4 hold rows t-1 .. t+3 (16-byte loads when aligned)
+    auto load_cf = [&](int rw, T (&v)[CPL]) {
+        if (rw >= 0 && rw < nrows) {
+            const T *c = cfp + (int64_t)(cj0 + rw) * cf_sj;
+            if (vec_ok && ncols == CPL) {
+                load_vec<T, CPL>(c, v);
+                return;
+            }
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) v[q] = (row >= 0 && row < nrows && q < ncols) ? cfp[(int64_t)(cj0 + row) * cf_sj + q] : T(0);
+            for (int q = 0; q < CPL; ++q) v[q] = q < ncols ? c[q] : T(0);
+        } else {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) v[q] = T(0);
+        }
     };
-    T cf0[CPL], cf1[CPL], cf2[CPL];
+    T cf0[CPL], cf1[CPL], cf2[CPL], cf3[CPL], cf4[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; ++q) cf0[q] = T(0), cf1[q] = T(0);
     load_cf(0, cf2);
-    // iteration t computes lap(row t) for t = -1 .. R and emits out(row t-1) for t >= 1
-#pragma unroll 1
+    load_cf(1, cf3);
+    load_cf(2, cf4);
+    // iteration t computes lap(row t) for t = -1 .. R and emits out(row t-1) for t >= 1;
+    // fully unrolled, so the rolling rows need no register moves
+#pragma unroll
     for (int t = -1; t <= R; ++t) {
         // X neighbours in i at row t
         V up = __shfl_up_sync(0xffffffffu, xb[CPL - 1], 1);
@@ -153,12 +182,13 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
                 V fxw = __shfl_up_sync(0xffffffffu, fx[CPL - 1], 1);
                 if (lane == 0)  // fx(i = -1) = lap(0) - lap(-1)
                     fxw = pol.limit(lp[0] - el, pol.grad(xa[0], nbL_prev, ptr(0, cj0 + j), ptr(-1, cj0 + j)));
-                T r[CPL];
+                T r[CPL], xin[CPL];
+                row(cj0 + j, xin);
 #pragma unroll
                 for (int q = 0; q < CPL; ++q) {
                     const V fwq = (q == 0) ? fxw : fx[q - 1];
                     const V D = (fx[q] - fwq) + (fyc[q] - fyp[q]);
-                    r[q] = pol.out(at(ci0 + q, cj0 + j), cf0[q], D);
+                    r[q] = pol.out(xin[q], cf0[q], D);
                 }
                 if (j < nrows) {
                     T *o = op + (int64_t)(cj0 + j) * out_sj;
@@ -174,17 +204,19 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
 #pragma unroll
             for (int q = 0; q < CPL; ++q) fyp[q] = fyc[q];
         }
+        T rn[CPL];
+        if (t + 2 <= R + 1) row(cj0 + t + 2, rn);
 #pragma unroll
         for (int q = 0; q < CPL; ++q) {
             lp[q] = lc[q];
             xa[q] = xb[q];
             xb[q] = xc[q];
-            if (t + 2 <= R + 1) xc[q] = pol.conv(at(ci0 + q, cj0 + t + 2));
+            if (t + 2 <= R + 1) xc[q] = pol.conv(rn[q]);
         }
         nbL_prev = up, nbR_prev = dn;
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) cf0[q] = cf1[q], cf1[q] = cf2[q];
-        load_cf(t + 2, cf2);
+        for (int q = 0; q < CPL; ++q) cf0[q] = cf1[q], cf1[q] = cf2[q], cf2[q] = cf3[q], cf3[q] = cf4[q];
+        load_cf(t + 4, cf4);
     }
 }
 

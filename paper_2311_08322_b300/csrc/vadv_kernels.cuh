@@ -49,6 +49,16 @@ template <> __device__ __forceinline__ float to_store<float, float>(float x) { r
 template <> __device__ __forceinline__ float to_store<float, double>(double x) { return __double2float_rn(x); }
 template <> __device__ __forceinline__ float to_store<float, df>(df x) { return df_to_float(x); }
 
+// Mixed operations with a storage value b (binary32 storage and double-float
+// arithmetic use the cheaper double-word x word forms; other pairs convert).
+template <typename N, typename T> __device__ __forceinline__ N mulx(N a, T b) { return a * to_num<N, T>(b); }
+template <> __device__ __forceinline__ df mulx<df, float>(df a, float b) { return a * b; }
+template <typename N, typename T> __device__ __forceinline__ N addx(N a, T b) { return a + to_num<N, T>(b); }
+template <> __device__ __forceinline__ df addx<df, float>(df a, float b) { return a + b; }
+// a + b of two storage values (exact for double-float)
+template <typename N, typename T> __device__ __forceinline__ N add2(T a, T b) { return to_num<N, T>(a) + to_num<N, T>(b); }
+template <> __device__ __forceinline__ df add2<df, float>(float a, float b) { return df_add2(a, b); }
+
 // face-velocity sum s_m of level m for this lane's column (all lanes take part
 // in the shuffle, so it is called warp-uniformly)
 template <typename T, typename N>
@@ -102,6 +112,11 @@ template <>
 __device__ __forceinline__ double coef<double>(double s, double k, int n) {
     return n ? scale_pow2(s, k, n) : k * s;
 }
+// double-float: k = -2^n is exact in binary32, so scaling both parts is exact
+template <>
+__device__ __forceinline__ df coef<df>(df s, df k, int n) {
+    return n ? df{__fmul_rn(s.hi, k.hi), __fmul_rn(s.lo, k.hi)} : k * s;
+}
 
 // Where the forward sweep keeps its eliminated coefficients:
 //  * shared memory, [K][block columns]: the K x 32 x BJ state caps the
@@ -153,7 +168,7 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
     GTB_LOAD(L0, 0);
     GTB_LOAD(L1, 1);
 
-    N us_cur = to_num<N, T>(pus[0]);
+    T us_cur = pus[0];
     N dm = zero;                    // u_stage_{k-1} - u_stage_k
     N a_cur = zero, as_cur = zero;  // a_0 = as_0 = 0
     N cp_prev = zero, dp_prev = zero;
@@ -168,17 +183,16 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
             } else {
                 T hi = __shfl_down_sync(0xffffffffu, L0.w, 1);
                 if (last_lane) hi = L0.w1;
-                s = to_num<N, T>(L0.w) + to_num<N, T>(hi);
+                s = add2<N, T>(L0.w, hi);
             }
             a_next = coef<N>(s, ka, kexp);
             as_next = g.sym ? a_next : kas * s;
-            const N us_next = to_num<N, T>(L0.us1);
-            dpl = us_next - us_cur;  // u_stage_{k+1} - u_stage_k
-            us_cur = us_next;
+            dpl = add2<N, T>(L0.us1, -us_cur);  // u_stage_{k+1} - u_stage_k
+            us_cur = L0.us1;
         }
         const N b = (dtr - a_cur) + a_next;  // dtr - a_k - c_k with c_k = -a_{k+1}
-        N d = dtr * to_num<N, T>(L0.up) + to_num<N, T>(L0.ut);
-        d = d + to_num<N, T>(L0.uts);
+        N d = addx<N, T>(mulx<N, T>(dtr, L0.up), L0.ut);
+        d = addx<N, T>(d, L0.uts);
         if (k > 0) d = d - as_cur * dm;
         if (has_next) d = d + as_next * dpl;  // - cs_k (u_{k+1} - u_k), cs_k = -as_{k+1}
         N p = b, num = d;
@@ -204,12 +218,12 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
 
     // backward substitution and output, utens_stage_out = dtr (x - u_pos)
     N x = dp_prev;
-    if (active) po[(int64_t)(K - 1) * out.sk] = to_store<T, N>(dtr * (x - to_num<N, T>(pup[(int64_t)(K - 1) * up.sk])));
+    if (active) po[(int64_t)(K - 1) * out.sk] = to_store<T, N>(dtr * addx<N, T>(x, -pup[(int64_t)(K - 1) * up.sk]));
 #pragma unroll 4
     for (int k = K - 2; k >= 0; --k) {
         const N dk = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : dpb[(size_t)k * cstride + cidx];
         x = dk - cpb[(size_t)k * cstride + cidx] * x;
-        const N o = dtr * (x - to_num<N, T>(pup[(int64_t)k * up.sk]));
+        const N o = dtr * addx<N, T>(x, -pup[(int64_t)k * up.sk]);
         if (active) po[(int64_t)k * out.sk] = to_store<T, N>(o);
     }
 }
