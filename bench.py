@@ -149,6 +149,21 @@ class ClockSampler:
                 "power_w_max": max(float(r[2]) for r in rows) if rows else None}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest value of x over all ranks (the slowest rank's time)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpoints(world: int, points_per_rank: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank's points over the slowest rank's time."""
+    return world * points_per_rank * steps / (max_ms / 1e3) / 1e6
+
+
 def oracle_step(f, jrows=None):
     """One oracle hdiff + vadv pass (optionally on the first `jrows` rows of J); returns points."""
     import oracle
@@ -279,11 +294,8 @@ def run_gtb(args):
     h_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     v_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
     adj = adjoint_ratio(gtb, f, sets) if rank == 0 and not args.no_adjoint else None
-    if world > 1:
-        t = torch.tensor([el_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
-    value = world * POINTS * args.steps / (el_ms / 1e3) / 1e6
+    el_ms = max_over_ranks(el_ms, dist if world > 1 else None, "cuda")
+    value = whole_job_mpoints(world, POINTS, args.steps, el_ms)
 
     # e2e through the C ABI: pinned host inputs -> device, two kernels, outputs -> host
     host = {n: torch.from_numpy(f[n]).pin_memory() for n in ("in", "coeff", *VADV_NAMES)}
@@ -314,11 +326,8 @@ def run_gtb(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * POINTS * args.e2e_steps / (e2e_ms / 1e3) / 1e6
+    e2e_ms = max_over_ranks(e2e_ms, dist if world > 1 else None, "cuda")
+    e2e_value = whole_job_mpoints(world, POINTS, args.e2e_steps, e2e_ms)
 
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6400.0))
