@@ -189,6 +189,36 @@ int gtb_halo_periodic(const gtb_field *f, int hi, int hj, const int64_t *domain,
 int gtb_halo_periodic_adj(const gtb_field *f, int hi, int hj, const int64_t *domain, void *stream);
 
 /*
+ * gtb_hdiff_vadv -- the two stencils chained as one computation (paper
+ * Sec. 3.1; Sec. 2.2 leaves the backend free to fuse the computations it
+ * runs):
+ *   h               = hdiff(in, coeff)                          (as gtb_hdiff)
+ *   utens_stage_out = vadv(u_stage = h, wcon, u_pos = h, utens, utens_stage)
+ * in one kernel; h is formed level by level on chip and never written to
+ * memory.  The back substitution runs on z = x - h (the same unknowns,
+ * utens_stage_out = dtr_stage z), so results agree with gtb_hdiff followed by
+ * gtb_vadv to rounding, not bit for bit.
+ * Fields: in needs 2 halo points in I and J (as gtb_hdiff), wcon one point
+ * above I unless GTB_WCON_LITERAL (as gtb_vadv); coeff, utens, utens_stage
+ * and utens_stage_out cover the domain.  utens_stage_out may be the very same
+ * view as utens_stage (in place); any other overlap of the output with an
+ * input is GTB_ERR_ALIAS.  dtr_stage, beta_v, prec and flags as gtb_vadv.
+ * workspace: REQUIRED caller-owned device scratch of at least
+ * gtb_hdiff_vadv_workspace_bytes() bytes (c', and e when it cannot be parked
+ * in the output), 16-byte aligned, overlapping no field; NULL or too small is
+ * GTB_ERR_ARG.  No K limit beyond the workspace size.
+ */
+int gtb_hdiff_vadv(const gtb_field *in, const gtb_field *coeff, const gtb_field *wcon,
+                   const gtb_field *utens, const gtb_field *utens_stage,
+                   const gtb_field *utens_stage_out, double dtr_stage, double beta_v,
+                   int prec, unsigned flags, const int64_t *domain,
+                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* Workspace bytes of gtb_hdiff_vadv (equal to gtb_vadv_workspace_bytes for
+ * the same dtype, prec and domain); 0 for bad arguments. */
+size_t gtb_hdiff_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain);
+
+/*
  * Batched ensembles of uneven domains (the paper's stencils over many
  * independent members, e.g. an ensemble forecast).  Each member runs
  *   h   = hdiff(in, coeff)                         (gtb_hdiff on its domain)

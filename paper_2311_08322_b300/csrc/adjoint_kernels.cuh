@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(32 * BJ)
     const int i = blockIdx.x * 32 + tx, j = blockIdx.y * BJ + ty;
     const bool active = (i < g.I) && (j < g.J);
     const int ic = min(i, g.I - 1), jc = min(j, g.J - 1);
-    const int iw = min(i, g.I);
+    const int ilim = g.literal ? g.I - 1 : g.I;  // last wcon column read (I-staggered unless literal)
+    const int iw = min(i, ilim);
     const int K = g.K;
 
     N *cpb, *vb;
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(32 * BJ)
     const bool wr = WS ? active : true;
 
     const T *pw = wc.p + iw + (int64_t)jc * wc.sj;
-    const T *pw1 = wc.p + min(i + 1, g.I) + (int64_t)jc * wc.sj;
+    const T *pw1 = wc.p + min(i + 1, ilim) + (int64_t)jc * wc.sj;
     const T *py = yb.p + ic + (int64_t)jc * yb.sj;
     const bool last_lane = (tx == 31);
     const bool lit = g.literal != 0;

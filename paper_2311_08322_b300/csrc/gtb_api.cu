@@ -21,6 +21,7 @@
 #include "vadv_kernels.cuh"
 #include "adjoint_kernels.cuh"
 #include "batch_kernels.cuh"
+#include "fused_kernels.cuh"
 
 namespace gtb {
 
@@ -180,6 +181,24 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// The column coefficients of vadv for beta_v and the face-velocity mode:
+// a_k = bp * (-w_k/2) with w_k = s_k/2 (I-face average) or s_k (literal), so
+// a_k = ka s_k with ka = (-bp/4) or (-bp/2); the explicit weights use bm.
+static VadvGeom make_vadv_geom(const int64_t dom[3], bool literal, double dtr_stage, double beta_v) {
+    VadvGeom g{};
+    g.I = (int)dom[0], g.J = (int)dom[1], g.K = (int)dom[2];
+    g.literal = literal ? 1 : 0;
+    const double bp = 0.5 * (1.0 + beta_v), bm = 0.5 * (1.0 - beta_v);
+    g.sym = (bp == bm) ? 1 : 0;
+    g.dtr = dtr_stage;
+    g.ka = (literal ? -0.5 : -0.25) * bp;
+    g.kas = (literal ? -0.5 : -0.25) * bm;
+    int n = 0;
+    const double m = std::frexp(-g.ka, &n);  // -ka = m 2^n, m in [0.5, 1)
+    g.ka_pow2 = (m == 0.5 && n - 1 < 0 && n - 1 > -64) ? n - 1 : 0;
+    return g;
+}
+
 // ------------------------------------------------------------------ hdiff
 template <typename T>
 struct HdiffCfg;
@@ -219,6 +238,40 @@ static int launch_hdiff_t(const CUtensorMap &map, const View<T> &in, const View<
     return launch_status("hdiff launch");
 }
 
+// TMA descriptor of hdiff's input for a (bx x by x 1) box whose column 0 is
+// domain i = -2 rounded down to 16 bytes: storage base rounded down to 16 B,
+// pitches multiples of 16 B.  Sets g.X0/Y0/Z0 and the alignment shift g.xs;
+// false (g.xs = 0) when the layout or the driver rules TMA out.
+template <typename T>
+static bool encode_in_map(const gtb_field *fin, int bx, int by, HdiffGeom &g, CUtensorMap &map) {
+    const size_t es = sizeof(T);
+    const uintptr_t base = reinterpret_cast<uintptr_t>(fin->ptr);
+    const uintptr_t abase = base & ~uintptr_t(15);
+    const int shift = (int)((base - abase) / es);
+    constexpr int kAlign = 16 / (int)sizeof(T);
+    bool tma = encode_fn() != nullptr && (fin->strides[1] * es) % 16 == 0 && (fin->strides[2] * es) % 16 == 0 &&
+               fin->strides[2] * es < (1ull << 40) && fin->shape[0] + shift < (1ll << 31);
+    memset(&map, 0, sizeof(map));
+    if (tma) {
+        const int xraw = (int)fin->origin[0] - 2 + shift;
+        g.xs = xraw % kAlign;
+        g.X0 = xraw - g.xs;
+        g.Y0 = (int)fin->origin[1] - 2;
+        g.Z0 = (int)fin->origin[2];
+        cuuint64_t gdim[3] = {(cuuint64_t)(fin->shape[0] + shift), (cuuint64_t)fin->shape[1], (cuuint64_t)fin->shape[2]};
+        cuuint64_t gstride[2] = {(cuuint64_t)(fin->strides[1] * es), (cuuint64_t)(fin->strides[2] * es)};
+        cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = encode_fn()(&map, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                 3, reinterpret_cast<void *>(abase), gdim, gstride, box, estr,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) tma = false;
+    }
+    if (!tma) g.xs = 0;
+    return tma;
+}
+
 template <typename T>
 static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field *fout, const int64_t dom[3],
                      cudaStream_t st) {
@@ -231,33 +284,9 @@ static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field
     g.tiles_j = (g.J + Tile::TJ - 1) / Tile::TJ;
     g.n_tiles = g.tiles_i * g.tiles_j;
 
-    // TMA path: storage base rounded down to 16 B, pitches multiples of 16 B
-    const size_t es = sizeof(T);
-    const uintptr_t base = reinterpret_cast<uintptr_t>(fin->ptr);
-    const uintptr_t abase = base & ~uintptr_t(15);
-    const int shift = (int)((base - abase) / es);
-    constexpr int kAlign = 16 / (int)sizeof(T);
-    bool tma = encode_fn() != nullptr && (fin->strides[1] * es) % 16 == 0 && (fin->strides[2] * es) % 16 == 0 &&
-               fin->strides[2] * es < (1ull << 40) && fin->shape[0] + shift < (1ll << 31);
     CUtensorMap map;
-    memset(&map, 0, sizeof(map));
-    if (tma) {
-        const int xraw = (int)fin->origin[0] - 2 + shift;
-        g.xs = xraw % kAlign;
-        g.X0 = xraw - g.xs;
-        g.Y0 = (int)fin->origin[1] - 2;
-        g.Z0 = (int)fin->origin[2];
-        cuuint64_t gdim[3] = {(cuuint64_t)(fin->shape[0] + shift), (cuuint64_t)fin->shape[1], (cuuint64_t)fin->shape[2]};
-        cuuint64_t gstride[2] = {(cuuint64_t)(fin->strides[1] * es), (cuuint64_t)(fin->strides[2] * es)};
-        cuuint32_t box[3] = {(cuuint32_t)Tile::BX, (cuuint32_t)Tile::BY, 1};
-        cuuint32_t estr[3] = {1, 1, 1};
-        CUresult r = encode_fn()(&map, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                                 3, reinterpret_cast<void *>(abase), gdim, gstride, box, estr,
-                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) tma = false;
-    }
-    if (!tma) g.xs = 0;
+    const bool tma = encode_in_map<T>(fin, Tile::BX, Tile::BY, g, map);
+    const size_t es = sizeof(T);
     auto aligned = [&](const View<T> &v) {
         return reinterpret_cast<uintptr_t>(v.p) % 16 == 0 && (v.sj * es) % 16 == 0 && (v.sk * es) % 16 == 0;
     };
@@ -378,6 +407,39 @@ static int run_halo(const gtb_field *f, int hi, int hj, const int64_t dom[3], bo
     return launch_status(adjoint ? "halo_periodic_adj launch" : "halo_periodic launch");
 }
 
+// ------------------------------------------------------------------ fused hdiff -> vadv
+// 2 consumer warps (64 columns) + 1 producer warp per CTA: at 256 x 256 the
+// 1024 CTAs are all resident, about 7 per SM, as the FP64 column solve needs;
+// the producer runs up to 8 levels ahead.
+constexpr int kFusedBJ = 2, kFusedStages = 2, kFusedRing = 8;
+
+template <typename T, typename N, bool TMA>
+static int launch_fused_t(const CUtensorMap &map, const gtb_field *const f[6], const HdiffGeom &hg,
+                          const VadvGeom &g, void *ws, cudaStream_t st) {
+    constexpr bool DPG = vadv_dp_global<T, N>();
+    constexpr int STG = TMA ? kFusedStages : 1;
+    using Lay = FusedLayout<T, kFusedBJ, STG, kFusedRing>;
+    auto kern = hdiff_vadv_kernel<T, N, kFusedBJ, STG, kFusedRing, TMA, DPG>;
+    if (prepare_kernel(kern, Lay::smem_bytes) != cudaSuccess) return launch_status("hdiff_vadv: shared-memory attribute");
+    dim3 grid((g.I + 31) / 32, (g.J + kFusedBJ - 1) / kFusedBJ);
+    kern<<<grid, 32 * (kFusedBJ + 1), Lay::smem_bytes, st>>>(map, view_of<const T>(f[0]), view_of<const T>(f[1]),
+                                                      view_of<const T>(f[2]), view_of<const T>(f[3]),
+                                                      view_of<const T>(f[4]), view_of<T>(f[5]), hg, g,
+                                                      static_cast<N *>(ws));
+    return launch_status("hdiff_vadv launch");
+}
+
+// f = {in, coeff, wcon, utens, utens_stage, utens_stage_out}
+template <typename T, typename N>
+static int run_fused_n(const gtb_field *const f[6], const VadvGeom &g, void *ws, cudaStream_t st) {
+    using Tile = typename FusedLayout<T, kFusedBJ, kFusedStages, kFusedRing>::Tile;
+    HdiffGeom hg{};
+    hg.I = g.I, hg.J = g.J, hg.K = g.K;
+    CUtensorMap map;
+    const bool tma = encode_in_map<T>(f[0], Tile::BX, Tile::BY, hg, map);
+    return tma ? launch_fused_t<T, N, true>(map, f, hg, g, ws, st) : launch_fused_t<T, N, false>(map, f, hg, g, ws, st);
+}
+
 }  // namespace gtb
 
 // ====================================================================== C ABI
@@ -445,20 +507,7 @@ extern "C" int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const g
         return fail(GTB_ERR_UNSUPPORTED, "gtb_vadv: K = %lld exceeds the limit %d", (long long)dom[2], kVadvMaxK);
     if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
 
-    VadvGeom g{};
-    g.I = (int)dom[0], g.J = (int)dom[1], g.K = (int)dom[2];
-    g.literal = literal ? 1 : 0;
-    const double bp = 0.5 * (1.0 + beta_v), bm = 0.5 * (1.0 - beta_v);
-    g.sym = (bp == bm) ? 1 : 0;
-    g.dtr = dtr_stage;
-    // a_k = bp * (-w_k/2): with w_k = s_k/2 (average) that is (-bp/4) s_k, else (-bp/2) s_k
-    g.ka = (literal ? -0.5 : -0.25) * bp;
-    g.kas = (literal ? -0.5 : -0.25) * bm;
-    {
-        int n = 0;
-        const double m = std::frexp(-g.ka, &n);  // -ka = m 2^n, m in [0.5, 1)
-        g.ka_pow2 = (m == 0.5 && n - 1 < 0 && n - 1 > -64) ? n - 1 : 0;
-    }
+    const VadvGeom g = make_vadv_geom(dom, literal, dtr_stage, beta_v);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (workspace) {
         if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
@@ -480,6 +529,63 @@ extern "C" size_t gtb_vadv_workspace_bytes(int dtype, int prec, const int64_t *d
     for (int d = 0; d < 3; ++d)
         if (domain[d] < 0) return 0;
     return vadv_ws_bytes_for(dtype, dtype == GTB_F64 ? GTB_PREC_NATIVE : prec, domain);
+}
+
+extern "C" int gtb_hdiff_vadv(const gtb_field *in, const gtb_field *coeff, const gtb_field *wcon,
+                              const gtb_field *utens, const gtb_field *utens_stage, const gtb_field *utens_stage_out,
+                              double dtr_stage, double beta_v, int prec, unsigned flags, const int64_t *domain,
+                              void *workspace, size_t workspace_bytes, void *stream) {
+    const gtb_field *f[6] = {in, coeff, wcon, utens, utens_stage, utens_stage_out};
+    static const char *names[6] = {"in", "coeff", "wcon", "utens", "utens_stage", "utens_stage_out"};
+    for (int q = 0; q < 6; ++q)
+        if (!f[q]) return fail(GTB_ERR_NULL, "gtb_hdiff_vadv: NULL field %s", names[q]);
+    const int dt = in->dtype;
+    if (!dtype_size(dt)) return fail(GTB_ERR_DTYPE, "gtb_hdiff_vadv: unknown dtype %d", dt);
+    int rc;
+    for (int q = 0; q < 6; ++q)
+        if ((rc = check_field(names[q], f[q], dt))) return rc;
+    if (flags & ~GTB_WCON_LITERAL) return fail(GTB_ERR_ARG, "gtb_hdiff_vadv: unknown flags 0x%x", flags);
+    if (prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return fail(GTB_ERR_ARG, "gtb_hdiff_vadv: unknown prec %d", prec);
+    if (dt == GTB_F64 && prec != GTB_PREC_NATIVE)
+        return fail(GTB_ERR_ARG, "gtb_hdiff_vadv: FP64 storage computes in binary64 (prec must be GTB_PREC_NATIVE)");
+    if (!(dtr_stage == dtr_stage) || !(beta_v == beta_v)) return fail(GTB_ERR_ARG, "gtb_hdiff_vadv: NaN scalar");
+    const bool literal = flags & GTB_WCON_LITERAL;
+    const Reach r_in{{2, 2, 0}, {2, 2, 0}}, r0{{0, 0, 0}, {0, 0, 0}}, rw{{0, 0, 0}, {literal ? 0 : 1, 0, 0}};
+    const Reach *reach[6] = {&r_in, &r0, &rw, &r0, &r0, &r0};
+    int64_t dom[3] = {INT64_MAX, INT64_MAX, INT64_MAX};
+    if (!domain)
+        for (int q = 0; q < 6; ++q) shrink_domain(f[q], *reach[q], dom);
+    if ((rc = resolve_domain(domain, dom))) return rc;
+    for (int q = 0; q < 6; ++q)
+        if ((rc = check_extent(names[q], f[q], *reach[q], dom))) return rc;
+    for (int q = 0; q < 5; ++q) {
+        if (q == 4 && same_view(utens_stage_out, utens_stage)) continue;  // in place
+        if (overlaps(utens_stage_out, f[q]))
+            return fail(GTB_ERR_ALIAS, "gtb_hdiff_vadv: utens_stage_out overlaps %s", names[q]);
+    }
+    if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
+    const size_t need = vadv_ws_bytes_for(dt, prec, dom);
+    if (!workspace || workspace_bytes < need)
+        return fail(GTB_ERR_ARG, "gtb_hdiff_vadv: a workspace of %zu bytes is required (got %zu)", need,
+                    workspace ? workspace_bytes : (size_t)0);
+    if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
+        return fail(GTB_ERR_LAYOUT, "gtb_hdiff_vadv: workspace must be 16-byte aligned");
+    {
+        const int64_t n = (int64_t)(workspace_bytes / dtype_size(dt));
+        const gtb_field wsf{workspace, dt, 0, {n, 1, 1}, {1, n, n}, {0, 0, 0}};
+        for (int q = 0; q < 6; ++q)
+            if (overlaps(&wsf, f[q])) return fail(GTB_ERR_ALIAS, "gtb_hdiff_vadv: workspace overlaps %s", names[q]);
+    }
+    const VadvGeom g = make_vadv_geom(dom, literal, dtr_stage, beta_v);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (dt == GTB_F64) return run_fused_n<double, double>(f, g, workspace, st);
+    if (prec == GTB_PREC_F64) return run_fused_n<float, double>(f, g, workspace, st);
+    if (prec == GTB_PREC_DF) return run_fused_n<float, df>(f, g, workspace, st);
+    return run_fused_n<float, float>(f, g, workspace, st);
+}
+
+extern "C" size_t gtb_hdiff_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain) {
+    return gtb_vadv_workspace_bytes(dtype, prec, domain);
 }
 
 extern "C" int gtb_device_status(void *stream) {
@@ -661,19 +767,7 @@ extern "C" int gtb_vadv_adj(const gtb_field *wcon, const gtb_field *y_bar, const
     if (workspace && reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
         return fail(GTB_ERR_LAYOUT, "gtb_vadv_adj: workspace must be 16-byte aligned");
     if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
-    VadvGeom g{};
-    g.I = (int)dom[0], g.J = (int)dom[1], g.K = (int)dom[2];
-    g.literal = literal ? 1 : 0;
-    const double bp = 0.5 * (1.0 + beta_v), bm = 0.5 * (1.0 - beta_v);
-    g.sym = (bp == bm) ? 1 : 0;
-    g.dtr = dtr_stage;
-    g.ka = (literal ? -0.5 : -0.25) * bp;
-    g.kas = (literal ? -0.5 : -0.25) * bm;
-    {
-        int n = 0;
-        const double m = std::frexp(-g.ka, &n);
-        g.ka_pow2 = (m == 0.5 && n - 1 < 0 && n - 1 > -64) ? n - 1 : 0;
-    }
+    const VadvGeom g = make_vadv_geom(dom, literal, dtr_stage, beta_v);
     const int acc = (flags & GTB_ADJ_ACCUMULATE) ? 1 : 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (dt == GTB_F64) return run_vadv_adj_n<double, double>(f, g, acc, merge, workspace, workspace_bytes, st);
@@ -834,17 +928,7 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
     int vitems = 0;
     for (int r = 0; r < n; ++r) {
         const gtb_member &M = mem[vorder[r]];
-        VadvGeom g{};
-        g.I = (int)M.domain[0], g.J = (int)M.domain[1], g.K = (int)M.domain[2];
-        g.literal = literal ? 1 : 0;
-        const double bp = 0.5 * (1.0 + beta), bm = 0.5 * (1.0 - beta);
-        g.sym = (bp == bm) ? 1 : 0;
-        g.dtr = dtr;
-        g.ka = (literal ? -0.5 : -0.25) * bp;
-        g.kas = (literal ? -0.5 : -0.25) * bm;
-        int e2 = 0;
-        const double mant = std::frexp(-g.ka, &e2);
-        g.ka_pow2 = (mant == 0.5 && e2 - 1 < 0 && e2 - 1 > -64) ? e2 - 1 : 0;
+        const VadvGeom g = make_vadv_geom(M.domain, literal, dtr, beta);
         const int bx = (g.I + 31) / 32, by = (g.J + BJ - 1) / BJ;
         const View<const T> h = view_of<const T>(&M.h);
         vm[r] = BatchVadvMember<T>{h, view_of<const T>(&M.wcon), h, view_of<const T>(&M.utens),

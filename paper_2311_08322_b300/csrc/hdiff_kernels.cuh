@@ -60,6 +60,18 @@ __device__ __forceinline__ void store_vec(T *p, const T (&v)[VEC]) {
     }
 }
 
+// Whether hdiff on an I x J domain reads in(i, j) (domain indices): the used
+// Laplacians are those of [-1, I] x [0, J) (for fx) and [0, I) x [-1, J] (for
+// fy), so the cells read are [-2, I+1] x [0, J), [-1, I] x [-1, J] and
+// [0, I) x [-2, J+1]: the halo ring of width 2 minus three cells at each
+// corner, whose contents the definition never uses.
+__device__ __forceinline__ bool hdiff_reads(int i, int j, int I, int J) {
+    if (i < -2 || i > I + 1 || j < -2 || j > J + 1) return false;
+    const bool i_out = (i < -1 || i > I), j_out = (j < -1 || j > J);
+    const bool i_in = (i >= 0 && i < I), j_in = (j >= 0 && j < J);
+    return !((i_out && !j_in) || (j_out && !i_in));
+}
+
 // in -> X = trunc(in * 2^(1078 - E)) for the box's largest biased exponent E:
 // the significand, pre-shifted by the 3 bits of headroom, shifted right by
 // E - e (values above the scan's E, outside every stored output's reach, are

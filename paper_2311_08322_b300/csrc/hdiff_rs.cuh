@@ -276,13 +276,16 @@ __device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const Vie
             T *op = out.p + (int64_t)(ti0 + lane * CPL) + (int64_t)tj0 * out.sj + (int64_t)k * out.sk;
             if constexpr (FIXED) {
                 // largest biased exponent over the values the strip's stored outputs read:
-                // the domain part of rows cj0-2 .. cj0+nrows+1, columns -2 .. ntile+1 (never the
-                // storage padding beyond the halo, whose contents are arbitrary)
+                // rows cj0-2 .. cj0+nrows+1, columns -2 .. ntile+1 of the tile, restricted to the
+                // cells the definition reads (never the storage padding beyond the halo or the
+                // unread halo corners, whose contents are arbitrary)
                 const int ntile = min(G::TI, g.I - ti0);
                 const int wx = ntile + 4, wy = nrows + 4;
                 unsigned emax = 0;
                 for (int idx = lane; idx < wx * wy; idx += 32) {
-                    const int bx = idx % wx + xs, by = idx / wx + cj0;
+                    const int cx = idx % wx, cy = idx / wx;
+                    if (!hdiff_reads(ti0 + cx - 2, tj0 + cj0 + cy - 2, g.I, g.J)) continue;
+                    const int bx = cx + xs, by = cy + cj0;
                     emax = max(emax, ((unsigned)__double2hiint(S[by * G::BX + bx]) >> 20) & 0x7FFu);
                 }
                 const int E = (int)__reduce_max_sync(0xffffffffu, emax);

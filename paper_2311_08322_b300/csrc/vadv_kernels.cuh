@@ -142,7 +142,9 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
     const int i = bx * 32 + tx, j = by * BJ + ty;
     const bool active = (i < g.I) && (j < g.J);
     const int ic = min(i, g.I - 1), jc = min(j, g.J - 1);
-    const int iw = min(i, g.I);  // wcon is valid up to i = I (staggered)
+    // wcon is read up to i = I (I-staggered faces), or up to I-1 with the literal face velocity
+    const int ilim = g.literal ? g.I - 1 : g.I;
+    const int iw = min(i, ilim);
     const int K = g.K;
     const size_t cidx = ws_domain ? (size_t)jc * g.I + ic : cidx_ws;
     const bool wr = ws_domain ? active : true;
@@ -152,7 +154,7 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
     const T *put = ut.p + ic + (int64_t)jc * ut.sj;
     const T *puts = uts.p + ic + (int64_t)jc * uts.sj;  // may alias po (in place)
     const T *pw = wc.p + iw + (int64_t)jc * wc.sj;
-    const T *pw1 = wc.p + min(i + 1, g.I) + (int64_t)jc * wc.sj;
+    const T *pw1 = wc.p + min(i + 1, ilim) + (int64_t)jc * wc.sj;
     T *po = out.p + ic + (int64_t)jc * out.sj;
     const bool last_lane = (tx == 31);
     const bool lit = g.literal != 0;

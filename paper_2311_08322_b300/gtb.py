@@ -54,7 +54,8 @@ class GtbError(RuntimeError):
 _lib = None
 EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_hdiff_adj", "gtb_vadv_adj",
            "gtb_vadv_adj_workspace_bytes", "gtb_halo_periodic", "gtb_halo_periodic_adj", "gtb_device_status",
-           "gtb_batch_plan", "gtb_batch_run", "gtb_plan_info", "gtb_plan_destroy", "gtb_last_error", "gtb_version")
+           "gtb_batch_plan", "gtb_batch_run", "gtb_plan_info", "gtb_plan_destroy", "gtb_hdiff_vadv",
+           "gtb_hdiff_vadv_workspace_bytes", "gtb_last_error", "gtb_version")
 GTB_ADJ_ACCUMULATE = 2
 
 
@@ -77,6 +78,11 @@ def lib() -> ctypes.CDLL:
                                    i64p, vp, ctypes.c_size_t, vp]
         L.gtb_vadv_adj_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, i64p]
         L.gtb_vadv_adj_workspace_bytes.restype = ctypes.c_size_t
+        L.gtb_hdiff_vadv.argtypes = [P, P, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_uint, i64p, vp, ctypes.c_size_t, vp]
+        L.gtb_hdiff_vadv.restype = ctypes.c_int
+        L.gtb_hdiff_vadv_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, i64p]
+        L.gtb_hdiff_vadv_workspace_bytes.restype = ctypes.c_size_t
         L.gtb_halo_periodic.argtypes = [P, ctypes.c_int, ctypes.c_int, i64p, vp]
         L.gtb_halo_periodic_adj.argtypes = [P, ctypes.c_int, ctypes.c_int, i64p, vp]
         for n in ("gtb_hdiff_adj", "gtb_vadv_adj", "gtb_halo_periodic", "gtb_halo_periodic_adj"):
@@ -251,6 +257,39 @@ def vadv(u_stage, wcon, u_pos, utens, utens_stage, out=None, *, dtr_stage=3.0 / 
     _check(lib().gtb_vadv(*[ctypes.byref(f) for f in fs], float(dtr_stage), float(beta_v),
                           PREC[prec] if isinstance(prec, str) else int(prec), GTB_WCON_LITERAL if literal else 0,
                           _dom(domain), ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes, _stream(stream)))
+    return out
+
+
+def _fused_domain(fs, literal):
+    """Deduced domain of hdiff_vadv: in needs 2 halo points in I and J, wcon one above I."""
+    dom = []
+    for d in range(3):
+        reach = [2 if d < 2 else 0] + [0] * 5
+        if d == 0 and not literal:
+            reach[2] = 1
+        dom.append(min(f.shape[d] - f.origin[d] - r for f, r in zip(fs, reach)))
+    return tuple(max(0, x) for x in dom)
+
+
+def hdiff_vadv(in_, coeff, wcon, utens, utens_stage, out=None, *, dtr_stage=3.0 / 20.0, beta_v=0.0,
+               prec="native", literal=False, domain=None, workspace="auto", stream=None):
+    """utens_stage_out = vadv(h, wcon, h, utens, utens_stage) with h = hdiff(in_, coeff), in one
+    kernel (gtb_hdiff_vadv); ``out=None`` updates utens_stage in place.  ``workspace``: "auto"
+    (a cached buffer from :func:`workspace`) or a CUDA tensor; the call needs one."""
+    out = utens_stage if out is None else out
+    fs = [_as_field(x) for x in (in_, coeff, wcon, utens, utens_stage, out)]
+    ws_ptr, ws_bytes = None, 0
+    if isinstance(workspace, str):
+        dom = tuple(domain) if domain is not None else _fused_domain(fs, literal)
+        need = int(lib().gtb_hdiff_vadv_workspace_bytes(fs[0].dtype, PREC[prec] if isinstance(prec, str)
+                                                        else int(prec), _dom(dom)))
+        workspace = globals()["workspace"](need, stream) if need else None
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    _check(lib().gtb_hdiff_vadv(*[ctypes.byref(f) for f in fs], float(dtr_stage), float(beta_v),
+                                PREC[prec] if isinstance(prec, str) else int(prec),
+                                GTB_WCON_LITERAL if literal else 0, _dom(domain),
+                                ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes, _stream(stream)))
     return out
 
 

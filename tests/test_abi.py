@@ -126,3 +126,37 @@ def test_vadv_workspace_alias_rejected(L):
     args = [*[ctypes.byref(f) for f in fs], 0.15, 0.0, 0, 0, (ctypes.c_int64 * 3)(8, 8, 6)]
     assert L.lib().gtb_vadv(*args, ctypes.c_void_p(3 * G + 64), 4096, None) == -5
     assert L.lib().gtb_vadv(*args, ctypes.c_void_p(40 * G + 8), 4096, None) == -4  # not 16-byte aligned
+
+
+def test_hdiff_vadv_validation(L):
+    """gtb_hdiff_vadv: in needs the 2-point I/J halo, wcon one point above I, a
+    workspace is required, the output may only be utens_stage itself."""
+    G = 1 << 24
+    fin = lambda o=(2, 2, 0): fake(L, 12, 12, 6, origin=o, ptr=1 * G)
+    mk = lambda n, o=(1, 1, 0): fake(L, 10, 10, 6, origin=o, ptr=n * G)
+    fs = [fin()] + [mk(n) for n in range(2, 7)]
+    lib = L.lib()
+
+    def call(fs, dom=(8, 8, 6), prec=0, flags=0, ws=None, wsb=0):
+        d = None if dom is None else (ctypes.c_int64 * 3)(*dom)
+        return lib.gtb_hdiff_vadv(*[ctypes.byref(f) for f in fs], 0.15, 0.0, prec, flags, d,
+                                  None if ws is None else ctypes.c_void_p(ws), wsb, None)
+
+    assert call(fs, dom=(0, 8, 6)) == 0                        # empty domain: nothing to do
+    assert call(fs) == -9                                       # no workspace
+    assert call(fs, ws=40 * G, wsb=8 * 8 * 8 * 6 - 8) == -9     # workspace too small
+    assert call(fs, ws=40 * G + 8, wsb=1 << 20) == -4           # not 16-byte aligned
+    assert call(fs, ws=3 * G + 64, wsb=1 << 20) == -5           # workspace overlaps wcon
+    assert call(fs, dom=(9, 8, 6), ws=40 * G, wsb=1 << 20) == -3  # wcon needs i+1 <= 9
+    assert call([fin((1, 2, 0))] + fs[1:], ws=40 * G, wsb=1 << 20) == -3  # in needs 2 halo points
+    assert call(fs, prec=1, ws=40 * G, wsb=1 << 20) == -9       # FP64 storage: binary64 only
+    assert call(fs, flags=2, ws=40 * G, wsb=1 << 20) == -9      # only GTB_WCON_LITERAL
+    fs_shift = fs[:5] + [mk(5, o=(1, 2, 0))]                    # output overlapping utens_stage shifted
+    assert call(fs_shift, ws=40 * G, wsb=1 << 20) == -5
+    fs_in = fs[:5] + [mk(3)]                                    # output on wcon
+    assert call(fs_in, ws=40 * G, wsb=1 << 20) == -5
+    fs_dt = fs[:3] + [fake(L, 10, 10, 6, origin=(1, 1, 0), dtype=1, ptr=4 * G)] + fs[4:]
+    assert call(fs_dt, ws=40 * G, wsb=1 << 20) == -2
+    # the deduced domain: min over fields of shape - origin - reach (in: 12-2-2 = 8, wcon: 10-1-1 = 8)
+    assert L.lib().gtb_hdiff_vadv_workspace_bytes(2, 0, (ctypes.c_int64 * 3)(8, 8, 6)) == 8 * 8 * 8 * 6
+    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 2, (ctypes.c_int64 * 3)(8, 8, 6)) == 16 * 8 * 8 * 6
