@@ -5,8 +5,10 @@ stencils) at 256x256x80 in FP64, through libgtb's C ABI.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gtb|reference]
 
 A step is one pass of the whole hot path over one batch: hdiff (Laplacian,
-limited fluxes, update) on one input set, then vadv (coefficients, forward
-elimination, back substitution) on another.  Prints ONE JSON line (rank 0).
+limited fluxes, update) on one input set and vadv (coefficients, forward
+elimination, back substitution) on another, co-scheduled in one launch
+(gtb_step); the same step as two separate launches is timed beside it.
+Prints ONE JSON line (rank 0).
 
 * value: domain points per second (Mpoints/s) of whole steps, inputs resident
   in HBM, device time from CUDA events on the launching stream, max over ranks.
@@ -19,6 +21,8 @@ elimination, back substitution) on another.  Prints ONE JSON line (rank 0).
   binary64 and double-float column arithmetic) beside the FP64 path there.
 * batched: the 48-member ensemble of uneven domains, autotuned plan replayed
   from a CUDA graph vs the loop of single-domain launches.
+* fused_chain: the chained step (vadv of hdiff's output) as two launches vs
+  gtb_hdiff_vadv, one kernel that keeps h on chip.
 * adjoint_forward_ratio: backward / forward time of one chained step
   (periodic halo + hdiff + vadv) through the adjoint kernels.
 * --impl reference: the oracle itself as the reference arm.
@@ -250,14 +254,20 @@ def run_gtb(args):
     stream = torch.cuda.current_stream()
 
     def step(s, ev=None):
+        """Both stencils on their own fields: one co-scheduled launch (gtb_step)."""
         if ev is not None:
             ev[0].record(stream)
-        gtb.hdiff(s["in"], s["coeff"], s["hout"], stream=stream)
+        gtb.step(s["in"], s["coeff"], s["hout"], *[s[n] for n in VADV_NAMES], s["vout"], stream=stream)
         if ev is not None:
             ev[1].record(stream)
+
+    def separate(s, ev):
+        """The same step as two launches, gtb_hdiff then gtb_vadv (per-kernel context)."""
+        ev[0].record(stream)
+        gtb.hdiff(s["in"], s["coeff"], s["hout"], stream=stream)
+        ev[1].record(stream)
         gtb.vadv(*[s[n] for n in VADV_NAMES], s["vout"], stream=stream)
-        if ev is not None:
-            ev[2].record(stream)
+        ev[2].record(stream)
 
     for w in range(args.warmup):
         step(sets[w % len(sets)])
@@ -283,16 +293,24 @@ def run_gtb(args):
     clk = clocks.stop()
     gtb.device_status()
     el_ms = t_start.elapsed_time(t_end)
-    # the same steps again with an event around each kernel (per-kernel rooflines)
+    # the same steps again with an event around each launch (the step kernel's roofline),
+    # then as two separate kernels with an event around each
     nser = max(20, min(args.steps, 500))
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nser)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(nser)]
     torch.cuda.synchronize()
     for q in range(nser):
         step(sets[q % len(sets)], evs[q])
     torch.cuda.synchronize()
+    st_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nser)]
+    for q in range(nser):
+        separate(sets[q % len(sets)], evs[q])
+    torch.cuda.synchronize()
     gtb.device_status()
     h_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     v_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    sep_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in evs]))
+    chain = fused_chain_compare(gtb, f, sets) if rank == 0 and not args.no_fused else None
     adj = adjoint_ratio(gtb, f, sets) if rank == 0 and not args.no_adjoint else None
     el_ms = max_over_ranks(el_ms, dist if world > 1 else None, "cuda")
     value = whole_job_mpoints(world, POINTS, args.steps, el_ms)
@@ -333,24 +351,30 @@ def run_gtb(args):
     hbm = float(peaks.get("hbm_gbs", 6400.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     kern = {}
-    for name, ms, nbytes, flops in (("hdiff", h_ms, hdiff_bytes(I, J, K, 8), HDIFF_FLOPS_PER_PT * POINTS),
-                                    ("vadv", v_ms, vadv_bytes(I, J, K, 8), VADV_FLOPS_PER_PT * POINTS)):
+    hb, vb = hdiff_bytes(I, J, K, 8), vadv_bytes(I, J, K, 8)
+    hf, vf = HDIFF_FLOPS_PER_PT * POINTS, VADV_FLOPS_PER_PT * POINTS
+    for name, ms, nbytes, flops in (("step", st_ms, hb + vb, hf + vf), ("hdiff", h_ms, hb, hf), ("vadv", v_ms, vb, vf)):
         gbs = nbytes / (ms / 1e3) / 1e9
         gfl = flops / (ms / 1e3) / 1e9
         kern[name] = {"ms": round(ms, 4), "mpoints_s": round(POINTS / (ms / 1e3) / 1e6, 1),
                       "algorithmic_bytes": nbytes, "hbm_gbs": round(gbs, 1),
                       "frac_of_measured_hbm": round(gbs / hbm, 4), "frac_of_8tbs": round(gbs / 8000.0, 4),
                       "fp64_gflops": round(gfl, 1), "frac_of_nominal_fp64": round(gfl / FP64_NOMINAL_GFLOPS, 4)}
-    dom = max(kern, key=lambda n: kern[n]["ms"])
+    kern["step"]["kernel"] = "hdiff_vadv_pair_kernel (hdiff and vadv co-scheduled in one launch)"
+    kern["separate_step_ms"] = round(sep_ms, 4)
+    dom = "step"  # the step is one launch: the dominant (only) kernel of the timed region
     kd = kern[dom]
-    traffic = profile_traffic(dom + "_kernel")
+    traffic = profile_traffic("hdiff_vadv_pair_kernel")
     if kd["frac_of_nominal_fp64"] > kd["frac_of_measured_hbm"]:
-        roof = {"bound": "alu", "kernel": dom, "achieved": kd["fp64_gflops"], "peak": FP64_NOMINAL_GFLOPS,
-                "unit": "GFLOP/s", "frac": kd["frac_of_nominal_fp64"], "traffic": traffic,
-                "peak_source": "nominal B300 FP64 1.25 TFLOP/s (148 SMs); algorithmic FP64 flops",
+        roof = {"bound": "alu", "kernel": "hdiff_vadv_pair_kernel", "achieved": kd["fp64_gflops"],
+                "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s", "frac": kd["frac_of_nominal_fp64"],
+                "traffic": traffic,
+                "peak_source": "nominal B300 FP64 1.25 TFLOP/s (148 SMs); algorithmic FP64 flops of both "
+                               "stencils (hdiff 16/pt, vadv 25/pt)",
                 "hbm_frac_of_measured": kd["frac_of_measured_hbm"]}
     else:
-        roof = {"bound": "hbm", "kernel": dom, "achieved": kd["hbm_gbs"], "peak": hbm, "unit": "GB/s",
+        roof = {"bound": "hbm", "kernel": "hdiff_vadv_pair_kernel", "achieved": kd["hbm_gbs"], "peak": hbm,
+                "unit": "GB/s",
                 "frac": kd["frac_of_measured_hbm"], "traffic": traffic, "peak_source": hbm_src}
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "Mpoints/s", "n_gpus": world,
@@ -360,7 +384,8 @@ def run_gtb(args):
             "config": {"workload": WORKLOAD, "I": I, "J": J, "K": K, "parallelism": f"replicas{world}",
                        "l2": f"{args.sets} rotating input sets of "
                              f"{(hdiff_bytes(I, J, K, 8) + vadv_bytes(I, J, K, 8)) / 1e6:.0f} MB each (> 126 MB L2)"},
-            "kernels": kern, "roofline": roof, "clocks": clk, "gpu_launches": 2 * args.steps,
+            "kernels": kern, "roofline": roof, "clocks": clk, "gpu_launches": args.steps,
+            "fused_chain": chain,
             "adjoint_forward_ratio": None if adj is None else adj["ratio"], "adjoint": adj,
             "e2e": {"value": round(e2e_value, 1), "unit": "Mpoints/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}}
@@ -377,6 +402,41 @@ def run_gtb(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def fused_chain_compare(gtb, f, sets, reps=50):
+    """The chained step h = hdiff(in, coeff), out = vadv(h, wcon, h, utens, utens_stage) at
+    256x256x80 FP64: gtb_hdiff + gtb_vadv (h through HBM) vs gtb_hdiff_vadv (one kernel)."""
+    import torch
+    dom = (I, J, K)
+    hs = [gtb.storage_from(np.zeros_like(f["utens"]), (VADV_HALO, VADV_HALO, 0)) for _ in sets]
+
+    def separate(q):
+        s, h = sets[q % len(sets)], hs[q % len(sets)]
+        gtb.hdiff(s["in"], s["coeff"], h, domain=dom)
+        gtb.vadv(h, s["wcon"], h, s["utens"], s["utens_stage"], s["vout"], domain=dom)
+
+    def fused(q):
+        s = sets[q % len(sets)]
+        gtb.hdiff_vadv(s["in"], s["coeff"], s["wcon"], s["utens"], s["utens_stage"], s["vout"], domain=dom)
+
+    def timed(fn):
+        for q in range(5):
+            fn(q)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for q in range(reps):
+            fn(q)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    sep, fus = timed(separate), timed(fused)
+    gtb.device_status()
+    return {"workload": "chained step 256x256x80 FP64: h = hdiff(in, coeff); out = vadv(h, wcon, h, utens, "
+                        "utens_stage)", "separate_ms": round(sep, 4), "fused_ms": round(fus, 4),
+            "speedup": round(sep / fus, 3), "fused_mpoints_s": round(POINTS / (fus / 1e3) / 1e6, 1)}
 
 
 def adjoint_ratio(gtb, f, sets, reps=50):
@@ -550,6 +610,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()

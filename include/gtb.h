@@ -219,6 +219,33 @@ int gtb_hdiff_vadv(const gtb_field *in, const gtb_field *coeff, const gtb_field 
 size_t gtb_hdiff_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain);
 
 /*
+ * gtb_step -- one step of the paper's benchmark (Sec. 3.1): both stencils on
+ * their own fields,
+ *   hdiff_out       = hdiff(in, coeff)                                (as gtb_hdiff)
+ *   utens_stage_out = vadv(u_stage, wcon, u_pos, utens, utens_stage)  (as gtb_vadv)
+ * For GTB_F64 storage the two are co-scheduled in one kernel: every CTA runs
+ * the hdiff of a 32 x 2 column tile on two warps and the vadv column solve of
+ * the same tile on two others (binary64 hdiff runs on the integer pipe and the
+ * solve on the FP64 pipe, so the two overlap in every SM); hdiff_out then
+ * equals gtb_hdiff's to rounding (the fixed-point scale is chosen per tile and
+ * level, not per strip).  For GTB_F32 storage (HBM-bound hdiff, FP32-pipe
+ * solve) the two kernels run back to back, which is faster there, and
+ * hdiff_out equals gtb_hdiff's.  utens_stage_out always equals gtb_vadv's
+ * result (workspace form) bit for bit.
+ * Both stencils share one domain (deduced from all nine fields when NULL).
+ * Reach and in-place rules: as gtb_hdiff and gtb_vadv; hdiff_out may overlap
+ * no other field, utens_stage_out none but possibly utens_stage itself (the
+ * very same view).  dtr_stage, beta_v, prec and flags as gtb_vadv.
+ * workspace: REQUIRED, at least gtb_vadv_workspace_bytes() bytes, 16-byte
+ * aligned, overlapping no field (NULL or too small: GTB_ERR_ARG).
+ */
+int gtb_step(const gtb_field *in, const gtb_field *coeff, const gtb_field *hdiff_out,
+             const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u_pos,
+             const gtb_field *utens, const gtb_field *utens_stage, const gtb_field *utens_stage_out,
+             double dtr_stage, double beta_v, int prec, unsigned flags, const int64_t *domain,
+             void *workspace, size_t workspace_bytes, void *stream);
+
+/*
  * Batched ensembles of uneven domains (the paper's stencils over many
  * independent members, e.g. an ensemble forecast).  Each member runs
  *   h   = hdiff(in, coeff)                         (gtb_hdiff on its domain)

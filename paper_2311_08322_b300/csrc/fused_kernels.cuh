@@ -5,19 +5,21 @@
 // produced level by level inside the SM and consumed there: it is never
 // written to memory.
 //
-// CTA = a 32 x BJ block of columns, all K levels, warp-specialised:
-//   * BJ consumer warps (lane = i, warp = j), one thread per column: the
-//     column's forward elimination step of level m-1 as soon as h_m is ready,
-//     then the back substitution (the FP64- or FP32-pipe bound part);
-//   * one producer warp: per level the (32+4) x (BJ+4) box of `in` arrives by
+// CTA = a TI x TJ tile of columns, all K levels, warp-specialised:
+//   * TI*TJ/32 consumer warps, one thread per column (t -> i = t % TI,
+//     j = t / TI): the column's forward elimination step of level m-1 as soon
+//     as h_m is ready, then the back substitution (the FP64- or FP32-pipe
+//     bound part);
+//   * PW producer warps: per level the (TI+4) x (TJ+4) box of `in` arrives by
 //     TMA (STAGES-deep ring); binary64 storage converts it to exact int64 fixed
 //     point (the form of hdiff_rs: E = the largest exponent among the cells the
-//     block's outputs read; a level whose E leaves [64, 2040] uses the
-//     definition in binary64), forms the Laplacian on (32+2) x (BJ+2) cells,
-//     the limited fluxes and h of the BJ x 32 columns into a RING-deep shared
-//     ring (the integer-pipe bound part).
+//     tile's outputs read; a level whose E leaves [64, 2040] uses the
+//     definition in binary64), forms the Laplacian on (TI+2) x (TJ+2) cells,
+//     the limited fluxes and h of the tile into a RING-deep shared ring (the
+//     integer-pipe bound part).  A squarer tile needs fewer halo cells per
+//     column: (TI+4)(TJ+4)/(TI TJ) conversions, (TI+2)(TJ+2)/(TI TJ) Laplacians.
 // The two sides meet only through the ring's full / empty mbarriers (bounded
-// waits), so the producer runs up to RING levels ahead and the consumers never
+// waits), so the producers run up to RING levels ahead and the consumers never
 // wait on a block barrier.
 // The back substitution runs on the shifted unknown z = x - h (u_pos = h), so
 // that h is not needed after the forward sweep:
@@ -34,186 +36,281 @@
 
 namespace gtb {
 
-template <typename T, int BJ, int STAGES, int RING>
+template <typename T, int TI, int TJ>
+struct FusedTile {
+    static_assert(TI == 8 || TI == 16 || TI == 32, "a warp covers whole rows of the tile");
+    static_assert((TI * TJ) % 32 == 0, "whole consumer warps");
+    static constexpr int kAlign = 16 / (int)sizeof(T);
+    static constexpr int BX = ((TI + 4 + kAlign - 1 + kAlign - 1) / kAlign) * kAlign;  // box width (+ alignment)
+    static constexpr int BY = TJ + 4;
+    static constexpr int box_elems = BX * BY;
+    static constexpr int box_bytes = box_elems * (int)sizeof(T);
+    static constexpr int stage_stride = ((box_bytes + 127) / 128) * 128;
+    static constexpr int XW = TI + 4, XH = TJ + 4;  // cells ci in [-2, TI+1], cj in [-2, TJ+1]
+    static constexpr int LW = TI + 2, LH = TJ + 2;  // Laplacians li in [-1, TI], lj in [-1, TJ]
+    static constexpr int NC = TI * TJ;              // columns = consumer threads
+    static constexpr int CW = NC / 32;              // consumer warps
+};
+
+template <typename T, int TI, int TJ, int PW, int STAGES, int RING>
 struct FusedLayout {
-    using Tile = RsTile<T, 1, BJ, 1>;           // 32 x BJ columns; box (32+4+align) x (BJ+4)
-    static constexpr int XW = 36, XH = BJ + 4;  // fixed-point cells: columns -2..33, rows -2..BJ+1
-    static constexpr int LW = 34, LH = BJ + 2;  // Laplacian cells: columns -1..32, rows -1..BJ
+    using Tile = FusedTile<T, TI, TJ>;
     static constexpr int x_off = STAGES * Tile::stage_stride;
-    static constexpr int l_off = x_off + XW * XH * 8;
-    static constexpr int h_off = l_off + LW * LH * 8;
-    static constexpr int bar_off = h_off + ((RING * BJ * 32 * (int)sizeof(T) + 7) / 8) * 8;
+    static constexpr int l_off = x_off + Tile::XW * Tile::XH * 8;
+    static constexpr int e_off = l_off + Tile::LW * Tile::LH * 8;  // per producer warp exponent maxima
+    static constexpr int h_off = e_off + ((PW * 4 + 15) / 16) * 16;
+    static constexpr int bar_off = h_off + ((RING * Tile::NC * (int)sizeof(T) + 7) / 8) * 8;
     static constexpr int bytes = bar_off + (STAGES + 2 * RING) * 8;
     static constexpr int smem_bytes = bytes + 128;  // + slack for the 128-byte base alignment
 };
 
-// Cells of one level's box, tile-relative (ci, cj) with ci in [-2, 33], cj in [-2, BJ+1].
-template <typename T, typename V, int BJ, bool FIXED>
+// Cells of one level's box, tile-relative (ci, cj).
+template <typename T, typename V, int TI, int TJ, bool FIXED>
 struct FusedCells {
+    using Tile = FusedTile<T, TI, TJ>;
     const T *S;  // the TMA box: cell (ci, cj) at S[(cj+2)*BX + ci+2+xs]
-    const V *X;  // fixed point: X[(cj+2)*36 + ci+2]; unused for the definition
-    const V *L;  // Laplacian: L[(lj+1)*34 + li+1]
+    const V *X;  // fixed point: X[(cj+2)*XW + ci+2]; unused for the definition
+    const V *L;  // Laplacian: L[(lj+1)*LW + li+1]
     int xs;
-    static constexpr int BX = RsTile<T, 1, BJ, 1>::BX;
-    __device__ __forceinline__ const T *sp(int ci, int cj) const { return S + (cj + 2) * BX + ci + 2 + xs; }
+    __device__ __forceinline__ const T *sp(int ci, int cj) const { return S + (cj + 2) * Tile::BX + ci + 2 + xs; }
     __device__ __forceinline__ V x(int ci, int cj) const {
-        if constexpr (FIXED) return X[(cj + 2) * 36 + ci + 2];
+        if constexpr (FIXED) return X[(cj + 2) * Tile::XW + ci + 2];
         else return *sp(ci, cj);
     }
-    __device__ __forceinline__ V lap(int li, int lj) const { return L[(lj + 1) * 34 + li + 1]; }
+    __device__ __forceinline__ V lap(int li, int lj) const { return L[(lj + 1) * Tile::LW + li + 1]; }
 };
 
-// The producer warp's level with policy P (FixedF64 or Native<T>): Laplacians
-// into Lw, then h of column `lane` in the BJ rows into hrow[r * 32 + lane].
-template <int BJ, typename P, typename C, typename T>
-__device__ __forceinline__ void fused_hdiff_level(const P &pol, const C &c, typename P::V *Lw, const T (&cf)[BJ],
-                                                  T *hrow) {
+// Barrier among the PW producer warps (named barrier 1; a warp barrier for one warp).
+template <int PW>
+__device__ __forceinline__ void producer_sync() {
+    if constexpr (PW == 1) __syncwarp();
+    else asm volatile("bar.sync 1, %0;" ::"n"(32 * PW) : "memory");
+}
+
+// The producers' level with policy P (FixedF64 or Native<T>): Laplacians into Lw
+// (split over the producer threads, then a producer barrier), then h of the
+// tile's points pt, pt + NPT, ... handed to em.put(level, point, value).
+template <int TI, int TJ, int PW, typename P, typename C, typename T, typename Emit>
+__device__ __forceinline__ void fused_hdiff_level(const P &pol, const C &c, typename P::V *Lw, int pt,
+                                                  const T (&cf)[(TI * TJ + 32 * PW - 1) / (32 * PW)], int m,
+                                                  const Emit &em) {
     using V = typename P::V;
-    const int lane = threadIdx.x & 31;
-    for (int idx = lane; idx < 34 * (BJ + 2); idx += 32) {
-        const int li = idx % 34 - 1, lj = idx / 34 - 1;
+    using Tile = FusedTile<T, TI, TJ>;
+    constexpr int NPT = 32 * PW, PPT = (Tile::NC + NPT - 1) / NPT;
+    for (int idx = pt; idx < Tile::LW * Tile::LH; idx += NPT) {
+        const int li = idx % Tile::LW - 1, lj = idx / Tile::LW - 1;
         Lw[idx] = pol.lap(c.x(li, lj), c.x(li + 1, lj), c.x(li - 1, lj), c.x(li, lj + 1), c.x(li, lj - 1));
     }
-    __syncwarp();
-    const int ci = lane;
+    producer_sync<PW>();
 #pragma unroll
-    for (int cj = 0; cj < BJ; ++cj) {
+    for (int q = 0; q < PPT; ++q) {
+        const int p = pt + q * NPT;
+        if (Tile::NC % NPT != 0 && p >= Tile::NC) break;
+        const int ci = p % TI, cj = p / TI;
         const V x0 = c.x(ci, cj), l0 = c.lap(ci, cj);
         const V fxe = pol.limit(c.lap(ci + 1, cj) - l0, pol.grad(c.x(ci + 1, cj), x0, c.sp(ci + 1, cj), c.sp(ci, cj)));
         const V fxw = pol.limit(l0 - c.lap(ci - 1, cj), pol.grad(x0, c.x(ci - 1, cj), c.sp(ci, cj), c.sp(ci - 1, cj)));
         const V fyn = pol.limit(c.lap(ci, cj + 1) - l0, pol.grad(c.x(ci, cj + 1), x0, c.sp(ci, cj + 1), c.sp(ci, cj)));
         const V fys = pol.limit(l0 - c.lap(ci, cj - 1), pol.grad(x0, c.x(ci, cj - 1), c.sp(ci, cj), c.sp(ci, cj - 1)));
         const V D = (fxe - fxw) + (fyn - fys);
-        hrow[cj * 32 + lane] = pol.out(*c.sp(ci, cj), cf[cj], D);
+        em.put(m, p, pol.out(*c.sp(ci, cj), cf[q], D));
     }
 }
 
-template <typename T, typename N, int BJ, int STAGES, int RING, bool USE_TMA, bool DPG>
-__global__ void __launch_bounds__(32 * (BJ + 1))
+// Where the producers put h: the shared ring of the chained kernel (a slot is
+// acquired through its `empty` barrier and published through `full`), or a
+// field in global memory (hdiff as a stencil of its own).
+template <typename T>
+struct RingEmit {
+    T *H;
+    uint64_t *full, *empty;
+    int nc, ring;
+    __device__ __forceinline__ bool acquire(int m) const {
+        return m < ring || mbar_wait(&empty[m % ring], ((m / ring) - 1) & 1);
+    }
+    __device__ __forceinline__ void put(int m, int p, T v) const { H[(m % ring) * nc + p] = v; }
+    __device__ __forceinline__ void publish(int m) const {
+        __syncwarp();  // this warp's points of h are written
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&full[m % ring]);
+    }
+};
+
+template <typename T>
+struct GlobalEmit {
+    View<T> out;
+    int ti0, tj0, I, J, ti;
+    __device__ __forceinline__ bool acquire(int) const { return true; }
+    __device__ __forceinline__ void put(int m, int p, T v) const {
+        const int i = ti0 + p % ti, j = tj0 + p / ti;
+        if (i < I && j < J) out.p[i + (int64_t)j * out.sj + (int64_t)m * out.sk] = v;
+    }
+    __device__ __forceinline__ void publish(int) const {}
+};
+
+// The producer warps of a CTA (warps CW .. CW+PW-1): hdiff of the TI x TJ tile
+// at (ti0, tj0), level by level, handed to `em`.  Shared memory: the TMA ring
+// at `base`, then X, L and the exponent slots of the layout; barriers tbar.
+template <typename T, int TI, int TJ, int PW, int STAGES, bool USE_TMA, typename Emit>
+__device__ __forceinline__ void hdiff_producer(const CUtensorMap *tmap, const View<const T> &in,
+                                               const View<const T> &coeff, const HdiffGeom &hg, int ti0, int tj0,
+                                               unsigned char *base, int x_off, int l_off, int e_off, uint64_t *tbar,
+                                               const Emit &em) {
+    using Tile = FusedTile<T, TI, TJ>;
+    constexpr bool FIX = sizeof(T) == 8;           // binary64 storage: exact fixed-point hdiff
+    constexpr int NC = Tile::NC, CW = Tile::CW;
+    constexpr int NPT = 32 * PW;                   // producer threads
+    constexpr int NCELL = Tile::XW * Tile::XH;     // box cells
+    constexpr int CPT = (NCELL + NPT - 1) / NPT;   // cells per producer thread
+    constexpr int PPT = (NC + NPT - 1) / NPT;      // points per producer thread
+    const int lane = threadIdx.x & 31, pw = (threadIdx.x >> 5) - CW, pt = pw * 32 + lane;
+    const int I = hg.I, J = hg.J, K = hg.K;
+    int64_t *Xs = reinterpret_cast<int64_t *>(base + x_off);
+    unsigned char *Lraw = base + l_off;
+    unsigned *es = reinterpret_cast<unsigned *>(base + e_off);
+    const int xs = hg.xs;
+    if (USE_TMA && pt == 0) {
+        prefetch_tensormap(tmap);
+        for (int p = 0; p < STAGES && p < K; ++p) {
+            mbar_arrive_expect_tx(&tbar[p], Tile::box_bytes);
+            tma_load_3d(base + p * Tile::stage_stride, tmap, &tbar[p], hg.X0 + ti0, hg.Y0 + tj0, hg.Z0 + p);
+        }
+    }
+    // this thread's box cells (the same at every level): offset in the box, and
+    // whether hdiff reads the cell (bit q of rmask)
+    int coff[CPT];
+    unsigned rmask = 0;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int idx = pt + q * NPT;
+        const int ci = idx % Tile::XW - 2, cj = idx / Tile::XW - 2;
+        coff[q] = (cj + 2) * Tile::BX + ci + 2 + xs;
+        if (idx < NCELL && hdiff_reads(ti0 + ci, tj0 + cj, I, J)) rmask |= 1u << q;
+    }
+    // coeff of this thread's points, one level ahead
+    const T *pcf[PPT];
+    T cf_n[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int p = min(pt + q * NPT, NC - 1);
+        pcf[q] = coeff.p + min(ti0 + p % TI, I - 1) + (int64_t)min(tj0 + p / TI, J - 1) * coeff.sj;
+        cf_n[q] = pcf[q][0];
+    }
+    bool failed = false;
+    for (int m = 0; m < K; ++m) {
+        T cf[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            cf[q] = cf_n[q];
+            if (m + 1 < K) cf_n[q] = pcf[q][(int64_t)(m + 1) * coeff.sk];
+        }
+        const int s = USE_TMA ? m % STAGES : 0;
+        const T *S = reinterpret_cast<const T *>(base + s * Tile::stage_stride);
+        if (USE_TMA) {
+            if (!mbar_wait(&tbar[s], (m / STAGES) & 1)) failed = true;
+        } else {
+            T *D = reinterpret_cast<T *>(base);
+            for (int idx = pt; idx < Tile::box_elems; idx += NPT) {
+                const int bx = idx % Tile::BX, by = idx / Tile::BX;
+                const int gi = ti0 - 2 + bx, gj = tj0 - 2 + by;
+                T v = T(0);
+                if (gi >= -2 && gi < I + 2 && gj >= -2 && gj < J + 2)
+                    v = in.p[(int64_t)gi + (int64_t)gj * in.sj + (int64_t)m * in.sk];
+                D[idx] = v;
+            }
+            producer_sync<PW>();
+        }
+        // this thread's cells; binary64: the largest exponent among the cells read
+        T v[CPT];
+        unsigned emax = 0;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            v[q] = (pt + q * NPT < NCELL) ? S[coff[q]] : T(0);
+            if constexpr (FIX)
+                if ((rmask >> q) & 1u) emax = max(emax, ((unsigned)__double2hiint(v[q]) >> 20) & 0x7FFu);
+        }
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        // a wait that expired (this level's box, or the previous level's ring slot) is
+        // published with the exponents, so that every producer warp leaves here together
+        const bool wf = __any_sync(0xffffffffu, failed);
+        if (lane == 0) es[pw] = wf ? 0xFFFFFFFFu : emax;
+        producer_sync<PW>();
+        unsigned E = 0;
+#pragma unroll
+        for (int q = 0; q < PW; ++q) E = max(E, es[q]);
+        if (E == 0xFFFFFFFFu) {
+            failed = true;
+            break;
+        }
+        // every producer is past the previous level: its box stage can be refilled
+        if (USE_TMA && pt == 0 && m >= 1 && m - 1 + STAGES < K) {
+            const int sp = (m - 1) % STAGES;
+            mbar_arrive_expect_tx(&tbar[sp], Tile::box_bytes);
+            tma_load_3d(base + sp * Tile::stage_stride, tmap, &tbar[sp], hg.X0 + ti0, hg.Y0 + tj0,
+                        hg.Z0 + m - 1 + STAGES);
+        }
+        const bool fixed = FIX && E >= 64 && E <= 2040;
+        if constexpr (FIX) {
+            if (fixed) {
+#pragma unroll
+                for (int q = 0; q < CPT; ++q)
+                    if (pt + q * NPT < NCELL) Xs[pt + q * NPT] = to_fixed(v[q], (int)E);
+            }
+        }
+        if (!em.acquire(m)) failed = true;
+        bool done = false;
+        if constexpr (FIX) {
+            if (fixed) {
+                producer_sync<PW>();  // X complete
+                const FusedCells<T, int64_t, TI, TJ, true> c{S, Xs, reinterpret_cast<const int64_t *>(Lraw), xs};
+                fused_hdiff_level<TI, TJ, PW>(FixedF64{(int)E}, c, reinterpret_cast<int64_t *>(Lraw), pt, cf, m, em);
+                done = true;
+            }
+        }
+        if (!done) {
+            const FusedCells<T, T, TI, TJ, false> c{S, nullptr, reinterpret_cast<const T *>(Lraw), xs};
+            fused_hdiff_level<TI, TJ, PW>(Native<T>{}, c, reinterpret_cast<T *>(Lraw), pt, cf, m, em);
+        }
+        em.publish(m);
+    }
+    if (USE_TMA && failed && pt == 0)  // let the box loads in flight land before leaving
+        for (int s = 0; s < STAGES; ++s) mbar_wait(&tbar[s], 0), mbar_wait(&tbar[s], 1);
+}
+
+template <typename T, typename N, int TI, int TJ, int PW, int STAGES, int RING, bool USE_TMA, bool DPG>
+__global__ void __launch_bounds__(TI * TJ + 32 * PW)
     hdiff_vadv_kernel(const __grid_constant__ CUtensorMap tmap, const View<const T> in, const View<const T> coeff,
                       const View<const T> wc, const View<const T> ut, const View<const T> uts, const View<T> out,
                       const HdiffGeom hg, const VadvGeom g, N *__restrict__ ws) {
-    using Lay = FusedLayout<T, BJ, STAGES, RING>;
+    using Lay = FusedLayout<T, TI, TJ, PW, STAGES, RING>;
     using Tile = typename Lay::Tile;
-    constexpr bool FIX = sizeof(T) == 8;  // binary64 storage: exact fixed-point hdiff
+    constexpr int NC = Tile::NC, CW = Tile::CW;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    T *H = reinterpret_cast<T *>(base + Lay::h_off);  // H[slot][row][lane]
+    T *H = reinterpret_cast<T *>(base + Lay::h_off);  // H[slot][point]
     uint64_t *tbar = reinterpret_cast<uint64_t *>(base + Lay::bar_off);
     uint64_t *full = tbar + STAGES, *empty = full + RING;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int ti0 = blockIdx.x * 32, tj0 = blockIdx.y * BJ;
+    const int ti0 = blockIdx.x * TI, tj0 = blockIdx.y * TJ;
     const int I = g.I, J = g.J, K = g.K;
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&tbar[s], 1);
-        for (int s = 0; s < RING; ++s) mbar_init(&full[s], 1), mbar_init(&empty[s], BJ);
+        for (int s = 0; s < RING; ++s) mbar_init(&full[s], PW), mbar_init(&empty[s], CW);
         fence_mbar_init();
     }
     __syncthreads();  // the only block-wide barrier
 
-    if (w == BJ) {
-        // ================================================================ producer warp
-        int64_t *Xs = reinterpret_cast<int64_t *>(base + Lay::x_off);
-        unsigned char *Lraw = base + Lay::l_off;
-        const int xs = hg.xs;
-        if (USE_TMA && lane == 0) {
-            prefetch_tensormap(&tmap);
-            for (int p = 0; p < STAGES && p < K; ++p) {
-                mbar_arrive_expect_tx(&tbar[p], Tile::box_bytes);
-                tma_load_3d(base + p * Tile::stage_stride, &tmap, &tbar[p], hg.X0 + ti0, hg.Y0 + tj0, hg.Z0 + p);
-            }
-        }
-        // coeff of this lane's column in the BJ rows, one level ahead
-        const int ic = min(ti0 + lane, I - 1);
-        const T *pcf[BJ];
-        T cf_n[BJ];
-#pragma unroll
-        for (int r = 0; r < BJ; ++r) {
-            pcf[r] = coeff.p + ic + (int64_t)min(tj0 + r, J - 1) * coeff.sj;
-            cf_n[r] = pcf[r][0];
-        }
-        bool failed = false;
-        for (int m = 0; m < K; ++m) {
-            T cf[BJ];
-#pragma unroll
-            for (int r = 0; r < BJ; ++r) {
-                cf[r] = cf_n[r];
-                if (m + 1 < K) cf_n[r] = pcf[r][(int64_t)(m + 1) * coeff.sk];
-            }
-            const int s = USE_TMA ? m % STAGES : 0;
-            const T *S = reinterpret_cast<const T *>(base + s * Tile::stage_stride);
-            if (USE_TMA) {
-                if (!mbar_wait(&tbar[s], (m / STAGES) & 1)) failed = true;
-            } else {
-                T *D = reinterpret_cast<T *>(base);
-                for (int idx = lane; idx < Tile::box_elems; idx += 32) {
-                    const int bx = idx % Tile::BX, by = idx / Tile::BX;
-                    const int gi = ti0 - 2 + bx, gj = tj0 - 2 + by;
-                    T v = T(0);
-                    if (gi >= -2 && gi < I + 2 && gj >= -2 && gj < J + 2)
-                        v = in.p[(int64_t)gi + (int64_t)gj * in.sj + (int64_t)m * in.sk];
-                    D[idx] = v;
-                }
-                __syncwarp();
-            }
-            if (__any_sync(0xffffffffu, failed)) break;
-            bool fixed = false;
-            int E = 0;
-            if constexpr (FIX) {
-                // largest exponent among the cells the block's outputs read
-                unsigned emax = 0;
-                for (int idx = lane; idx < 36 * (BJ + 4); idx += 32) {
-                    const int ci = idx % 36 - 2, cj = idx / 36 - 2;
-                    if (!hdiff_reads(ti0 + ci, tj0 + cj, I, J)) continue;
-                    emax = max(emax, ((unsigned)__double2hiint(S[(cj + 2) * Tile::BX + ci + 2 + xs]) >> 20) & 0x7FFu);
-                }
-                E = (int)__reduce_max_sync(0xffffffffu, emax);
-                fixed = (E >= 64 && E <= 2040);
-                if (fixed) {
-                    for (int idx = lane; idx < 36 * (BJ + 4); idx += 32) {
-                        const int ci = idx % 36 - 2, cj = idx / 36 - 2;
-                        Xs[idx] = to_fixed(S[(cj + 2) * Tile::BX + ci + 2 + xs], E);
-                    }
-                    __syncwarp();
-                }
-            }
-            // the ring slot must have been consumed (level m - RING)
-            const int slot = m % RING;
-            if (m >= RING && !mbar_wait(&empty[slot], ((m / RING) - 1) & 1)) failed = true;
-            if (__any_sync(0xffffffffu, failed)) break;
-            T *hrow = H + slot * BJ * 32;
-            bool done = false;
-            if constexpr (FIX) {
-                if (fixed) {
-                    const FusedCells<T, int64_t, BJ, true> c{S, Xs, reinterpret_cast<const int64_t *>(Lraw), xs};
-                    fused_hdiff_level<BJ>(FixedF64{E}, c, reinterpret_cast<int64_t *>(Lraw), cf, hrow);
-                    done = true;
-                }
-            }
-            if (!done) {
-                const FusedCells<T, T, BJ, false> c{S, nullptr, reinterpret_cast<const T *>(Lraw), xs};
-                fused_hdiff_level<BJ>(Native<T>{}, c, reinterpret_cast<T *>(Lraw), cf, hrow);
-            }
-            __syncwarp();  // h written and the box, X and L read by every lane
-            if (lane == 0) {
-                mbar_arrive(&full[slot]);
-                if (USE_TMA && m + STAGES < K) {
-                    mbar_arrive_expect_tx(&tbar[s], Tile::box_bytes);
-                    tma_load_3d(base + s * Tile::stage_stride, &tmap, &tbar[s], hg.X0 + ti0, hg.Y0 + tj0,
-                                hg.Z0 + m + STAGES);
-                }
-            }
-        }
-        if (USE_TMA && failed && lane == 0)  // let the box loads in flight land before leaving
-            for (int s = 0; s < STAGES; ++s) mbar_wait(&tbar[s], 0), mbar_wait(&tbar[s], 1);
+    if (w >= CW) {
+        hdiff_producer<T, TI, TJ, PW, STAGES, USE_TMA>(&tmap, in, coeff, hg, ti0, tj0, base, Lay::x_off, Lay::l_off,
+                                                       Lay::e_off, tbar, RingEmit<T>{H, full, empty, NC, RING});
         return;
     }
 
     // ==================================================================== consumer warps
-    const int i = ti0 + lane, j = tj0 + w;
+    const int ci = tid % TI, cj = tid / TI;
+    const int i = ti0 + ci, j = tj0 + cj;
     const bool active = (i < I) && (j < J);
     const int ilim = g.literal ? I - 1 : I;  // last wcon column read (I-staggered unless literal)
     const int ic = min(i, I - 1), jc = min(j, J - 1), iw = min(i, ilim);
@@ -225,7 +322,7 @@ __global__ void __launch_bounds__(32 * (BJ + 1))
     const size_t cstride = (size_t)I * J, cidx = (size_t)jc * I + ic;
     N *cpb = ws;
     N *epb = ws + (size_t)K * cstride;  // e_k when it is not parked in the output
-    const bool last_lane = (lane == 31);
+    const bool row_end = (ci == TI - 1);  // wcon(i+1) is not held by the next lane
     const bool lit = g.literal != 0;
 
     const N dtr = num_const<N>(g.dtr);
@@ -245,7 +342,7 @@ __global__ void __launch_bounds__(32 * (BJ + 1))
                 sface = to_num<N, T>(wk1);
             } else {
                 T hi = __shfl_down_sync(0xffffffffu, wk1, 1);
-                if (last_lane) hi = w1k1;
+                if (row_end) hi = w1k1;
                 sface = add2<N, T>(wk1, hi);
             }
             a_next = coef<N>(sface, ka, kexp);
@@ -283,14 +380,14 @@ __global__ void __launch_bounds__(32 * (BJ + 1))
         const T ut_k = ut_n, uts_k = uts_n, w_m = w_n, w1_m = w1_n;
         if (m + 1 < K) {
             w_n = pw[(int64_t)(m + 1) * wc.sk];
-            if (last_lane) w1_n = pw1[(int64_t)(m + 1) * wc.sk];
+            if (row_end) w1_n = pw1[(int64_t)(m + 1) * wc.sk];
         }
         ut_n = put[(int64_t)m * ut.sk];
         uts_n = puts[(int64_t)m * uts.sk];
         const int slot = m % RING;
         const bool ok = mbar_wait(&full[slot], (m / RING) & 1);
-        if (!__all_sync(0xffffffffu, ok)) return;  // the producer gave up (device error word set)
-        const T h = H[(slot * BJ + w) * 32 + lane];
+        if (!__all_sync(0xffffffffu, ok)) return;  // the producers gave up (device error word set)
+        const T h = H[slot * NC + tid];
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
         if (m >= 1) vstep(m - 1, true, h_prev, h, ut_k, uts_k, w_m, w1_m);
@@ -309,6 +406,43 @@ __global__ void __launch_bounds__(32 * (BJ + 1))
             po[(int64_t)k * out.sk] = to_store<T, N>(dtr * z);
         }
     }
+}
+
+// One step of the benchmark's two stencils on their own fields, co-scheduled:
+// per CTA, the producer warps run hdiff on the 32 x BJ tile (out = hout) while
+// the BJ consumer warps run the vadv column solve of the same tile
+// (vadv_columns, the code of gtb_vadv's workspace form: same results, bit for
+// bit).  The binary64 hdiff runs on the integer pipe and the column solve on the
+// FP64 pipe, so on B300 the two overlap inside every SM.  No data passes
+// between the roles; the only block-wide barrier is the initial one.
+template <typename T, typename N, int BJ, int PW, int STAGES, bool USE_TMA, bool DPG>
+__global__ void __launch_bounds__(32 * (BJ + PW), 7 * 4 / (BJ + PW))
+    hdiff_vadv_pair_kernel(const __grid_constant__ CUtensorMap tmap, const View<const T> in,
+                           const View<const T> coeff, const View<T> hout, const View<const T> us,
+                           const View<const T> wc, const View<const T> up, const View<const T> ut,
+                           const View<const T> uts, const View<T> out, const HdiffGeom hg, const VadvGeom g,
+                           N *__restrict__ ws) {
+    using Lay = FusedLayout<T, 32, BJ, PW, STAGES, 1>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t *tbar = reinterpret_cast<uint64_t *>(base + Lay::bar_off);
+    const int tid = threadIdx.x, w = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&tbar[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // the only block-wide barrier
+    const int ti0 = blockIdx.x * 32, tj0 = blockIdx.y * BJ;
+    if (w >= BJ) {
+        hdiff_producer<T, 32, BJ, PW, STAGES, USE_TMA>(&tmap, in, coeff, hg, ti0, tj0, base, Lay::x_off, Lay::l_off,
+                                                       Lay::e_off, tbar,
+                                                       GlobalEmit<T>{hout, ti0, tj0, hg.I, hg.J, 32});
+        return;
+    }
+    const size_t cstride = (size_t)g.I * g.J;
+    vadv_columns<T, N, BJ, DPG>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws, ws + (size_t)g.K * cstride,
+                                cstride, 0, true, tid & 31, w);
 }
 
 }  // namespace gtb

@@ -408,36 +408,76 @@ static int run_halo(const gtb_field *f, int hi, int hj, const int64_t dom[3], bo
 }
 
 // ------------------------------------------------------------------ fused hdiff -> vadv
-// 2 consumer warps (64 columns) + 1 producer warp per CTA: at 256 x 256 the
-// 1024 CTAs are all resident, about 7 per SM, as the FP64 column solve needs;
-// the producer runs up to 8 levels ahead.
-constexpr int kFusedBJ = 2, kFusedStages = 2, kFusedRing = 8;
+// Column tile TI x TJ (TI*TJ/32 consumer warps) and PW producer warps per CTA,
+// measured on B300: binary64 runs best with 32 x 2 tiles (1024 CTAs at 256 x 256,
+// every column resident at once, as the FP64 column solve needs), binary32 with
+// 16 x 8 tiles (fewer halo cells per column for its lighter solve).
+template <typename T>
+struct FusedCfg;
+template <> struct FusedCfg<double> { static constexpr int TI = 32, TJ = 2, PW = 2; };
+template <> struct FusedCfg<float> { static constexpr int TI = 16, TJ = 8, PW = 2; };
+constexpr int kFusedStages = 2, kFusedRing = 8;
 
 template <typename T, typename N, bool TMA>
 static int launch_fused_t(const CUtensorMap &map, const gtb_field *const f[6], const HdiffGeom &hg,
                           const VadvGeom &g, void *ws, cudaStream_t st) {
+    using C = FusedCfg<T>;
     constexpr bool DPG = vadv_dp_global<T, N>();
     constexpr int STG = TMA ? kFusedStages : 1;
-    using Lay = FusedLayout<T, kFusedBJ, STG, kFusedRing>;
-    auto kern = hdiff_vadv_kernel<T, N, kFusedBJ, STG, kFusedRing, TMA, DPG>;
+    using Lay = FusedLayout<T, C::TI, C::TJ, C::PW, STG, kFusedRing>;
+    auto kern = hdiff_vadv_kernel<T, N, C::TI, C::TJ, C::PW, STG, kFusedRing, TMA, DPG>;
     if (prepare_kernel(kern, Lay::smem_bytes) != cudaSuccess) return launch_status("hdiff_vadv: shared-memory attribute");
-    dim3 grid((g.I + 31) / 32, (g.J + kFusedBJ - 1) / kFusedBJ);
-    kern<<<grid, 32 * (kFusedBJ + 1), Lay::smem_bytes, st>>>(map, view_of<const T>(f[0]), view_of<const T>(f[1]),
-                                                      view_of<const T>(f[2]), view_of<const T>(f[3]),
-                                                      view_of<const T>(f[4]), view_of<T>(f[5]), hg, g,
-                                                      static_cast<N *>(ws));
+    dim3 grid((g.I + C::TI - 1) / C::TI, (g.J + C::TJ - 1) / C::TJ);
+    kern<<<grid, C::TI * C::TJ + 32 * C::PW, Lay::smem_bytes, st>>>(
+        map, view_of<const T>(f[0]), view_of<const T>(f[1]), view_of<const T>(f[2]), view_of<const T>(f[3]),
+        view_of<const T>(f[4]), view_of<T>(f[5]), hg, g, static_cast<N *>(ws));
     return launch_status("hdiff_vadv launch");
 }
 
 // f = {in, coeff, wcon, utens, utens_stage, utens_stage_out}
 template <typename T, typename N>
 static int run_fused_n(const gtb_field *const f[6], const VadvGeom &g, void *ws, cudaStream_t st) {
-    using Tile = typename FusedLayout<T, kFusedBJ, kFusedStages, kFusedRing>::Tile;
+    using Tile = FusedTile<T, FusedCfg<T>::TI, FusedCfg<T>::TJ>;
     HdiffGeom hg{};
     hg.I = g.I, hg.J = g.J, hg.K = g.K;
     CUtensorMap map;
     const bool tma = encode_in_map<T>(f[0], Tile::BX, Tile::BY, hg, map);
     return tma ? launch_fused_t<T, N, true>(map, f, hg, g, ws, st) : launch_fused_t<T, N, false>(map, f, hg, g, ws, st);
+}
+
+// ------------------------------------------------------------------ co-scheduled step
+// 32 x 2 column tile: 2 vadv (consumer) warps + 2 hdiff (producer) warps per CTA,
+// at most 73 registers a thread so that 7 CTAs (every column of 256 x 256) are
+// resident per SM.
+constexpr int kPairBJ = 2, kPairPW = 2;
+
+// fh = {in, coeff, hdiff_out}; fv = {u_stage, wcon, u_pos, utens, utens_stage, utens_stage_out}
+template <typename T, typename N, bool TMA>
+static int launch_pair_t(const CUtensorMap &map, const gtb_field *const fh[3], const gtb_field *const fv[6],
+                         const HdiffGeom &hg, const VadvGeom &g, void *ws, cudaStream_t st) {
+    constexpr bool DPG = vadv_dp_global<T, N>();
+    constexpr int STG = TMA ? kFusedStages : 1;
+    using Lay = FusedLayout<T, 32, kPairBJ, kPairPW, STG, 1>;
+    auto kern = hdiff_vadv_pair_kernel<T, N, kPairBJ, kPairPW, STG, TMA, DPG>;
+    if (prepare_kernel(kern, Lay::smem_bytes) != cudaSuccess) return launch_status("step: shared-memory attribute");
+    dim3 grid((g.I + 31) / 32, (g.J + kPairBJ - 1) / kPairBJ);
+    kern<<<grid, 32 * (kPairBJ + kPairPW), Lay::smem_bytes, st>>>(
+        map, view_of<const T>(fh[0]), view_of<const T>(fh[1]), view_of<T>(fh[2]), view_of<const T>(fv[0]),
+        view_of<const T>(fv[1]), view_of<const T>(fv[2]), view_of<const T>(fv[3]), view_of<const T>(fv[4]),
+        view_of<T>(fv[5]), hg, g, static_cast<N *>(ws));
+    return launch_status("step launch");
+}
+
+template <typename T, typename N>
+static int run_pair_n(const gtb_field *const fh[3], const gtb_field *const fv[6], const VadvGeom &g, void *ws,
+                      cudaStream_t st) {
+    using Tile = FusedTile<T, 32, kPairBJ>;
+    HdiffGeom hg{};
+    hg.I = g.I, hg.J = g.J, hg.K = g.K;
+    CUtensorMap map;
+    const bool tma = encode_in_map<T>(fh[0], Tile::BX, Tile::BY, hg, map);
+    return tma ? launch_pair_t<T, N, true>(map, fh, fv, hg, g, ws, st)
+               : launch_pair_t<T, N, false>(map, fh, fv, hg, g, ws, st);
 }
 
 }  // namespace gtb
@@ -582,6 +622,70 @@ extern "C" int gtb_hdiff_vadv(const gtb_field *in, const gtb_field *coeff, const
     if (prec == GTB_PREC_F64) return run_fused_n<float, double>(f, g, workspace, st);
     if (prec == GTB_PREC_DF) return run_fused_n<float, df>(f, g, workspace, st);
     return run_fused_n<float, float>(f, g, workspace, st);
+}
+
+extern "C" int gtb_step(const gtb_field *in, const gtb_field *coeff, const gtb_field *hdiff_out,
+                        const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u_pos,
+                        const gtb_field *utens, const gtb_field *utens_stage, const gtb_field *utens_stage_out,
+                        double dtr_stage, double beta_v, int prec, unsigned flags, const int64_t *domain,
+                        void *workspace, size_t workspace_bytes, void *stream) {
+    const gtb_field *f[9] = {in, coeff, hdiff_out, u_stage, wcon, u_pos, utens, utens_stage, utens_stage_out};
+    static const char *names[9] = {"in", "coeff", "hdiff_out", "u_stage", "wcon", "u_pos", "utens", "utens_stage",
+                                   "utens_stage_out"};
+    for (int q = 0; q < 9; ++q)
+        if (!f[q]) return fail(GTB_ERR_NULL, "gtb_step: NULL field %s", names[q]);
+    const int dt = in->dtype;
+    if (!dtype_size(dt)) return fail(GTB_ERR_DTYPE, "gtb_step: unknown dtype %d", dt);
+    int rc;
+    for (int q = 0; q < 9; ++q)
+        if ((rc = check_field(names[q], f[q], dt))) return rc;
+    if (flags & ~GTB_WCON_LITERAL) return fail(GTB_ERR_ARG, "gtb_step: unknown flags 0x%x", flags);
+    if (prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return fail(GTB_ERR_ARG, "gtb_step: unknown prec %d", prec);
+    if (dt == GTB_F64 && prec != GTB_PREC_NATIVE)
+        return fail(GTB_ERR_ARG, "gtb_step: FP64 storage computes in binary64 (prec must be GTB_PREC_NATIVE)");
+    if (!(dtr_stage == dtr_stage) || !(beta_v == beta_v)) return fail(GTB_ERR_ARG, "gtb_step: NaN scalar");
+    const bool literal = flags & GTB_WCON_LITERAL;
+    const Reach r_in{{2, 2, 0}, {2, 2, 0}}, r0{{0, 0, 0}, {0, 0, 0}}, rw{{0, 0, 0}, {literal ? 0 : 1, 0, 0}};
+    const Reach *reach[9] = {&r_in, &r0, &r0, &r0, &rw, &r0, &r0, &r0, &r0};
+    int64_t dom[3] = {INT64_MAX, INT64_MAX, INT64_MAX};
+    if (!domain)
+        for (int q = 0; q < 9; ++q) shrink_domain(f[q], *reach[q], dom);
+    if ((rc = resolve_domain(domain, dom))) return rc;
+    for (int q = 0; q < 9; ++q)
+        if ((rc = check_extent(names[q], f[q], *reach[q], dom))) return rc;
+    // hdiff_out overlaps nothing; utens_stage_out overlaps nothing but possibly utens_stage itself
+    for (int q = 0; q < 9; ++q)
+        if (q != 2 && overlaps(hdiff_out, f[q]))
+            return fail(GTB_ERR_ALIAS, "gtb_step: hdiff_out overlaps %s", names[q]);
+    for (int q = 0; q < 8; ++q) {
+        if (q == 7 && same_view(utens_stage_out, utens_stage)) continue;  // in place
+        if (q != 2 && overlaps(utens_stage_out, f[q]))
+            return fail(GTB_ERR_ALIAS, "gtb_step: utens_stage_out overlaps %s", names[q]);
+    }
+    if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
+    const size_t need = vadv_ws_bytes_for(dt, prec, dom);
+    if (!workspace || workspace_bytes < need)
+        return fail(GTB_ERR_ARG, "gtb_step: a workspace of %zu bytes is required (got %zu)", need,
+                    workspace ? workspace_bytes : (size_t)0);
+    if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
+        return fail(GTB_ERR_LAYOUT, "gtb_step: workspace must be 16-byte aligned");
+    {
+        const int64_t n = (int64_t)(workspace_bytes / dtype_size(dt));
+        const gtb_field wsf{workspace, dt, 0, {n, 1, 1}, {1, n, n}, {0, 0, 0}};
+        for (int q = 0; q < 9; ++q)
+            if (overlaps(&wsf, f[q])) return fail(GTB_ERR_ALIAS, "gtb_step: workspace overlaps %s", names[q]);
+    }
+    const VadvGeom g = make_vadv_geom(dom, literal, dtr_stage, beta_v);
+    const gtb_field *fh[3] = {in, coeff, hdiff_out};
+    const gtb_field *fv[6] = {u_stage, wcon, u_pos, utens, utens_stage, utens_stage_out};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (dt == GTB_F64) return run_pair_n<double, double>(fh, fv, g, workspace, st);
+    // binary32 storage: hdiff is bound by HBM and the column solve by the FP32 pipe;
+    // on B300 the two separate kernels back to back are faster than sharing SMs
+    if ((rc = run_hdiff<float>(in, coeff, hdiff_out, dom, st))) return rc;
+    if (prec == GTB_PREC_F64) return run_vadv_n<float, double>(fv, g, workspace, workspace_bytes, st);
+    if (prec == GTB_PREC_DF) return run_vadv_n<float, df>(fv, g, workspace, workspace_bytes, st);
+    return run_vadv_n<float, float>(fv, g, workspace, workspace_bytes, st);
 }
 
 extern "C" size_t gtb_hdiff_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain) {

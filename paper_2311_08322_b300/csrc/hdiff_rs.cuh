@@ -281,11 +281,23 @@ __device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const Vie
                 // unread halo corners, whose contents are arbitrary)
                 const int ntile = min(G::TI, g.I - ti0);
                 const int wx = ntile + 4, wy = nrows + 4;
+                // a strip at a corner of the domain first zeroes, in its copy of the box,
+                // the halo cells that the definition never reads (their contents are arbitrary)
+                if ((ti0 == 0 || ti0 + ntile == g.I) && (tj0 + cj0 == 0 || tj0 + cj0 + nrows == g.J)) {
+                    if (lane < 12) {
+                        const int c = lane / 3, e = lane % 3;
+                        const int di = e == 2 ? -1 : -2, dj = e == 1 ? -1 : -2;
+                        const int gi = (c & 1) ? g.I - 1 - di : di, gj = (c & 2) ? g.J - 1 - dj : dj;
+                        const int cx = gi - ti0 + 2, cy = gj - tj0 - cj0 + 2;
+                        if (cx >= 0 && cx < wx && cy >= 0 && cy < wy)
+                            const_cast<T *>(S)[(cy + cj0) * G::BX + cx + xs] = T(0);
+                    }
+                    fence_proxy_async_shared();  // before the stage's next TMA refill
+                    __syncwarp();
+                }
                 unsigned emax = 0;
                 for (int idx = lane; idx < wx * wy; idx += 32) {
-                    const int cx = idx % wx, cy = idx / wx;
-                    if (!hdiff_reads(ti0 + cx - 2, tj0 + cj0 + cy - 2, g.I, g.J)) continue;
-                    const int bx = cx + xs, by = cy + cj0;
+                    const int bx = idx % wx + xs, by = idx / wx + cj0;
                     emax = max(emax, ((unsigned)__double2hiint(S[by * G::BX + bx]) >> 20) & 0x7FFu);
                 }
                 const int E = (int)__reduce_max_sync(0xffffffffu, emax);

@@ -5,7 +5,7 @@
 // the specialised intervals).
 //
 // Mapping: one thread per column, 32 consecutive i per warp (coalesced loads
-// of every level), K streamed.  The forward sweep keeps the eliminated
+// of every level), K streamed, inputs loaded one level ahead.  The forward sweep keeps the eliminated
 // coefficients c'_k and d'_k of its column in shared memory ([k][thread]
 // layout, conflict-free); the backward sweep reads them back.  wcon(i+1) comes
 // from the neighbouring lane by a warp shuffle, the last lane loading its own.
@@ -137,8 +137,7 @@ template <typename T, typename N, int BJ, bool DPG>
 __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                              const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                              const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
-                                             size_t cidx_ws, bool ws_domain) {
-    const int tx = threadIdx.x, ty = threadIdx.y;
+                                             size_t cidx_ws, bool ws_domain, int tx, int ty) {
     const int i = bx * 32 + tx, j = by * BJ + ty;
     const bool active = (i < g.I) && (j < g.J);
     const int ic = min(i, g.I - 1), jc = min(j, g.J - 1);
@@ -166,9 +165,10 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
     const int kexp = g.ka_pow2;  // a = ka * s as an exact exponent shift when ka = -2^kexp
 
 #define GTB_LOAD(L, k) load_level<T>(L, k, K, pup, put, puts, pus, pw, pw1, up.sk, ut.sk, uts.sk, us.sk, wc.sk, last_lane)
-    Level<T> L0, L1;  // levels k, k+1 (prefetch distance 2)
+    // level k's inputs in L0; level k+1's are loaded at the top of iteration k (one
+    // level ahead: on B300 a deeper prefetch only costs registers, i.e. resident warps)
+    Level<T> L0, L1;
     GTB_LOAD(L0, 0);
-    GTB_LOAD(L1, 1);
 
     T us_cur = pus[0];
     N dm = zero;                    // u_stage_{k-1} - u_stage_k
@@ -176,6 +176,7 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
     N cp_prev = zero, dp_prev = zero;
 
     for (int k = 0; k < K; ++k) {
+        GTB_LOAD(L1, k + 1);
         const bool has_next = (k + 1 < K);
         N a_next = zero, as_next = zero, dpl = zero;
         if (has_next) {
@@ -214,7 +215,6 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
         dm = -dpl;
         a_cur = a_next, as_cur = as_next;
         L0 = L1;
-        GTB_LOAD(L1, k + 2);
     }
 #undef GTB_LOAD
 
@@ -242,11 +242,11 @@ __global__ void __launch_bounds__(32 * BJ)
     if (WS) {
         const size_t cstride = (size_t)g.I * g.J;
         vadv_columns<T, N, BJ, DPG>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws, ws + (size_t)g.K * cstride,
-                                    cstride, 0, true);
+                                    cstride, 0, true, threadIdx.x, threadIdx.y);
     } else {
         N *cpb = reinterpret_cast<N *>(smem_raw);
         vadv_columns<T, N, BJ, DPG>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, cpb, cpb + (size_t)g.K * NT,
-                                    NT, t, false);
+                                    NT, t, false, threadIdx.x, threadIdx.y);
     }
 }
 

@@ -55,7 +55,7 @@ _lib = None
 EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_hdiff_adj", "gtb_vadv_adj",
            "gtb_vadv_adj_workspace_bytes", "gtb_halo_periodic", "gtb_halo_periodic_adj", "gtb_device_status",
            "gtb_batch_plan", "gtb_batch_run", "gtb_plan_info", "gtb_plan_destroy", "gtb_hdiff_vadv",
-           "gtb_hdiff_vadv_workspace_bytes", "gtb_last_error", "gtb_version")
+           "gtb_hdiff_vadv_workspace_bytes", "gtb_step", "gtb_last_error", "gtb_version")
 GTB_ADJ_ACCUMULATE = 2
 
 
@@ -81,6 +81,9 @@ def lib() -> ctypes.CDLL:
         L.gtb_hdiff_vadv.argtypes = [P, P, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_uint, i64p, vp, ctypes.c_size_t, vp]
         L.gtb_hdiff_vadv.restype = ctypes.c_int
+        L.gtb_step.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                               ctypes.c_uint, i64p, vp, ctypes.c_size_t, vp]
+        L.gtb_step.restype = ctypes.c_int
         L.gtb_hdiff_vadv_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, i64p]
         L.gtb_hdiff_vadv_workspace_bytes.restype = ctypes.c_size_t
         L.gtb_halo_periodic.argtypes = [P, ctypes.c_int, ctypes.c_int, i64p, vp]
@@ -290,6 +293,29 @@ def hdiff_vadv(in_, coeff, wcon, utens, utens_stage, out=None, *, dtr_stage=3.0 
                                 PREC[prec] if isinstance(prec, str) else int(prec),
                                 GTB_WCON_LITERAL if literal else 0, _dom(domain),
                                 ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes, _stream(stream)))
+    return out
+
+
+def step(in_, coeff, hdiff_out, u_stage, wcon, u_pos, utens, utens_stage, out=None, *, dtr_stage=3.0 / 20.0,
+         beta_v=0.0, prec="native", literal=False, domain=None, workspace="auto", stream=None):
+    """Both benchmark stencils on their own fields in one co-scheduled kernel (gtb_step):
+    hdiff_out = hdiff(in_, coeff); out = vadv(u_stage, wcon, u_pos, utens, utens_stage)
+    (``out=None`` updates utens_stage in place).  ``workspace``: "auto" or a CUDA tensor."""
+    out = utens_stage if out is None else out
+    fs = [_as_field(x) for x in (in_, coeff, hdiff_out, u_stage, wcon, u_pos, utens, utens_stage, out)]
+    ws_ptr, ws_bytes = None, 0
+    if isinstance(workspace, str):
+        # deduced domain: in reaches 2 points in I and J, wcon one point above I
+        reach = [(2, 2, 0), (0, 0, 0), (0, 0, 0), (0, 0, 0), (0 if literal else 1, 0, 0)] + [(0, 0, 0)] * 4
+        dom = tuple(domain) if domain is not None else tuple(
+            max(0, min(f.shape[d] - f.origin[d] - r[d] for f, r in zip(fs, reach))) for d in range(3))
+        need = vadv_workspace_bytes(fs[0].dtype, prec, dom)
+        workspace = globals()["workspace"](need, stream) if need else None
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    _check(lib().gtb_step(*[ctypes.byref(f) for f in fs], float(dtr_stage), float(beta_v),
+                          PREC[prec] if isinstance(prec, str) else int(prec), GTB_WCON_LITERAL if literal else 0,
+                          _dom(domain), ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes, _stream(stream)))
     return out
 
 

@@ -160,3 +160,35 @@ def test_hdiff_vadv_validation(L):
     # the deduced domain: min over fields of shape - origin - reach (in: 12-2-2 = 8, wcon: 10-1-1 = 8)
     assert L.lib().gtb_hdiff_vadv_workspace_bytes(2, 0, (ctypes.c_int64 * 3)(8, 8, 6)) == 8 * 8 * 8 * 6
     assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 2, (ctypes.c_int64 * 3)(8, 8, 6)) == 16 * 8 * 8 * 6
+
+
+def test_step_validation(L):
+    """gtb_step: the checks of gtb_hdiff and gtb_vadv over one shared domain, a
+    required workspace, hdiff_out overlapping nothing."""
+    G = 1 << 24
+    fin = lambda n, o=(2, 2, 0): fake(L, 12, 12, 6, origin=o, ptr=n * G)
+    mk = lambda n, o=(1, 1, 0): fake(L, 10, 10, 6, origin=o, ptr=n * G)
+    fs = [fin(1), fin(2), fin(3)] + [mk(n) for n in range(4, 10)]
+    lib = L.lib()
+
+    def call(fs, dom=(8, 8, 6), prec=0, flags=0, ws=None, wsb=0):
+        d = None if dom is None else (ctypes.c_int64 * 3)(*dom)
+        return lib.gtb_step(*[ctypes.byref(f) for f in fs], 0.15, 0.0, prec, flags, d,
+                            None if ws is None else ctypes.c_void_p(ws), wsb, None)
+
+    ok_ws = dict(ws=40 * G, wsb=1 << 20)
+    assert call(fs, dom=(8, 0, 6)) == 0                           # empty domain
+    assert call(fs) == -9                                          # workspace required
+    assert call(fs, ws=40 * G, wsb=100) == -9                      # too small
+    assert call(fs, ws=40 * G + 8, wsb=1 << 20) == -4              # misaligned
+    assert call(fs, ws=5 * G, wsb=1 << 20) == -5                   # overlaps wcon
+    assert call(fs, dom=(9, 8, 6), **ok_ws) == -3                  # wcon needs i+1
+    assert call(fs, prec=2, **ok_ws) == -9                         # FP64 storage: binary64 only
+    assert call(fs, flags=8, **ok_ws) == -9
+    assert call(fs[:2] + [fin(1)] + fs[3:], **ok_ws) == -5         # hdiff_out on in
+    assert call(fs[:2] + [mk(4)] + fs[3:], **ok_ws) == -5          # hdiff_out on u_stage
+    assert call(fs[:8] + [mk(6)], **ok_ws) == -5                   # vadv output on u_pos
+    assert call(fs[:8] + [fin(3)], **ok_ws) == -5                  # vadv output on hdiff_out
+    assert call(fs[:8] + [mk(8, o=(1, 2, 0))], **ok_ws) == -5      # shifted view of utens_stage
+    fs_dt = fs[:6] + [fake(L, 10, 10, 6, origin=(1, 1, 0), dtype=1, ptr=7 * G)] + fs[7:]
+    assert call(fs_dt, **ok_ws) == -2

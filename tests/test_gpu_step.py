@@ -1,0 +1,148 @@
+"""GPU parity of gtb_step: the benchmark's two stencils on their own fields in
+one co-scheduled kernel (GT4Py paper Sec. 3.1).  hdiff_out against the FP64
+oracle (1e-12 max-norm relative; FP32 storage 1e-5 on the FP32-rounded
+inputs); utens_stage_out against gtb_vadv with the same workspace form, bit
+for bit (the same column code), and through it against the oracle."""
+import numpy as np
+import pytest
+
+from helpers import region, rel_err
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+F32_TOL = 1e-5
+VN = ("u_stage", "wcon", "u_pos", "utens", "utens_stage")
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    from paper_2311_08322_b300 import build, gtb
+    assert torch.cuda.is_available()
+    build.build()
+    return gtb
+
+
+def draw(I, J, K, seed, wamp=0.5):
+    rng = np.random.default_rng(seed)
+    hs, vs = (K, J + 4, I + 4), (K, J + 2, I + 2)
+    f = dict(inp=rng.uniform(-1, 1, hs), coeff=rng.uniform(0, 0.025, hs))
+    for n in ("u_stage", "u_pos", "utens", "utens_stage"):
+        f[n] = rng.uniform(-1, 1, vs)
+    f["wcon"] = rng.uniform(-wamp, wamp, vs)
+    return f
+
+
+def run(G, f, dom, dtype=np.float64, prec="native", beta_v=0.0, literal=False, inplace=False, contiguous=False):
+    """(hdiff_out, utens_stage_out) of gtb_step, and utens_stage_out of gtb_vadv."""
+    import torch
+    g = {k: v.astype(dtype) for k, v in f.items()}
+    if contiguous:
+        sin, scf = (G.Storage(torch.from_numpy(g[k]).cuda(), (2, 2, 0)) for k in ("inp", "coeff"))
+    else:
+        sin, scf = G.storage_from(g["inp"], (2, 2, 0)), G.storage_from(g["coeff"], (2, 2, 0))
+    hout = G.storage_from(np.zeros_like(g["coeff"]), (2, 2, 0))
+    sv = {n: G.storage_from(g[n], (1, 1, 0)) for n in VN}
+    vout = sv["utens_stage"] if inplace else G.storage_from(np.zeros_like(g["utens"]), (1, 1, 0))
+    kw = dict(prec=prec, beta_v=beta_v, literal=literal, domain=dom)
+    ref_v = G.storage_from(np.zeros_like(g["utens"]), (1, 1, 0))
+    G.vadv(*[sv[n] for n in VN], ref_v, **kw)  # before an in-place step overwrites utens_stage
+    G.step(sin, scf, hout, *[sv[n] for n in VN], vout, **kw)
+    G.device_status()
+    return (region(hout.numpy(), (2, 2, 0), dom), region(vout.numpy(), (1, 1, 0), dom),
+            region(ref_v.numpy(), (1, 1, 0), dom))
+
+
+def oracle(orc, f, dom, beta_v=0.0, literal=False):
+    h = region(orc.hdiff(f["inp"], f["coeff"], origin_in=(2, 2, 0), domain=dom), (2, 2, 0), dom)
+    v = region(orc.vadv(*[f[n] for n in VN], origin=(1, 1, 0), domain=dom, beta_v=beta_v,
+                        wmode=1 if literal else 0), (1, 1, 0), dom)
+    return h, v
+
+
+def test_256_fp64_full_field(G, orc):
+    """256x256x80 FP64, the benchmark's workload and launch configuration."""
+    dom = (256, 256, 80)
+    f = draw(*dom, 0)
+    h, v, v1 = run(G, f, dom)
+    rh, rv = oracle(orc, f, dom)
+    assert rel_err(h, rh) <= F64_TOL
+    assert np.array_equal(v, v1)
+    assert rel_err(v, rv) <= F64_TOL
+
+
+@pytest.mark.parametrize("I,J,K", [(64, 64, 40), (96, 40, 37), (33, 7, 1), (1, 1, 2), (31, 5, 3), (70, 9, 137),
+                                   (3, 65, 17)])
+def test_shapes_fp64(G, orc, I, J, K):
+    dom = (I, J, K)
+    f = draw(*dom, I * J + K)
+    h, v, v1 = run(G, f, dom)
+    rh, rv = oracle(orc, f, dom)
+    assert rel_err(h, rh) <= F64_TOL
+    assert np.array_equal(v, v1)
+    assert rel_err(v, rv) <= F64_TOL
+
+
+@pytest.mark.parametrize("beta_v,literal,inplace", [(0.3, False, False), (0.0, True, True), (-0.2, True, False)])
+def test_options_fp64(G, orc, beta_v, literal, inplace):
+    dom = (96, 40, 37)
+    f = draw(*dom, 5)
+    h, v, v1 = run(G, f, dom, beta_v=beta_v, literal=literal, inplace=inplace)
+    rh, rv = oracle(orc, f, dom, beta_v, literal)
+    assert rel_err(h, rh) <= F64_TOL
+    assert np.array_equal(v, v1)
+    assert rel_err(v, rv) <= F64_TOL
+
+
+def test_unpadded_in_fp64(G, orc):
+    """in as a plain tensor (pitch not a 16-byte multiple): no TMA, producer loads."""
+    dom = (71, 9, 12)
+    f = draw(*dom, 7)
+    h, v, v1 = run(G, f, dom, contiguous=True)
+    rh, rv = oracle(orc, f, dom)
+    assert rel_err(h, rh) <= F64_TOL and np.array_equal(v, v1)
+
+
+def test_unread_corners_and_nonfinite_fp64(G, orc):
+    """Arbitrary values in the unread halo corners change nothing; an inf in a read
+    cell gives the oracle's non-finite pattern."""
+    dom = (40, 12, 3)
+    f = draw(*dom, 10)
+    I, J = dom[0], dom[1]
+    for (ci, cj) in ((-2, -2), (-2, -1), (-1, -2)):
+        for (si, sj) in ((1, 1), (-1, 1), (1, -1), (-1, -1)):
+            i = ci if si > 0 else I - 1 - ci
+            j = cj if sj > 0 else J - 1 - cj
+            f["inp"][:, j + 2, i + 2] = 1e300
+    f["inp"][1, 7, 20] = np.inf
+    h, v, v1 = run(G, f, dom)
+    rh, _ = oracle(orc, f, dom)
+    fin = np.isfinite(rh)
+    assert (~fin).sum() > 0 and np.array_equal(fin, np.isfinite(h))
+    assert rel_err(h[fin], rh[fin]) <= F64_TOL
+    assert np.array_equal(v, v1)
+
+
+@pytest.mark.parametrize("prec", ["native", "f64", "df"])
+def test_fp32_storage(G, orc, prec):
+    dom = (96, 40, 37)
+    f = draw(*dom, 3)
+    h, v, v1 = run(G, f, dom, np.float32, prec)
+    f32 = {k: a.astype(np.float32).astype(np.float64) for k, a in f.items()}
+    rh, rv = oracle(orc, f32, dom)
+    assert rel_err(h, rh) <= F32_TOL
+    assert np.array_equal(v, v1)
+    if prec != "native":
+        assert rel_err(v, rv) <= F32_TOL
+
+
+def test_workspace_required(G):
+    dom = (8, 8, 4)
+    f = draw(*dom, 1)
+    sin, scf = G.storage_from(f["inp"], (2, 2, 0)), G.storage_from(f["coeff"], (2, 2, 0))
+    hout = G.storage_from(np.zeros_like(f["coeff"]), (2, 2, 0))
+    sv = {n: G.storage_from(f[n], (1, 1, 0)) for n in VN}
+    with pytest.raises(G.GtbError) as e:
+        G.step(sin, scf, hout, *[sv[n] for n in VN], workspace=None)
+    assert e.value.code == -9
