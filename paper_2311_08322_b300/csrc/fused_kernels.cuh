@@ -14,7 +14,9 @@
 //     TMA (STAGES-deep ring); binary64 storage converts it to exact int64 fixed
 //     point (the form of hdiff_rs: E = the largest exponent among the cells the
 //     tile's outputs read; a level whose E leaves [64, 2040] uses the
-//     definition in binary64), forms the Laplacian on (TI+2) x (TJ+2) cells,
+//     definition in binary64; the result goes back to binary64 on the integer
+//     pipe, leaving the FP64 pipe to the column solve), forms the Laplacian on
+//     (TI+2) x (TJ+2) cells,
 //     the limited fluxes and h of the tile into a RING-deep shared ring (the
 //     integer-pipe bound part).  A squarer tile needs fewer halo cells per
 //     column: (TI+4)(TJ+4)/(TI TJ) conversions, (TI+2)(TJ+2)/(TI TJ) Laplacians.
@@ -262,7 +264,8 @@ __device__ __forceinline__ void hdiff_producer(const CUtensorMap *tmap, const Vi
             if (fixed) {
                 producer_sync<PW>();  // X complete
                 const FusedCells<T, int64_t, TI, TJ, true> c{S, Xs, reinterpret_cast<const int64_t *>(Lraw), xs};
-                fused_hdiff_level<TI, TJ, PW>(FixedF64{(int)E}, c, reinterpret_cast<int64_t *>(Lraw), pt, cf, m, em);
+                fused_hdiff_level<TI, TJ, PW>(FixedF64T<true>{(int)E}, c, reinterpret_cast<int64_t *>(Lraw), pt, cf,
+                                              m, em);
                 done = true;
             }
         }

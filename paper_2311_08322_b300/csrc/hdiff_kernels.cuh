@@ -97,6 +97,25 @@ __device__ __forceinline__ double from_fixed(int64_t D, int E) {
     return D == 0 ? 0.0 : __hiloint2double(hi, __double2loint(d));
 }
 
+// The same value, bit for bit, computed on the integer pipe, for kernels whose
+// FP64 pipe is the bottleneck (hdiff sharing SMs with the column solve): |D| has its leading
+// one at bit msb; its top 53 bits form the significand m, the bits shifted out
+// round it to nearest, ties to even (IEEE 754-2019, 4.3.1); the biased exponent
+// is msb + 1023 + (E - 1078), always normal in that range.  The significand
+// (implicit bit included) is added to the exponent field less one, so a
+// rounding carry into bit 53 raises the exponent by itself.
+__device__ __forceinline__ double from_fixed_int(int64_t D, int E) {
+    if (D == 0) return 0.0;
+    const uint64_t u = D < 0 ? 0ull - (uint64_t)D : (uint64_t)D;
+    const int msb = 63 - __clzll((long long)u);
+    const int sh = max(msb - 52, 0), ls = max(52 - msb, 0);
+    uint64_t m = (u << ls) >> sh;
+    const uint64_t rem = u & ((1ull << sh) - 1ull), half = sh ? 1ull << (sh - 1) : 1ull;
+    m += (sh != 0) & ((rem > half) | ((rem == half) & (unsigned)(m & 1ull)));
+    const uint64_t bits = ((uint64_t)(msb + E - 1078 + 1023 - 1) << 52) + m;
+    return __longlong_as_double((long long)(bits | (D < 0 ? 0x8000000000000000ull : 0ull)));
+}
+
 // Exact sign of x1 - x0 for finite binary64 values (-0 == +0).
 __device__ __forceinline__ int exact_dir(int64_t X1, int64_t X0, double x1, double x0) {
     if (X1 != X0) return X1 > X0 ? 1 : -1;

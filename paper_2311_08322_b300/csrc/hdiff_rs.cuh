@@ -38,7 +38,10 @@ struct Native {
     __device__ __forceinline__ T out(T in, T c, V D) const { return in - c * D; }
 };
 
-struct FixedF64 {
+// ICVT: convert the flux divergence back to binary64 on the integer pipe
+// (from_fixed_int) instead of the FP64 pipe (from_fixed); the same results.
+template <bool ICVT>
+struct FixedF64T {
     using V = int64_t;
     using Gd = int;
     int E;
@@ -50,8 +53,11 @@ struct FixedF64 {
         return exact_dir(x1, x0, *p1, *p0);
     }
     __device__ __forceinline__ V limit(V f, Gd g) const { return ((f > 0 && g > 0) || (f < 0 && g < 0)) ? 0 : f; }
-    __device__ __forceinline__ double out(double in, double c, V D) const { return fma(-c, from_fixed(D, E), in); }
+    __device__ __forceinline__ double out(double in, double c, V D) const {
+        return fma(-c, ICVT ? from_fixed_int(D, E) : from_fixed(D, E), in);
+    }
 };
+using FixedF64 = FixedF64T<false>;
 
 template <typename T, int CPL, int W, int R>
 struct RsTile {
