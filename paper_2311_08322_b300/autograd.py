@@ -4,7 +4,8 @@ One step of the chain, on a periodic (I, J) domain of K levels:
     field storage <- field (interior, halo refreshed periodically, 2 points)
     h             <- hdiff(field, coeff)
     field'        <- vadv(u_stage = h, u_pos = h, utens, utens_stage, wcon)
-utens, utens_stage and wcon are fixed inputs of every step.  The step's
+utens, utens_stage and wcon are fixed inputs of every step.  The forward runs
+the two stencils as one kernel (gtb_hdiff_vadv: h never leaves the chip).  The step's
 backward runs the hand-written adjoint kernels (gtb_vadv_adj with the u_stage
 and u_pos cotangents merged, gtb_hdiff_adj with the limiter recomputed from
 the saved input, gtb_halo_periodic_adj) — no autodiff of the stencils.  Each
@@ -59,11 +60,11 @@ class ChainStep(torch.autograd.Function):
         fs.interior((I, J, K)).copy_(field)
         gtb.halo_periodic(fs, 2, 2, domain=(I, J, K))
         cs = _as_storage(coeff)
-        h = interior_storage(I, J, K, field.dtype, field.device)
-        gtb.hdiff(fs, cs, h, domain=(I, J, K))
         y = interior_storage(I, J, K, field.dtype, field.device)
-        gtb.vadv(h, fixed.wcon, h, fixed.utens, fixed.utens_stage, y, dtr_stage=fixed.dtr_stage,
-                 beta_v=fixed.beta_v, prec=fixed.prec, domain=(I, J, K))
+        # h = hdiff(field, coeff) and y = vadv(h, wcon, h, utens, utens_stage) in one kernel
+        # (h stays on chip; the backward needs only the checkpointed input)
+        gtb.hdiff_vadv(fs, cs, fixed.wcon, fixed.utens, fixed.utens_stage, y, dtr_stage=fixed.dtr_stage,
+                       beta_v=fixed.beta_v, prec=fixed.prec, domain=(I, J, K))
         ctx.fixed = fixed
         ctx.fs, ctx.cs = fs, cs  # the checkpoint: this step's input (with its halo) and coeff
         return y.data.clone()

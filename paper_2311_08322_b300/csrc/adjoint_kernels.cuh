@@ -153,14 +153,18 @@ struct HadjTile {
     static constexpr int QX = TI + 4, QY = TJ + 4;   // q, lap: tile +- 2
     static constexpr int GXX = TI + 3, GXY = TJ + 2; // x-faces: i in [-2, TI], rows tile +- 1
     static constexpr int GYX = TI + 2, GYY = TJ + 3; // y-faces: cols tile +- 1, j in [-2, TJ]
-    static constexpr int LX = TI + 2, LY = TJ + 2;   // lb: tile +- 1
-    // per face: its cotangent g and its forward (limited) value f
-    static constexpr int elems = IX * IY + 2 * QX * QY + 2 * (GXX * GXY + GYX * GYY) + LX * LY;
+    static constexpr int LX = TI + 2, LY = TJ + 2;   // lb: tile +- 1 (kept in the q region)
+    static constexpr int NF = GXX * GXY + GYX * GYY; // faces
+    // slots of sizeof(T) bytes: in (binary64: or its fixed-point copy, in place), q then
+    // lb, lap, face cotangents; then one keep byte per face
+    static constexpr int slots = IX * IY + 2 * QX * QY + NF;
+    static_assert(LX * LY <= QX * QY, "lb fits the q region");
 };
 
 template <typename T, int TI, int TJ>
 constexpr int hdiff_adj_smem_bytes() {
-    return HadjTile<T, TI, TJ>::elems * (int)sizeof(T) + 64;
+    using H = HadjTile<T, TI, TJ>;
+    return H::slots * (int)sizeof(T) + ((H::NF + 15) / 16) * 16 + 64;
 }
 
 struct HadjGeom {
@@ -183,108 +187,202 @@ __device__ __forceinline__ bool limited(T f, T g) {
     }
 }
 
+// The adjoint of one tile (staged in shared memory by the caller: in at
+// tile +- 3, q = coeff * out_bar at tile +- 2, in the 8-byte slots of S_x and
+// S_q) with the arithmetic of policy P: V is the value type of in, lap, fluxes
+// and cotangents; cvt_in / cvt_q bring in and q to V in place, lap /
+// limited_face / out_* do the rest.
+//   faces:  keep = not (f * (in[+1] - in) > 0),  g = keep (q - q[+1])
+//   lb      = (gx[i-1] - gx[i]) + (gy[j-1] - gy[j])      (cotangent of lap)
+//   in_bar  = out_bar - (4 lb - sum of the 4 neighbours of lb)
+//   coeff_bar = -D out_bar,  D = (fx[i] - fx[i-1]) + (fy[j] - fy[j-1]),  f = keep (lap[+1] - lap)
+template <typename T, int TI, int TJ, int NT, typename P>
+__device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x, typename P::V *S_q,
+                                               unsigned char *S_keep, const View<const T> &in,
+                                               const View<const T> &ob, const View<T> &ib, const View<T> &cb,
+                                               const HadjGeom &g, int ti0, int tj0, int k) {
+    using V = typename P::V;
+    using H = HadjTile<T, TI, TJ>;
+    V *S_lap = S_q + H::QX * H::QY;   // forward lap, same region as q
+    V *S_gx = S_lap + H::QX * H::QY;  // x-face cotangents, faces i in [-2, TI], rows [-1, TJ]
+    V *S_gy = S_gx + H::GXX * H::GXY; // y-face cotangents, cols [-1, TI], faces j in [-2, TJ]
+    V *S_lb = S_q;                    // lap cotangents, tile +- 1 (q is dead by then)
+    unsigned char *S_kx = S_keep, *S_ky = S_keep + H::GXX * H::GXY;
+    const int tid = threadIdx.x, I = g.I, J = g.J;
+    if (P::kConvert) {  // in place: each slot converted by the thread that reads it
+        for (int idx = tid; idx < H::IX * H::IY; idx += NT) S_x[idx] = pol.cvt_in(S_x[idx]);
+        for (int idx = tid; idx < H::QX * H::QY; idx += NT) S_q[idx] = pol.cvt_q(S_q[idx]);
+        __syncthreads();
+    }
+    auto X = [&](int a, int b) -> V { return S_x[(a + 3) + (b + 3) * H::IX]; };  // tile-relative
+    auto GIN = [&](int a, int b) -> const T * {  // the binary64 value, for exact ties
+        return in.p + (ti0 + a) + (int64_t)(tj0 + b) * in.sj + (int64_t)k * in.sk;
+    };
+    for (int idx = tid; idx < H::QX * H::QY; idx += NT) {
+        const int a = idx % H::QX - 2, b = idx / H::QX - 2;
+        S_lap[idx] = pol.lap(X(a, b), X(a + 1, b), X(a - 1, b), X(a, b + 1), X(a, b - 1));
+    }
+    __syncthreads();
+    auto LAP = [&](int a, int b) -> V { return S_lap[(a + 2) + (b + 2) * H::QX]; };
+    auto Q = [&](int a, int b) -> V { return S_q[(a + 2) + (b + 2) * H::QX]; };
+    // every face once: keep/zero from the forward values and its cotangent
+    // (a face exists for domain-relative i in [-1, I-1], j in [0, J) in x, and likewise in y)
+    for (int idx = tid; idx < H::GXX * H::GXY; idx += NT) {
+        const int a = idx % H::GXX - 2, b = idx / H::GXX - 1;  // face between cells a and a+1, row b
+        const int da = ti0 + a, db = tj0 + b;
+        V gv = V(0);
+        bool keep = false;
+        if (da >= -1 && da <= I - 1 && db >= 0 && db < J) {
+            keep = !pol.limited_face(LAP(a + 1, b) - LAP(a, b), X(a + 1, b), X(a, b), GIN(a + 1, b), GIN(a, b));
+            if (keep) gv = Q(a, b) - Q(a + 1, b);
+        }
+        S_gx[idx] = gv;
+        S_kx[idx] = keep;
+    }
+    for (int idx = tid; idx < H::GYX * H::GYY; idx += NT) {
+        const int a = idx % H::GYX - 1, b = idx / H::GYX - 2;  // face between rows b and b+1, column a
+        const int da = ti0 + a, db = tj0 + b;
+        V gv = V(0);
+        bool keep = false;
+        if (da >= 0 && da < I && db >= -1 && db <= J - 1) {
+            keep = !pol.limited_face(LAP(a, b + 1) - LAP(a, b), X(a, b + 1), X(a, b), GIN(a, b + 1), GIN(a, b));
+            if (keep) gv = Q(a, b) - Q(a, b + 1);
+        }
+        S_gy[idx] = gv;
+        S_ky[idx] = keep;
+    }
+    __syncthreads();
+    auto GX = [&](int a, int b) -> V { return S_gx[(a + 2) + (b + 1) * H::GXX]; };
+    auto GY = [&](int a, int b) -> V { return S_gy[(a + 1) + (b + 2) * H::GYX]; };
+    for (int idx = tid; idx < H::LX * H::LY; idx += NT) {
+        const int a = idx % H::LX - 1, b = idx / H::LX - 1;
+        S_lb[idx] = (GX(a - 1, b) - GX(a, b)) + (GY(a, b - 1) - GY(a, b));
+    }
+    __syncthreads();
+    auto LB = [&](int a, int b) -> V { return S_lb[(a + 1) + (b + 1) * H::LX]; };
+    auto FX = [&](int a, int b) -> V {  // forward x-flux of face (a, a+1) in row b, 0 where limited
+        return S_kx[(a + 2) + (b + 1) * H::GXX] ? LAP(a + 1, b) - LAP(a, b) : V(0);
+    };
+    auto FY = [&](int a, int b) -> V {
+        return S_ky[(a + 1) + (b + 2) * H::GYX] ? LAP(a, b + 1) - LAP(a, b) : V(0);
+    };
+    for (int idx = tid; idx < TI * TJ; idx += NT) {
+        const int a = idx % TI, b = idx / TI;
+        const int da = ti0 + a, db = tj0 + b;
+        if (da < -2 || da >= I + 2 || db < -2 || db >= J + 2) continue;
+        const V tr = pol.lap(LB(a, b), LB(a + 1, b), LB(a - 1, b), LB(a, b + 1), LB(a, b - 1));
+        const bool dom = da >= 0 && da < I && db >= 0 && db < J;
+        const T o = dom ? ob.p[da + (int64_t)db * ob.sj + (int64_t)k * ob.sk] : T(0);
+        ib.p[da + (int64_t)db * ib.sj + (int64_t)k * ib.sk] = o - pol.out_q(tr);
+        if (cb.p && dom) {
+            const T D = pol.out_in((FX(a, b) - FX(a - 1, b)) + (FY(a, b) - FY(a, b - 1)));
+            T *c = cb.p + da + (int64_t)db * cb.sj + (int64_t)k * cb.sk;
+            *c = g.accumulate_coeff_bar ? *c - D * o : -D * o;
+        }
+    }
+}
+
+// The definition in the storage type.
+template <typename T>
+struct AdjNative {
+    using V = T;
+    static constexpr bool kConvert = false;
+    __device__ __forceinline__ V cvt_in(V x) const { return x; }
+    __device__ __forceinline__ V cvt_q(V x) const { return x; }
+    __device__ __forceinline__ V lap(V c, V e, V w, V n, V s) const { return T(4) * c - (((e + w) + n) + s); }
+    __device__ __forceinline__ bool limited_face(V f, V x1, V x0, const T *, const T *) const {
+        return limited(f, x1 - x0);
+    }
+    __device__ __forceinline__ T out_q(V v) const { return v; }
+    __device__ __forceinline__ T out_in(V v) const { return v; }
+};
+
+// Binary64 in exact int64 fixed point (the form of the forward kernels): in with
+// scale Ein, q with scale Eq (each converted in place from its binary64 bits);
+// every add and subtract exact, the limiter takes the exact signs (the binary64
+// inputs are read back only when two cells truncate alike); the two outputs are
+// rounded once each on the way back.
+struct AdjFixed {
+    using V = int64_t;
+    static constexpr bool kConvert = true;
+    int Ein, Eq;
+    __device__ __forceinline__ V cvt_in(V raw) const { return to_fixed(__longlong_as_double(raw), Ein); }
+    __device__ __forceinline__ V cvt_q(V raw) const { return to_fixed(__longlong_as_double(raw), Eq); }
+    __device__ __forceinline__ V lap(V c, V e, V w, V n, V s) const { return 4 * c - (((e + w) + n) + s); }
+    __device__ __forceinline__ bool limited_face(V f, V x1, V x0, const double *p1, const double *p0) const {
+        const int gsign = x1 != x0 ? (x1 > x0 ? 1 : -1) : exact_dir(x1, x0, *p1, *p0);
+        return (f > 0 && gsign > 0) || (f < 0 && gsign < 0);
+    }
+    __device__ __forceinline__ double out_q(V v) const { return from_fixed(v, Eq); }
+    __device__ __forceinline__ double out_in(V v) const { return from_fixed(v, Ein); }
+};
+
 template <typename T, int TI, int TJ, int NT>
 __global__ void __launch_bounds__(NT)
     hdiff_adj_kernel(const View<const T> in, const View<const T> coeff, const View<const T> ob, const View<T> ib,
                      const View<T> cb, const HadjGeom g) {
     using H = HadjTile<T, TI, TJ>;
+    constexpr bool FIX = sizeof(T) == 8;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *S_in = reinterpret_cast<T *>(smem_raw);  // in at tile (-3..TI+2, -3..TJ+2)
-    T *S_q = S_in + H::IX * H::IY;              // q at tile (-2..TI+1, -2..TJ+1)
-    T *S_lap = S_q + H::QX * H::QY;             // forward lap, same region as q
-    T *S_gx = S_lap + H::QX * H::QY;            // x-face cotangents, faces i in [-2, TI], rows [-1, TJ]
-    T *S_fx = S_gx + H::GXX * H::GXY;           // x-face forward values (0 when limited), same region
-    T *S_gy = S_fx + H::GXX * H::GXY;           // y-face cotangents, cols [-1, TI], faces j in [-2, TJ]
-    T *S_fy = S_gy + H::GYX * H::GYY;           // y-face forward values, same region
-    T *S_lb = S_fy + H::GYX * H::GYY;           // lap cotangents, tile +- 1
+    T *S_q = S_in + H::IX * H::IY;              // q at tile (-2..TI+1, -2..TJ+1), then the rest
+    unsigned char *S_keep = smem_raw + H::slots * sizeof(T);
+    __shared__ unsigned s_e[NT / 32][4];
 
     const int tid = threadIdx.x;
     const int ti0 = (blockIdx.x % g.tiles_i) * TI - 2;  // domain-relative i of tile column 0
     const int tj0 = (blockIdx.x / g.tiles_i) * TJ - 2;
     const int k = blockIdx.y;
     const int I = g.I, J = g.J;
-    auto in_dom = [&](int a, int b) { return a >= 0 && a < I && b >= 0 && b < J; };
 
-    // in (valid on the domain plus 2), q = coeff * out_bar (domain only)
+    // in on the cells the forward definition reads (zero elsewhere, including the
+    // unread halo corners), q = coeff * out_bar on the domain
+    unsigned ein = 0, eq = 0, qnz = 0, inz = 0;
     for (int idx = tid; idx < H::IX * H::IY; idx += NT) {
         const int a = ti0 - 3 + idx % H::IX, b = tj0 - 3 + idx / H::IX;
         T v = T(0);
-        if (a >= -2 && a < I + 2 && b >= -2 && b < J + 2) v = in.p[a + (int64_t)b * in.sj + (int64_t)k * in.sk];
+        if (hdiff_reads(a, b, I, J)) v = in.p[a + (int64_t)b * in.sj + (int64_t)k * in.sk];
         S_in[idx] = v;
+        if constexpr (FIX) {
+            ein = max(ein, ((unsigned)__double2hiint(v) >> 20) & 0x7FFu);
+            inz |= (unsigned)((__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll) != 0);
+        }
     }
     for (int idx = tid; idx < H::QX * H::QY; idx += NT) {
         const int a = ti0 - 2 + idx % H::QX, b = tj0 - 2 + idx / H::QX;
         T v = T(0);
-        if (in_dom(a, b))
+        if (a >= 0 && a < I && b >= 0 && b < J)
             v = coeff.p[a + (int64_t)b * coeff.sj + (int64_t)k * coeff.sk] * ob.p[a + (int64_t)b * ob.sj + (int64_t)k * ob.sk];
         S_q[idx] = v;
-    }
-    __syncthreads();
-    auto IN = [&](int a, int b) -> T { return S_in[(a + 3) + (b + 3) * H::IX]; };  // tile-relative
-    // forward Laplacian on tile +- 2 (needed only where -1 <= cell <= I, J)
-    for (int idx = tid; idx < H::QX * H::QY; idx += NT) {
-        const int a = idx % H::QX - 2, b = idx / H::QX - 2;
-        const T sum = ((IN(a + 1, b) + IN(a - 1, b)) + IN(a, b + 1)) + IN(a, b - 1);
-        S_lap[idx] = T(4) * IN(a, b) - sum;
-    }
-    __syncthreads();
-    auto LAP = [&](int a, int b) -> T { return S_lap[(a + 2) + (b + 2) * H::QX]; };
-    auto Q = [&](int a, int b) -> T { return S_q[(a + 2) + (b + 2) * H::QX]; };
-    // every face once: keep/zero from the forward values, its forward flux and its cotangent
-    // (a face exists for domain-relative i in [-1, I-1], j in [0, J) in x, and likewise in y)
-    for (int idx = tid; idx < H::GXX * H::GXY; idx += NT) {
-        const int a = idx % H::GXX - 2, b = idx / H::GXX - 1;  // face between cells a and a+1, row b
-        const int da = ti0 + a, db = tj0 + b;
-        T gv = T(0), fv = T(0);
-        if (da >= -1 && da <= I - 1 && db >= 0 && db < J) {
-            const T f = LAP(a + 1, b) - LAP(a, b);
-            if (!limited(f, IN(a + 1, b) - IN(a, b))) {
-                gv = Q(a, b) - Q(a + 1, b);
-                fv = f;
-            }
-        }
-        S_gx[idx] = gv;
-        S_fx[idx] = fv;
-    }
-    for (int idx = tid; idx < H::GYX * H::GYY; idx += NT) {
-        const int a = idx % H::GYX - 1, b = idx / H::GYX - 2;  // face between rows b and b+1, column a
-        const int da = ti0 + a, db = tj0 + b;
-        T gv = T(0), fv = T(0);
-        if (da >= 0 && da < I && db >= -1 && db <= J - 1) {
-            const T f = LAP(a, b + 1) - LAP(a, b);
-            if (!limited(f, IN(a, b + 1) - IN(a, b))) {
-                gv = Q(a, b) - Q(a, b + 1);
-                fv = f;
-            }
-        }
-        S_gy[idx] = gv;
-        S_fy[idx] = fv;
-    }
-    __syncthreads();
-    auto GX = [&](int a, int b) -> T { return S_gx[(a + 2) + (b + 1) * H::GXX]; };
-    auto GY = [&](int a, int b) -> T { return S_gy[(a + 1) + (b + 2) * H::GYX]; };
-    auto FX = [&](int a, int b) -> T { return S_fx[(a + 2) + (b + 1) * H::GXX]; };
-    auto FY = [&](int a, int b) -> T { return S_fy[(a + 1) + (b + 2) * H::GYX]; };
-    for (int idx = tid; idx < H::LX * H::LY; idx += NT) {
-        const int a = idx % H::LX - 1, b = idx / H::LX - 1;
-        S_lb[idx] = (GX(a - 1, b) - GX(a, b)) + (GY(a, b - 1) - GY(a, b));
-    }
-    __syncthreads();
-    auto LB = [&](int a, int b) -> T { return S_lb[(a + 1) + (b + 1) * H::LX]; };
-    for (int idx = tid; idx < TI * TJ; idx += NT) {
-        const int a = idx % TI, b = idx / TI;
-        const int da = ti0 + a, db = tj0 + b;
-        if (da < -2 || da >= I + 2 || db < -2 || db >= J + 2) continue;
-        const T tr = T(4) * LB(a, b) - (((LB(a + 1, b) + LB(a - 1, b)) + LB(a, b + 1)) + LB(a, b - 1));
-        const bool dom = in_dom(da, db);
-        const T o = dom ? ob.p[da + (int64_t)db * ob.sj + (int64_t)k * ob.sk] : T(0);
-        ib.p[da + (int64_t)db * ib.sj + (int64_t)k * ib.sk] = o - tr;
-        if (cb.p && dom) {
-            const T D = (FX(a, b) - FX(a - 1, b)) + (FY(a, b) - FY(a, b - 1));
-            T *c = cb.p + da + (int64_t)db * cb.sj + (int64_t)k * cb.sk;
-            *c = g.accumulate_coeff_bar ? *c - D * o : -D * o;
+        if constexpr (FIX) {
+            eq = max(eq, ((unsigned)__double2hiint(v) >> 20) & 0x7FFu);
+            qnz |= (unsigned)((__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll) != 0);
         }
     }
+    if constexpr (FIX) {
+        ein = __reduce_max_sync(0xffffffffu, ein);
+        eq = __reduce_max_sync(0xffffffffu, eq);
+        qnz = __reduce_or_sync(0xffffffffu, qnz);
+        inz = __reduce_or_sync(0xffffffffu, inz);
+        if ((tid & 31) == 0)
+            s_e[tid >> 5][0] = ein, s_e[tid >> 5][1] = eq, s_e[tid >> 5][2] = qnz, s_e[tid >> 5][3] = inz;
+    }
+    __syncthreads();
+    if constexpr (FIX) {
+        ein = eq = qnz = inz = 0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w)
+            ein = max(ein, s_e[w][0]), eq = max(eq, s_e[w][1]), qnz |= s_e[w][2], inz |= s_e[w][3];
+        // a field that is zero on the whole tile converts exactly at any scale
+        if (ein == 0 && !inz) ein = 64;
+        if (eq == 0 && !qnz) eq = 64;
+        if (ein >= 64 && ein <= 2040 && eq >= 64 && eq <= 2040) {
+            hdiff_adj_tile<T, TI, TJ, NT>(AdjFixed{(int)ein, (int)eq}, reinterpret_cast<int64_t *>(S_in),
+                                          reinterpret_cast<int64_t *>(S_q), S_keep, in, ob, ib, cb, g, ti0, tj0, k);
+            return;
+        }
+    }
+    hdiff_adj_tile<T, TI, TJ, NT>(AdjNative<T>{}, S_in, S_q, S_keep, in, ob, ib, cb, g, ti0, tj0, k);
 }
 
 // ------------------------------------------------------------------ periodic halo

@@ -376,7 +376,7 @@ static size_t vadv_adj_ws_bytes_for(int dt, int prec, const int64_t dom[3]) {
 template <typename T>
 static int run_hdiff_adj(const gtb_field *fin, const gtb_field *fcf, const gtb_field *fob, const gtb_field *fib,
                          const gtb_field *fcb, int accumulate, const int64_t dom[3], cudaStream_t st) {
-    constexpr int TI = 64, TJ = 16, NT = 256;
+    constexpr int TI = 52, TJ = 20, NT = 256;
     auto kern = hdiff_adj_kernel<T, TI, TJ, NT>;
     constexpr int smem = hdiff_adj_smem_bytes<T, TI, TJ>();
     if (prepare_kernel(kern, smem) != cudaSuccess) return launch_status("hdiff_adj: shared-memory attribute");
