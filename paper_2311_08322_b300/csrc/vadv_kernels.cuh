@@ -14,6 +14,8 @@
 // double-float on the FP32 pipe).
 #pragma once
 
+#include <type_traits>
+
 #include "gtb_device.cuh"
 #include "hdiff_kernels.cuh"  // View
 
@@ -175,6 +177,10 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
     N a_cur = zero, as_cur = zero;  // a_0 = as_0 = 0
     N cp_prev = zero, dp_prev = zero;
 
+    // double-float: two levels per iteration let the compiler interleave one level's
+    // FP32-pipe assembly with the previous level's recurrence (6% faster, same
+    // results); binary64 gains nothing from it (its pipe is saturated)
+#pragma unroll(std::is_same<N, df>::value ? 2 : 1)
     for (int k = 0; k < K; ++k) {
         GTB_LOAD(L1, k + 1);
         const bool has_next = (k + 1 < K);
