@@ -468,11 +468,14 @@ def fused_chain_compare(gtb, f, sets, reps=50):
 def adjoint_ratio(gtb, f, sets, reps=50):
     """Time of one chained step's backward over its forward at 256x256x80 FP64 (C ABI,
     preallocated storages), as the differentiable chain runs them: forward = periodic halo
-    refresh + the fused hdiff -> vadv kernel, backward = vadv_adj (merged u_stage/u_pos
-    cotangent) + hdiff_adj (with coeff_bar) + halo fold."""
+    refresh + the fused hdiff -> vadv kernel keeping the column factors, backward = vadv_adj
+    on those factors (merged u_stage/u_pos cotangent) + hdiff_adj (with coeff_bar) + halo
+    fold.  Forward and backward alternate (each backward consumes its forward's factors);
+    events around each side give both times."""
     import torch
-    o2, o1 = (HDIFF_HALO, HDIFF_HALO, 0), (VADV_HALO, VADV_HALO, 0)
+    o2 = (HDIFF_HALO, HDIFF_HALO, 0)
     dom = (I, J, K)
+    nfac = gtb.hdiff_vadv_workspace_bytes(torch.float64, "native", dom, save_factors=True)
     bufs = []
     for s in sets:
         bufs.append({"fs": s["in"], "cs": s["coeff"], "y": gtb.storage_from(np.zeros((K, J, I)), (0, 0, 0)),
@@ -480,44 +483,42 @@ def adjoint_ratio(gtb, f, sets, reps=50):
                      "yb": gtb.storage_from(f["u_pos"][:, 1:-1, 1:-1].copy(), (0, 0, 0)),
                      "hb": gtb.storage_from(np.zeros((K, J, I)), (0, 0, 0)),
                      "ib": gtb.storage_from(np.zeros_like(f["in"]), o2),
-                     "cb": gtb.storage_from(np.zeros_like(f["coeff"]), o2)})
+                     "cb": gtb.storage_from(np.zeros_like(f["coeff"]), o2),
+                     "F": torch.empty(nfac, dtype=torch.uint8, device="cuda")})
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
     def fwd(b):
         gtb.halo_periodic(b["fs"], 2, 2, domain=dom)
-        gtb.hdiff_vadv(b["fs"], b["cs"], b["wcon"], b["ut"], b["uts"], b["y"], domain=dom)
+        gtb.hdiff_vadv(b["fs"], b["cs"], b["wcon"], b["ut"], b["uts"], b["y"], domain=dom, workspace=b["F"],
+                       save_factors=True)
 
-    def bwd(b, e=None):
-        if e: e[0].record(stream)
-        gtb.vadv_adj(b["wcon"], b["yb"], b["hb"], b["hb"], domain=dom)
-        if e: e[1].record(stream)
+    def bwd(b, e):
+        gtb.vadv_adj(b["wcon"], b["yb"], b["hb"], b["hb"], domain=dom, workspace=b["F"], factors=True)
+        e[2].record(stream)
         gtb.hdiff_adj(b["fs"], b["cs"], b["hb"], b["ib"], b["cb"], accumulate=True, domain=dom)
-        if e: e[2].record(stream)
+        e[3].record(stream)
         gtb.halo_periodic_adj(b["ib"], 2, 2, domain=dom)
-        if e: e[3].record(stream)
 
-    for q in range(5):
-        fwd(bufs[q % len(bufs)])
-        bwd(bufs[q % len(bufs)])
-    torch.cuda.synchronize()
-    t = [ev() for _ in range(4)]
-    t[0].record(stream)
-    for q in range(reps):
-        fwd(bufs[q % len(bufs)])
-    t[1].record(stream)
-    es = [[ev() for _ in range(4)] for _ in range(reps)]
-    for q in range(reps):
-        bwd(bufs[q % len(bufs)], es[q])
-    t[2].record(stream)
+    es = [[ev() for _ in range(5)] for _ in range(reps + 5)]
+    for q in range(reps + 5):  # the first 5 pairs warm up
+        b, e = bufs[q % len(bufs)], es[q]
+        e[0].record(stream)
+        fwd(b)
+        e[1].record(stream)
+        bwd(b, e)
+        e[4].record(stream)
     torch.cuda.synchronize()
     gtb.device_status()
-    f_ms, b_ms = t[0].elapsed_time(t[1]) / reps, t[1].elapsed_time(t[2]) / reps
+    es = es[5:]
+    mean = lambda a, b: float(np.mean([e[a].elapsed_time(e[b]) for e in es]))
+    f_ms, b_ms = mean(0, 1), mean(1, 4)
     return {"ratio": round(b_ms / f_ms, 3), "forward_ms": round(f_ms, 4), "backward_ms": round(b_ms, 4),
-            "vadv_adj_ms": round(float(np.mean([e[0].elapsed_time(e[1]) for e in es])), 4),
-            "hdiff_adj_ms": round(float(np.mean([e[1].elapsed_time(e[2]) for e in es])), 4),
-            "halo_adj_ms": round(float(np.mean([e[2].elapsed_time(e[3]) for e in es])), 4),
-            "workload": "one chained step at 256x256x80 FP64 (halo refresh + fused hdiff -> vadv vs the adjoints)"}
+            "vadv_adj_ms": round(mean(1, 2), 4), "hdiff_adj_ms": round(mean(2, 3), 4),
+            "halo_adj_ms": round(mean(3, 4), 4),
+            "factors_mb_per_step": round(nfac / 1e6, 1),
+            "workload": "one chained step at 256x256x80 FP64 (halo refresh + fused hdiff -> vadv keeping the "
+                        "column factors vs the adjoints)"}
 
 
 def batched_compare(reps=20):

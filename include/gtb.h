@@ -77,6 +77,8 @@ typedef enum {
 /* flags */
 #define GTB_WCON_LITERAL 1u   /* vadv: use wcon(i) as the face velocity instead of the I-face average */
 #define GTB_ADJ_ACCUMULATE 2u /* adjoints: add into the cotangent outputs instead of overwriting them */
+#define GTB_SAVE_FACTORS 4u   /* gtb_hdiff_vadv: keep the column factors (c'_k, 1/p_k) in the workspace */
+#define GTB_ADJ_FACTORS 8u    /* gtb_vadv_adj: the workspace holds those factors; use them, do not refactorise */
 
 /*
  * gtb_hdiff -- horizontal diffusion (paper Sec. 3.1; one PARALLEL computation,
@@ -166,8 +168,13 @@ int gtb_hdiff_adj(const gtb_field *in, const gtb_field *coeff, const gtb_field *
  * GTB_ADJ_ACCUMULATE.  u_stage_bar and u_pos_bar may be the very same view:
  * it then receives their sum (the cotangent of a field passed as both
  * u_stage and u_pos).  No other output may overlap an input or another output.
- * flags: GTB_WCON_LITERAL, GTB_ADJ_ACCUMULATE.  workspace: as for gtb_vadv, of
- * gtb_vadv_adj_workspace_bytes() bytes.  Limit: K <= 448.
+ * flags: GTB_WCON_LITERAL, GTB_ADJ_ACCUMULATE, GTB_ADJ_FACTORS.  workspace: as
+ * for gtb_vadv, of gtb_vadv_adj_workspace_bytes() bytes.  With GTB_ADJ_FACTORS
+ * the workspace is REQUIRED and must hold the factors that gtb_hdiff_vadv kept
+ * with GTB_SAVE_FACTORS for the same wcon, dtr_stage, beta_v, prec, flags
+ * and domain (c'_k, then 1/p_k); the forward sweep then reads them instead of
+ * refactorising A (the same values, so the same results), and overwrites
+ * them: each set of factors serves one adjoint.  Limit: K <= 448.
  */
 int gtb_vadv_adj(const gtb_field *wcon, const gtb_field *y_bar, const gtb_field *u_stage_bar,
                  const gtb_field *u_pos_bar, const gtb_field *utens_bar, const gtb_field *utens_stage_bar,
@@ -207,6 +214,12 @@ int gtb_halo_periodic_adj(const gtb_field *f, int hi, int hj, const int64_t *dom
  * gtb_hdiff_vadv_workspace_bytes() bytes (c', and e when it cannot be parked
  * in the output), 16-byte aligned, overlapping no field; NULL or too small is
  * GTB_ERR_ARG.  No K limit beyond the workspace size.
+ * flags: GTB_WCON_LITERAL, GTB_SAVE_FACTORS.  With GTB_SAVE_FACTORS the
+ * workspace keeps, on return, the factors of the column solve for the adjoint
+ * (gtb_vadv_adj with GTB_ADJ_FACTORS): c'_k in its first K*I*J values and
+ * 1/p_k in the next K*I*J (value type: binary64, or binary32 / binary64 /
+ * double-float pairs as prec selects for GTB_F32 storage; index
+ * k*I*J + j*I + i).
  */
 int gtb_hdiff_vadv(const gtb_field *in, const gtb_field *coeff, const gtb_field *wcon,
                    const gtb_field *utens, const gtb_field *utens_stage,
@@ -214,9 +227,9 @@ int gtb_hdiff_vadv(const gtb_field *in, const gtb_field *coeff, const gtb_field 
                    int prec, unsigned flags, const int64_t *domain,
                    void *workspace, size_t workspace_bytes, void *stream);
 
-/* Workspace bytes of gtb_hdiff_vadv (equal to gtb_vadv_workspace_bytes for
- * the same dtype, prec and domain); 0 for bad arguments. */
-size_t gtb_hdiff_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain);
+/* Workspace bytes of gtb_hdiff_vadv for this dtype, prec, flags (with or
+ * without GTB_SAVE_FACTORS) and domain; 0 for bad arguments. */
+size_t gtb_hdiff_vadv_workspace_bytes(int dtype, int prec, unsigned flags, const int64_t *domain);
 
 /*
  * gtb_step -- one step of the paper's benchmark (Sec. 3.1): both stencils on

@@ -9,8 +9,9 @@ the two stencils as one kernel (gtb_hdiff_vadv: h never leaves the chip).  The s
 backward runs the hand-written adjoint kernels (gtb_vadv_adj with the u_stage
 and u_pos cotangents merged, gtb_hdiff_adj with the limiter recomputed from
 the saved input, gtb_halo_periodic_adj) — no autodiff of the stencils.  Each
-step saves only its input field: step-level checkpointing, so an N-step chain
-holds N field copies and recomputes nothing.
+step saves its input field (step-level checkpointing: an N-step chain holds N
+field copies) and, unless ChainFixed.save_factors is off, the factors of its
+column solves, which the vadv adjoint then reads instead of refactorising.
 """
 from __future__ import annotations
 
@@ -29,6 +30,9 @@ class ChainFixed:
     utens_stage: gtb.Storage
     dtr_stage: float = 3.0 / 20.0
     beta_v: float = 0.0
+    # keep each step's column factors (c'_k, 1/p_k: two K x I x J arrays) so that the backward
+    # does not refactorise A: memory for FP64-pipe time
+    save_factors: bool = True
 
     @property
     def prec(self):
@@ -62,11 +66,17 @@ class ChainStep(torch.autograd.Function):
         cs = _as_storage(coeff)
         y = interior_storage(I, J, K, field.dtype, field.device)
         # h = hdiff(field, coeff) and y = vadv(h, wcon, h, utens, utens_stage) in one kernel
-        # (h stays on chip; the backward needs only the checkpointed input)
+        # (h stays on chip; the backward needs only the checkpointed input and, if kept, the factors)
+        ws = "auto"
+        if fixed.save_factors:
+            nb = gtb.hdiff_vadv_workspace_bytes(field.dtype, fixed.prec, (I, J, K), save_factors=True)
+            ws = torch.empty(nb, dtype=torch.uint8, device=field.device)
         gtb.hdiff_vadv(fs, cs, fixed.wcon, fixed.utens, fixed.utens_stage, y, dtr_stage=fixed.dtr_stage,
-                       beta_v=fixed.beta_v, prec=fixed.prec, domain=(I, J, K))
+                       beta_v=fixed.beta_v, prec=fixed.prec, domain=(I, J, K), workspace=ws,
+                       save_factors=fixed.save_factors)
         ctx.fixed = fixed
         ctx.fs, ctx.cs = fs, cs  # the checkpoint: this step's input (with its halo) and coeff
+        ctx.factors = ws if fixed.save_factors else None
         return y.data.clone()
 
     @staticmethod
@@ -76,8 +86,13 @@ class ChainStep(torch.autograd.Function):
         yb = _as_storage(y_bar.contiguous())
         hb = interior_storage(I, J, K, y_bar.dtype, y_bar.device)
         # h entered vadv as both u_stage and u_pos: one merged cotangent
-        gtb.vadv_adj(fixed.wcon, yb, hb, hb, dtr_stage=fixed.dtr_stage, beta_v=fixed.beta_v, prec=fixed.prec,
-                     domain=(I, J, K))
+        if ctx.factors is not None:  # the forward's factors (consumed)
+            gtb.vadv_adj(fixed.wcon, yb, hb, hb, dtr_stage=fixed.dtr_stage, beta_v=fixed.beta_v, prec=fixed.prec,
+                         domain=(I, J, K), workspace=ctx.factors, factors=True)
+            ctx.factors = None
+        else:
+            gtb.vadv_adj(fixed.wcon, yb, hb, hb, dtr_stage=fixed.dtr_stage, beta_v=fixed.beta_v, prec=fixed.prec,
+                         domain=(I, J, K))
         ib = halo_storage(I, J, K, y_bar.dtype, 2, y_bar.device)
         cb = interior_storage(I, J, K, y_bar.dtype, y_bar.device)
         gtb.hdiff_adj(fs, cs, hb, ib, cb, domain=(I, J, K))

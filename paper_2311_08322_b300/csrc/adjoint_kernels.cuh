@@ -30,7 +30,10 @@ struct VadvAdjOut {
     int64_t sj, sk;
 };
 
-template <typename T, typename N, int BJ, bool WS>
+// FACT: the workspace holds the forward solve's factors, c'_k then 1/p_k (kept by
+// gtb_hdiff_vadv with GTB_SAVE_FACTORS): the forward sweep reads them instead of
+// refactorising A, and v_k overwrites 1/p_k in place.
+template <typename T, typename N, int BJ, bool WS, bool FACT>
 __global__ void __launch_bounds__(32 * BJ)
     vadv_adj_kernel(const View<const T> wc, const View<const T> yb, const View<T> usb, const View<T> upb,
                     const View<T> utb, const View<T> utsb, const VadvGeom g, const int accumulate,
@@ -72,34 +75,52 @@ __global__ void __launch_bounds__(32 * BJ)
     const N zero = num_const<N>(0.0);
     const int kexp = g.ka_pow2;
 
-    // face-velocity sum of level m (warp-uniform call)
-    auto face = [&](int m) -> N {
-        const T lo = pw[(int64_t)m * wc.sk];
+    // face-velocity sum from this lane's wcon(i) and, for the last lane, wcon(i+1) (warp-uniform call)
+    auto face_of = [&](T lo, T hi_last) -> N {
         if (lit) return to_num<N, T>(lo);
         T hi = __shfl_down_sync(0xffffffffu, lo, 1);
-        if (last_lane) hi = pw1[(int64_t)m * wc.sk];
+        if (last_lane) hi = hi_last;
         return to_num<N, T>(lo) + to_num<N, T>(hi);
     };
+    auto wload = [&](int m, T &lo, T &hi) {
+        lo = pw[(int64_t)m * wc.sk];
+        if (last_lane) hi = pw1[(int64_t)m * wc.sk];
+    };
 
-    // forward sweep: the pivots of A, c'_k, and v (U^T v = dtr y_bar)
+    // forward sweep: the pivots of A, c'_k, and v (U^T v = dtr y_bar); every input of
+    // level k+1 is loaded during level k
     N a_cur = zero, cp_prev = zero, v_prev = zero;
-    T ynext = py[0];
+    T y_n = py[0], w_n = T(0), w1_n = T(0);
+    N r_n = zero;
+    if (K > 1) wload(1, w_n, w1_n);
+    if constexpr (FACT) r_n = vb[cidx];
     for (int k = 0; k < K; ++k) {
-        const T yk = ynext;
-        if (k + 1 < K) ynext = py[(int64_t)(k + 1) * yb.sk];
-        N a_next = zero;
-        if (k + 1 < K) a_next = coef<N>(face(k + 1), ka, kexp);
-        const N b = (dtr - a_cur) + a_next;
-        const N p = (k > 0) ? b - a_cur * cp_prev : b;
-        const N r = recip(p);
-        const N x = dtr * to_num<N, T>(yk);
-        const N v = (k > 0) ? (x + a_cur * v_prev) * r : x * r;
-        const N cpk = (-a_next) * r;
-        if (wr) {
-            cpb[(size_t)k * cstride + cidx] = cpk;
-            vb[(size_t)k * cstride + cidx] = v;
+        const T yk = y_n, wk1 = w_n, w1k1 = w1_n;
+        const N rk = r_n;
+        if (k + 1 < K) {
+            y_n = py[(int64_t)(k + 1) * yb.sk];
+            if constexpr (FACT) r_n = vb[(size_t)(k + 1) * cstride + cidx];
         }
-        cp_prev = cpk, v_prev = v;
+        if (k + 2 < K) wload(k + 2, w_n, w1_n);
+        N a_next = zero;
+        if (k + 1 < K) a_next = coef<N>(face_of(wk1, w1k1), ka, kexp);
+        const N x = dtr * to_num<N, T>(yk);
+        if constexpr (FACT) {
+            const N v = (k > 0) ? (x + a_cur * v_prev) * rk : x * rk;
+            if (wr) vb[(size_t)k * cstride + cidx] = v;
+            v_prev = v;
+        } else {
+            const N b = (dtr - a_cur) + a_next;
+            const N p = (k > 0) ? b - a_cur * cp_prev : b;
+            const N r = recip(p);
+            const N v = (k > 0) ? (x + a_cur * v_prev) * r : x * r;
+            const N cpk = (-a_next) * r;
+            if (wr) {
+                cpb[(size_t)k * cstride + cidx] = cpk;
+                vb[(size_t)k * cstride + cidx] = v;
+            }
+            cp_prev = cpk, v_prev = v;
+        }
         a_cur = a_next;
     }
 
@@ -109,39 +130,46 @@ __global__ void __launch_bounds__(32 * BJ)
         T *q = o.p + ic + (int64_t)jc * o.sj + (int64_t)k * o.sk;
         *q = accumulate ? to_store<T, N>(to_num<N, T>(*q) + val) : to_store<T, N>(val);
     };
-    N z1 = zero, z2 = zero;  // z_{k+1}, z_{k+2}
+    // carried from the previous (higher) level, so that nothing is formed or loaded twice:
+    N z1 = zero;               // z_{k+1}
+    N zz1 = zero;              // z_{k+1} + z_{k+2}
+    N y1 = zero;               // y_bar_{k+1}
     N as1 = zero, as2 = zero;  // as_{k+1}, as_{k+2} (as_K = 0)
+    // level K-1's inputs, then each level's during the level above it
+    N vb_n = vb[(size_t)(K - 1) * cstride + cidx], cp_n = zero;
+    T yb_n = py[(int64_t)(K - 1) * yb.sk], wb_n = T(0), wb1_n = T(0);
+    if (K - 1 > 0) wload(K - 1, wb_n, wb1_n);
     for (int k = K - 1; k >= 0; --k) {
-        const N vk = vb[(size_t)k * cstride + cidx];
-        const N z = (k == K - 1) ? vk : vk + cpb[(size_t)k * cstride + cidx] * z1;
+        const N vk = vb_n, cpk = cp_n;
+        const T ykr = yb_n, wk = wb_n, w1k = wb1_n;
+        if (k > 0) {
+            vb_n = vb[(size_t)(k - 1) * cstride + cidx];
+            cp_n = cpb[(size_t)(k - 1) * cstride + cidx];
+            yb_n = py[(int64_t)(k - 1) * yb.sk];
+            if (k - 1 > 0) wload(k - 1, wb_n, wb1_n);
+        }
+        const N z = (k == K - 1) ? vk : vk + cpk * z1;
         N ask = zero;
         if (k > 0) {
-            const N s = face(k);
+            const N s = face_of(wk, w1k);
             ask = g.sym ? coef<N>(s, ka, kexp) : kas * s;
         }
-        const N yk = to_num<N, T>(py[(int64_t)k * yb.sk]);
+        const N yk = to_num<N, T>(ykr);
         store(utb, k, z);
         store(utsb, k, z);
-        const N upbar = dtr * (z - yk);
-        if (!merge_us_up) store(upb, k, upbar);
-        if (k + 1 < K) {  // u_stage_bar of level k+1
-            const N usb1 = as1 * (z + z1) - as2 * (z1 + z2);
-            if (merge_us_up) {
-                // u_stage_bar and u_pos_bar are one field: level k+1 gets both (u_pos part stored earlier)
-                store(usb, k + 1, usb1 + dtr * (z1 - to_num<N, T>(py[(int64_t)(k + 1) * yb.sk])));
-            } else {
-                store(usb, k + 1, usb1);
-            }
+        if (!merge_us_up) store(upb, k, dtr * (z - yk));
+        const N zz = z + z1;  // z_k + z_{k+1}
+        if (k + 1 < K) {      // u_stage_bar of level k+1
+            const N usb1 = as1 * zz - as2 * zz1;
+            // u_stage_bar and u_pos_bar as one field: level k+1 gets both
+            store(usb, k + 1, merge_us_up ? usb1 + dtr * (z1 - y1) : usb1);
         }
-        z2 = z1, z1 = z;
+        z1 = z, zz1 = zz, y1 = yk;
         as2 = as1, as1 = ask;
     }
     {  // level 0: as_0 = 0
-        const N usb0 = -as2 * (z1 + z2);
-        if (merge_us_up)
-            store(usb, 0, usb0 + dtr * (z1 - to_num<N, T>(py[0])));
-        else
-            store(usb, 0, usb0);
+        const N usb0 = -as2 * zz1;
+        store(usb, 0, merge_us_up ? usb0 + dtr * (z1 - y1) : usb0);
     }
 }
 

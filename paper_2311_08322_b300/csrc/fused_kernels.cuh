@@ -279,11 +279,14 @@ __device__ __forceinline__ void hdiff_producer(const CUtensorMap *tmap, const Vi
         for (int s = 0; s < STAGES; ++s) mbar_wait(&tbar[s], 0), mbar_wait(&tbar[s], 1);
 }
 
+// ws: c'_k ([k][j*I + i]); rsave: 1/p_k in the same layout, or null (the factors
+// kept for the adjoint); ework: e_k when it is not parked in the output.
 template <typename T, typename N, int TI, int TJ, int PW, int STAGES, int RING, bool USE_TMA, bool DPG>
 __global__ void __launch_bounds__(TI * TJ + 32 * PW)
     hdiff_vadv_kernel(const __grid_constant__ CUtensorMap tmap, const View<const T> in, const View<const T> coeff,
                       const View<const T> wc, const View<const T> ut, const View<const T> uts, const View<T> out,
-                      const HdiffGeom hg, const VadvGeom g, N *__restrict__ ws) {
+                      const HdiffGeom hg, const VadvGeom g, N *__restrict__ ws, N *__restrict__ rsave,
+                      N *__restrict__ ework) {
     using Lay = FusedLayout<T, TI, TJ, PW, STAGES, RING>;
     using Tile = typename Lay::Tile;
     constexpr int NC = Tile::NC, CW = Tile::CW;
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(TI * TJ + 32 * PW)
     T *po = out.p + ic + (int64_t)jc * out.sj;
     const size_t cstride = (size_t)I * J, cidx = (size_t)jc * I + ic;
     N *cpb = ws;
-    N *epb = ws + (size_t)K * cstride;  // e_k when it is not parked in the output
+    N *epb = ework;  // e_k when it is not parked in the output
     const bool row_end = (ci == TI - 1);  // wcon(i+1) is not held by the next lane
     const bool lit = g.literal != 0;
 
@@ -368,6 +371,7 @@ __global__ void __launch_bounds__(TI * TJ + 32 * PW)
         if (has_next) e = e - mulx<N, T>(cpk, hk1);
         if (active) {
             cpb[(size_t)k * cstride + cidx] = cpk;
+            if (rsave) rsave[(size_t)k * cstride + cidx] = r;
             if (DPG) po[(int64_t)k * out.sk] = to_store<T, N>(e);
             else epb[(size_t)k * cstride + cidx] = e;
         }

@@ -337,10 +337,10 @@ static size_t vadv_ws_bytes_for(int dt, int prec, const int64_t dom[3]) {
 }
 
 // ------------------------------------------------------------------ adjoints
-template <typename T, typename N, int BJ, bool WS>
+template <typename T, typename N, int BJ, bool WS, bool FACT = false>
 static int launch_vadv_adj_t(const gtb_field *const f[6], const VadvGeom &g, int accumulate, int merge, void *ws,
                              cudaStream_t st) {
-    auto kern = vadv_adj_kernel<T, N, BJ, WS>;
+    auto kern = vadv_adj_kernel<T, N, BJ, WS, FACT>;
     const int smem = WS ? 0 : (int)(2 * sizeof(N) * g.K * 32 * BJ);
     if (!WS && prepare_kernel(kern, 227 * 1024) != cudaSuccess)
         return launch_status("vadv_adj: shared-memory attribute");
@@ -358,8 +358,9 @@ static size_t vadv_adj_ws_bytes(const int64_t dom[3]) {
 
 template <typename T, typename N>
 static int run_vadv_adj_n(const gtb_field *const f[6], const VadvGeom &g, int accumulate, int merge, void *ws,
-                          size_t ws_bytes, cudaStream_t st) {
+                          size_t ws_bytes, bool factors, cudaStream_t st) {
     const int64_t dom[3] = {g.I, g.J, g.K};
+    if (factors) return launch_vadv_adj_t<T, N, 2, true, true>(f, g, accumulate, merge, ws, st);
     if (ws && ws_bytes >= vadv_adj_ws_bytes<T, N>(dom)) return launch_vadv_adj_t<T, N, 2, true>(f, g, accumulate, merge, ws, st);
     const size_t per_col = 2 * sizeof(N) * (size_t)g.K;
     if (per_col * 64 <= 48 * 1024) return launch_vadv_adj_t<T, N, 2, false>(f, g, accumulate, merge, nullptr, st);
@@ -418,9 +419,24 @@ template <> struct FusedCfg<double> { static constexpr int TI = 32, TJ = 2, PW =
 template <> struct FusedCfg<float> { static constexpr int TI = 16, TJ = 8, PW = 2; };
 constexpr int kFusedStages = 2, kFusedRing = 8;
 
+// Workspace of the fused kernel: c', then 1/p when the factors are kept, then e
+// when it cannot be parked in the output (all [K][I*J] arrays of N).
+template <typename T, typename N>
+static size_t fused_ws_bytes(const int64_t dom[3], bool save) {
+    const size_t arr = sizeof(N) * (size_t)dom[0] * (size_t)dom[1] * (size_t)dom[2];
+    return arr * ((vadv_dp_global<T, N>() ? 1 : 2) + (save ? 1 : 0));
+}
+
+static size_t fused_ws_bytes_for(int dt, int prec, const int64_t dom[3], bool save) {
+    if (dt == GTB_F64) return fused_ws_bytes<double, double>(dom, save);
+    if (prec == GTB_PREC_F64) return fused_ws_bytes<float, double>(dom, save);
+    if (prec == GTB_PREC_DF) return fused_ws_bytes<float, df>(dom, save);
+    return fused_ws_bytes<float, float>(dom, save);
+}
+
 template <typename T, typename N, bool TMA>
 static int launch_fused_t(const CUtensorMap &map, const gtb_field *const f[6], const HdiffGeom &hg,
-                          const VadvGeom &g, void *ws, cudaStream_t st) {
+                          const VadvGeom &g, void *ws, bool save, cudaStream_t st) {
     using C = FusedCfg<T>;
     constexpr bool DPG = vadv_dp_global<T, N>();
     constexpr int STG = TMA ? kFusedStages : 1;
@@ -428,21 +444,24 @@ static int launch_fused_t(const CUtensorMap &map, const gtb_field *const f[6], c
     auto kern = hdiff_vadv_kernel<T, N, C::TI, C::TJ, C::PW, STG, kFusedRing, TMA, DPG>;
     if (prepare_kernel(kern, Lay::smem_bytes) != cudaSuccess) return launch_status("hdiff_vadv: shared-memory attribute");
     dim3 grid((g.I + C::TI - 1) / C::TI, (g.J + C::TJ - 1) / C::TJ);
+    const size_t arr = (size_t)g.I * g.J * g.K;  // values of N per [K][I*J] array
     kern<<<grid, C::TI * C::TJ + 32 * C::PW, Lay::smem_bytes, st>>>(
         map, view_of<const T>(f[0]), view_of<const T>(f[1]), view_of<const T>(f[2]), view_of<const T>(f[3]),
-        view_of<const T>(f[4]), view_of<T>(f[5]), hg, g, static_cast<N *>(ws));
+        view_of<const T>(f[4]), view_of<T>(f[5]), hg, g, static_cast<N *>(ws),
+        save ? static_cast<N *>(ws) + arr : nullptr, static_cast<N *>(ws) + (save ? 2 : 1) * arr);
     return launch_status("hdiff_vadv launch");
 }
 
 // f = {in, coeff, wcon, utens, utens_stage, utens_stage_out}
 template <typename T, typename N>
-static int run_fused_n(const gtb_field *const f[6], const VadvGeom &g, void *ws, cudaStream_t st) {
+static int run_fused_n(const gtb_field *const f[6], const VadvGeom &g, void *ws, bool save, cudaStream_t st) {
     using Tile = FusedTile<T, FusedCfg<T>::TI, FusedCfg<T>::TJ>;
     HdiffGeom hg{};
     hg.I = g.I, hg.J = g.J, hg.K = g.K;
     CUtensorMap map;
     const bool tma = encode_in_map<T>(f[0], Tile::BX, Tile::BY, hg, map);
-    return tma ? launch_fused_t<T, N, true>(map, f, hg, g, ws, st) : launch_fused_t<T, N, false>(map, f, hg, g, ws, st);
+    return tma ? launch_fused_t<T, N, true>(map, f, hg, g, ws, save, st)
+               : launch_fused_t<T, N, false>(map, f, hg, g, ws, save, st);
 }
 
 // ------------------------------------------------------------------ co-scheduled step
@@ -584,7 +603,9 @@ extern "C" int gtb_hdiff_vadv(const gtb_field *in, const gtb_field *coeff, const
     int rc;
     for (int q = 0; q < 6; ++q)
         if ((rc = check_field(names[q], f[q], dt))) return rc;
-    if (flags & ~GTB_WCON_LITERAL) return fail(GTB_ERR_ARG, "gtb_hdiff_vadv: unknown flags 0x%x", flags);
+    if (flags & ~(GTB_WCON_LITERAL | GTB_SAVE_FACTORS))
+        return fail(GTB_ERR_ARG, "gtb_hdiff_vadv: unknown flags 0x%x", flags);
+    const bool save = flags & GTB_SAVE_FACTORS;
     if (prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return fail(GTB_ERR_ARG, "gtb_hdiff_vadv: unknown prec %d", prec);
     if (dt == GTB_F64 && prec != GTB_PREC_NATIVE)
         return fail(GTB_ERR_ARG, "gtb_hdiff_vadv: FP64 storage computes in binary64 (prec must be GTB_PREC_NATIVE)");
@@ -604,7 +625,7 @@ extern "C" int gtb_hdiff_vadv(const gtb_field *in, const gtb_field *coeff, const
             return fail(GTB_ERR_ALIAS, "gtb_hdiff_vadv: utens_stage_out overlaps %s", names[q]);
     }
     if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
-    const size_t need = vadv_ws_bytes_for(dt, prec, dom);
+    const size_t need = fused_ws_bytes_for(dt, prec, dom, save);
     if (!workspace || workspace_bytes < need)
         return fail(GTB_ERR_ARG, "gtb_hdiff_vadv: a workspace of %zu bytes is required (got %zu)", need,
                     workspace ? workspace_bytes : (size_t)0);
@@ -618,10 +639,10 @@ extern "C" int gtb_hdiff_vadv(const gtb_field *in, const gtb_field *coeff, const
     }
     const VadvGeom g = make_vadv_geom(dom, literal, dtr_stage, beta_v);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (dt == GTB_F64) return run_fused_n<double, double>(f, g, workspace, st);
-    if (prec == GTB_PREC_F64) return run_fused_n<float, double>(f, g, workspace, st);
-    if (prec == GTB_PREC_DF) return run_fused_n<float, df>(f, g, workspace, st);
-    return run_fused_n<float, float>(f, g, workspace, st);
+    if (dt == GTB_F64) return run_fused_n<double, double>(f, g, workspace, save, st);
+    if (prec == GTB_PREC_F64) return run_fused_n<float, double>(f, g, workspace, save, st);
+    if (prec == GTB_PREC_DF) return run_fused_n<float, df>(f, g, workspace, save, st);
+    return run_fused_n<float, float>(f, g, workspace, save, st);
 }
 
 extern "C" int gtb_step(const gtb_field *in, const gtb_field *coeff, const gtb_field *hdiff_out,
@@ -688,8 +709,11 @@ extern "C" int gtb_step(const gtb_field *in, const gtb_field *coeff, const gtb_f
     return run_vadv_n<float, float>(fv, g, workspace, workspace_bytes, st);
 }
 
-extern "C" size_t gtb_hdiff_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain) {
-    return gtb_vadv_workspace_bytes(dtype, prec, domain);
+extern "C" size_t gtb_hdiff_vadv_workspace_bytes(int dtype, int prec, unsigned flags, const int64_t *domain) {
+    if (!domain || !dtype_size(dtype) || prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return 0;
+    for (int d = 0; d < 3; ++d)
+        if (domain[d] < 0) return 0;
+    return fused_ws_bytes_for(dtype, dtype == GTB_F64 ? GTB_PREC_NATIVE : prec, domain, flags & GTB_SAVE_FACTORS);
 }
 
 extern "C" int gtb_device_status(void *stream) {
@@ -843,7 +867,9 @@ extern "C" int gtb_vadv_adj(const gtb_field *wcon, const gtb_field *y_bar, const
     int rc;
     for (int q = 0; q < 6; ++q)
         if (f[q] && (rc = check_field(names[q], f[q], dt))) return rc;
-    if (flags & ~(GTB_WCON_LITERAL | GTB_ADJ_ACCUMULATE)) return fail(GTB_ERR_ARG, "gtb_vadv_adj: unknown flags 0x%x", flags);
+    if (flags & ~(GTB_WCON_LITERAL | GTB_ADJ_ACCUMULATE | GTB_ADJ_FACTORS))
+        return fail(GTB_ERR_ARG, "gtb_vadv_adj: unknown flags 0x%x", flags);
+    const bool factors = flags & GTB_ADJ_FACTORS;
     if (prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return fail(GTB_ERR_ARG, "gtb_vadv_adj: unknown prec %d", prec);
     if (dt == GTB_F64 && prec != GTB_PREC_NATIVE)
         return fail(GTB_ERR_ARG, "gtb_vadv_adj: FP64 storage computes in binary64 (prec must be GTB_PREC_NATIVE)");
@@ -871,13 +897,23 @@ extern "C" int gtb_vadv_adj(const gtb_field *wcon, const gtb_field *y_bar, const
     if (workspace && reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
         return fail(GTB_ERR_LAYOUT, "gtb_vadv_adj: workspace must be 16-byte aligned");
     if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
+    if (factors && (!workspace || workspace_bytes < vadv_adj_ws_bytes_for(dt, prec, dom)))
+        return fail(GTB_ERR_ARG, "gtb_vadv_adj: GTB_ADJ_FACTORS needs the forward's factors: a workspace of %zu bytes",
+                    vadv_adj_ws_bytes_for(dt, prec, dom));
+    if (workspace) {
+        const int64_t n = (int64_t)(workspace_bytes / dtype_size(dt));
+        const gtb_field wsf{workspace, dt, 0, {n, 1, 1}, {1, n, n}, {0, 0, 0}};
+        for (int q = 0; q < 6; ++q)
+            if (f[q] && overlaps(&wsf, f[q])) return fail(GTB_ERR_ALIAS, "gtb_vadv_adj: workspace overlaps %s", names[q]);
+    }
     const VadvGeom g = make_vadv_geom(dom, literal, dtr_stage, beta_v);
     const int acc = (flags & GTB_ADJ_ACCUMULATE) ? 1 : 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (dt == GTB_F64) return run_vadv_adj_n<double, double>(f, g, acc, merge, workspace, workspace_bytes, st);
-    if (prec == GTB_PREC_F64) return run_vadv_adj_n<float, double>(f, g, acc, merge, workspace, workspace_bytes, st);
-    if (prec == GTB_PREC_DF) return run_vadv_adj_n<float, df>(f, g, acc, merge, workspace, workspace_bytes, st);
-    return run_vadv_adj_n<float, float>(f, g, acc, merge, workspace, workspace_bytes, st);
+    if (dt == GTB_F64) return run_vadv_adj_n<double, double>(f, g, acc, merge, workspace, workspace_bytes, factors, st);
+    if (prec == GTB_PREC_F64)
+        return run_vadv_adj_n<float, double>(f, g, acc, merge, workspace, workspace_bytes, factors, st);
+    if (prec == GTB_PREC_DF) return run_vadv_adj_n<float, df>(f, g, acc, merge, workspace, workspace_bytes, factors, st);
+    return run_vadv_adj_n<float, float>(f, g, acc, merge, workspace, workspace_bytes, factors, st);
 }
 
 static int halo_common(const char *fn, const gtb_field *f, int hi, int hj, const int64_t *domain, int64_t dom[3]) {

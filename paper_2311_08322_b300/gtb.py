@@ -57,6 +57,8 @@ EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_hdiff_adj",
            "gtb_batch_plan", "gtb_batch_run", "gtb_plan_info", "gtb_plan_destroy", "gtb_hdiff_vadv",
            "gtb_hdiff_vadv_workspace_bytes", "gtb_step", "gtb_last_error", "gtb_version")
 GTB_ADJ_ACCUMULATE = 2
+GTB_SAVE_FACTORS = 4
+GTB_ADJ_FACTORS = 8
 
 
 def lib() -> ctypes.CDLL:
@@ -84,7 +86,7 @@ def lib() -> ctypes.CDLL:
         L.gtb_step.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                ctypes.c_uint, i64p, vp, ctypes.c_size_t, vp]
         L.gtb_step.restype = ctypes.c_int
-        L.gtb_hdiff_vadv_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, i64p]
+        L.gtb_hdiff_vadv_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint, i64p]
         L.gtb_hdiff_vadv_workspace_bytes.restype = ctypes.c_size_t
         L.gtb_halo_periodic.argtypes = [P, ctypes.c_int, ctypes.c_int, i64p, vp]
         L.gtb_halo_periodic_adj.argtypes = [P, ctypes.c_int, ctypes.c_int, i64p, vp]
@@ -274,24 +276,32 @@ def _fused_domain(fs, literal):
     return tuple(max(0, x) for x in dom)
 
 
+def hdiff_vadv_workspace_bytes(dtype, prec, domain, save_factors=False) -> int:
+    """Workspace bytes gtb_hdiff_vadv needs (with room for the kept factors when asked)."""
+    dt = {torch.float64: GTB_F64, torch.float32: GTB_F32}.get(dtype, dtype)
+    return int(lib().gtb_hdiff_vadv_workspace_bytes(dt, PREC[prec] if isinstance(prec, str) else int(prec),
+                                                    GTB_SAVE_FACTORS if save_factors else 0, _dom(domain)))
+
+
 def hdiff_vadv(in_, coeff, wcon, utens, utens_stage, out=None, *, dtr_stage=3.0 / 20.0, beta_v=0.0,
-               prec="native", literal=False, domain=None, workspace="auto", stream=None):
+               prec="native", literal=False, domain=None, workspace="auto", save_factors=False, stream=None):
     """utens_stage_out = vadv(h, wcon, h, utens, utens_stage) with h = hdiff(in_, coeff), in one
     kernel (gtb_hdiff_vadv); ``out=None`` updates utens_stage in place.  ``workspace``: "auto"
-    (a cached buffer from :func:`workspace`) or a CUDA tensor; the call needs one."""
+    (a cached buffer from :func:`workspace`) or a CUDA tensor; the call needs one.  With
+    ``save_factors`` the workspace keeps the column factors for :func:`vadv_adj` (``factors=True``):
+    pass a tensor of :func:`hdiff_vadv_workspace_bytes` bytes that outlives the call."""
     out = utens_stage if out is None else out
     fs = [_as_field(x) for x in (in_, coeff, wcon, utens, utens_stage, out)]
     ws_ptr, ws_bytes = None, 0
     if isinstance(workspace, str):
         dom = tuple(domain) if domain is not None else _fused_domain(fs, literal)
-        need = int(lib().gtb_hdiff_vadv_workspace_bytes(fs[0].dtype, PREC[prec] if isinstance(prec, str)
-                                                        else int(prec), _dom(dom)))
+        need = hdiff_vadv_workspace_bytes(fs[0].dtype, prec, dom, save_factors)
         workspace = globals()["workspace"](need, stream) if need else None
     if workspace is not None:
         ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    flags = (GTB_WCON_LITERAL if literal else 0) | (GTB_SAVE_FACTORS if save_factors else 0)
     _check(lib().gtb_hdiff_vadv(*[ctypes.byref(f) for f in fs], float(dtr_stage), float(beta_v),
-                                PREC[prec] if isinstance(prec, str) else int(prec),
-                                GTB_WCON_LITERAL if literal else 0, _dom(domain),
+                                PREC[prec] if isinstance(prec, str) else int(prec), flags, _dom(domain),
                                 ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes, _stream(stream)))
     return out
 
@@ -333,9 +343,10 @@ def hdiff_adj(in_, coeff, out_bar, in_bar, coeff_bar=None, *, accumulate=False, 
 
 def vadv_adj(wcon, y_bar, u_stage_bar=None, u_pos_bar=None, utens_bar=None, utens_stage_bar=None, *,
              dtr_stage=3.0 / 20.0, beta_v=0.0, prec="native", literal=False, accumulate=False, domain=None,
-             workspace="auto", stream=None):
+             workspace="auto", factors=False, stream=None):
     """Reverse-mode vadv for fixed wcon (gtb_vadv_adj).  Passing one storage as both
-    u_stage_bar and u_pos_bar stores their sum there."""
+    u_stage_bar and u_pos_bar stores their sum there.  ``factors=True``: ``workspace`` is the
+    buffer that :func:`hdiff_vadv` filled with ``save_factors=True`` (consumed here)."""
     fw, fy = _as_field(wcon), _as_field(y_bar)
     ws_ptr, ws_bytes = None, 0
     if workspace is not None:
@@ -345,7 +356,7 @@ def vadv_adj(wcon, y_bar, u_stage_bar=None, u_pos_bar=None, utens_bar=None, uten
             workspace = globals()["workspace"](need, stream) if need else None
         if workspace is not None:
             ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
-    flags = (1 if literal else 0) | (GTB_ADJ_ACCUMULATE if accumulate else 0)
+    flags = (1 if literal else 0) | (GTB_ADJ_ACCUMULATE if accumulate else 0) | (GTB_ADJ_FACTORS if factors else 0)
     _check(lib().gtb_vadv_adj(ctypes.byref(fw), ctypes.byref(fy), _ptr(u_stage_bar), _ptr(u_pos_bar),
                               _ptr(utens_bar), _ptr(utens_stage_bar), float(dtr_stage), float(beta_v), PREC[prec],
                               flags, _dom(domain), ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes,

@@ -158,8 +158,24 @@ def test_hdiff_vadv_validation(L):
     fs_dt = fs[:3] + [fake(L, 10, 10, 6, origin=(1, 1, 0), dtype=1, ptr=4 * G)] + fs[4:]
     assert call(fs_dt, ws=40 * G, wsb=1 << 20) == -2
     # the deduced domain: min over fields of shape - origin - reach (in: 12-2-2 = 8, wcon: 10-1-1 = 8)
-    assert L.lib().gtb_hdiff_vadv_workspace_bytes(2, 0, (ctypes.c_int64 * 3)(8, 8, 6)) == 8 * 8 * 8 * 6
-    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 2, (ctypes.c_int64 * 3)(8, 8, 6)) == 16 * 8 * 8 * 6
+    n = 8 * 8 * 6
+    dom = (ctypes.c_int64 * 3)(8, 8, 6)
+    assert L.lib().gtb_hdiff_vadv_workspace_bytes(2, 0, 0, dom) == 8 * n       # c' (e parked in the output)
+    assert L.lib().gtb_hdiff_vadv_workspace_bytes(2, 0, 4, dom) == 16 * n      # + 1/p (GTB_SAVE_FACTORS)
+    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 2, 0, dom) == 16 * n      # double-float c' and e
+    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 2, 4, dom) == 24 * n
+    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 0, 4, dom) == 8 * n       # binary32 c' and 1/p
+    # the workspace with GTB_SAVE_FACTORS must be the larger size
+    assert call(fs, flags=4, ws=40 * G, wsb=8 * n) == -9
+    # gtb_vadv_adj: GTB_ADJ_FACTORS needs a workspace of the forward's factors
+    fw, fy = mk(3), mk(4)
+    adj = lambda flags, ws=None, wsb=0: lib.gtb_vadv_adj(ctypes.byref(fw), ctypes.byref(fy), None, None,
+                                                         ctypes.byref(mk(5)), None, 0.15, 0.0, 0, flags, dom,
+                                                         None if ws is None else ctypes.c_void_p(ws), wsb, None)
+    assert adj(8) == -9
+    assert adj(8, ws=40 * G, wsb=8 * n) == -9
+    assert adj(16) == -9                                                      # unknown flag
+    assert adj(8, ws=3 * G, wsb=16 * n) == -5                                 # overlaps wcon
 
 
 def test_step_validation(L):

@@ -213,3 +213,51 @@ def test_chain_gradient_central_differences(G):
         assert abs(fd[0] - exact) <= 1e-5 * max(1.0, abs(exact)), (d, fd[0], exact)
         good += 1
     assert good >= 24, good
+
+
+@pytest.mark.parametrize("dtype,prec", [(np.float64, "native"), (np.float32, "df"), (np.float32, "f64"),
+                                        (np.float32, "native")])
+def test_adjoint_from_kept_factors(G, dtype, prec):
+    """gtb_hdiff_vadv with GTB_SAVE_FACTORS returns the same output, and gtb_vadv_adj
+    on the kept factors (GTB_ADJ_FACTORS) the same cotangents as the refactorising
+    adjoint, bit for bit (the same pivots and c' values), merged and separate."""
+    import torch
+    from paper_2311_08322_b300 import inputs
+    I, J, K = 70, 33, 41
+    f = inputs.hdiff_vadv(I, J, K, seed=12)
+    dom = (I, J, K)
+    s = {n: G.storage_from(f[n].astype(dtype), (2, 2, 0) if n in ("in", "coeff") else (1, 1, 0))
+         for n in ("in", "coeff", "wcon", "utens", "utens_stage", "u_pos")}
+    zeros = lambda: G.storage_from(np.zeros_like(f["utens"]).astype(dtype), (1, 1, 0))
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    for merge in (True, False):
+        o1, o2 = zeros(), zeros()
+        F = torch.empty(G.hdiff_vadv_workspace_bytes(tdt, prec, dom, save_factors=True), dtype=torch.uint8,
+                        device="cuda")
+        G.hdiff_vadv(s["in"], s["coeff"], s["wcon"], s["utens"], s["utens_stage"], o1, prec=prec, domain=dom)
+        G.hdiff_vadv(s["in"], s["coeff"], s["wcon"], s["utens"], s["utens_stage"], o2, prec=prec, domain=dom,
+                     workspace=F, save_factors=True)
+        a1, b1, c1, a2, b2, c2 = (zeros() for _ in range(6))
+        if merge:
+            G.vadv_adj(s["wcon"], s["u_pos"], a1, a1, c1, prec=prec, domain=dom)
+            G.vadv_adj(s["wcon"], s["u_pos"], a2, a2, c2, prec=prec, domain=dom, workspace=F, factors=True)
+        else:
+            G.vadv_adj(s["wcon"], s["u_pos"], a1, b1, c1, prec=prec, domain=dom)
+            G.vadv_adj(s["wcon"], s["u_pos"], a2, b2, c2, prec=prec, domain=dom, workspace=F, factors=True)
+        G.device_status()
+        assert np.array_equal(o1.numpy(), o2.numpy())
+        for x, y in ((a1, a2), (b1, b2), (c1, c2)):
+            assert np.array_equal(x.numpy(), y.numpy()), (merge, prec)
+
+
+def test_chain_gradient_with_and_without_factors(G):
+    """The differentiable chain keeps each step's factors by default; without them the
+    backward refactorises: the same gradients, bit for bit."""
+    import torch
+    from paper_2311_08322_b300.autograd import chain_inputs
+    field, coeff, fixed, _ = chain_inputs(64, 40, 30, seed=4, dtype=torch.float64)
+    l1, gf1, gc1 = gpu_chain(G, field, coeff, fixed, 4)
+    fixed.save_factors = False
+    l2, gf2, gc2 = gpu_chain(G, field, coeff, fixed, 4)
+    assert l1 == l2
+    assert torch.equal(gf1, gf2) and torch.equal(gc1, gc2)
