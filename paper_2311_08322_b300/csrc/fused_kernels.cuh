@@ -402,15 +402,35 @@ __global__ void __launch_bounds__(TI * TJ + 32 * PW)
     }
     vstep(K - 1, false, h_prev, T(0), ut_n, uts_n, T(0), T(0));
 
-    // back substitution in z = x - h
+    // back substitution in z = x - h; levels in groups of BG, a group's inputs loaded
+    // before the previous group's outputs are stored (distinct levels, distinct addresses)
     if (active) {
         N z = e_last;
         po[(int64_t)(K - 1) * out.sk] = to_store<T, N>(dtr * z);
-#pragma unroll 4
-        for (int k = K - 2; k >= 0; --k) {
-            const N ek = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : epb[(size_t)k * cstride + cidx];
-            z = ek - cpb[(size_t)k * cstride + cidx] * z;
-            po[(int64_t)k * out.sk] = to_store<T, N>(dtr * z);
+        constexpr int BG = 4;
+        N eq[BG], cq[BG];
+        auto load_group = [&](int k0) {
+#pragma unroll
+            for (int q = 0; q < BG; ++q) {
+                const int k = k0 - q;
+                if (k < 0) break;
+                eq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : epb[(size_t)k * cstride + cidx];
+                cq[q] = cpb[(size_t)k * cstride + cidx];
+            }
+        };
+        if (K >= 2) load_group(K - 2);
+        for (int k0 = K - 2; k0 >= 0; k0 -= BG) {
+            N ec[BG], cc[BG];
+#pragma unroll
+            for (int q = 0; q < BG; ++q) ec[q] = eq[q], cc[q] = cq[q];
+            if (k0 - BG >= 0) load_group(k0 - BG);
+#pragma unroll
+            for (int q = 0; q < BG; ++q) {
+                const int k = k0 - q;
+                if (k < 0) break;
+                z = ec[q] - cc[q] * z;
+                po[(int64_t)k * out.sk] = to_store<T, N>(dtr * z);
+            }
         }
     }
 }

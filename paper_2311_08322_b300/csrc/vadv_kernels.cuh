@@ -224,15 +224,40 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
     }
 #undef GTB_LOAD
 
-    // backward substitution and output, utens_stage_out = dtr (x - u_pos)
+    // backward substitution and output, utens_stage_out = dtr (x - u_pos).  Levels go in
+    // groups of BG; a group's inputs (d'_k, c'_k, u_pos_k) are loaded before the previous
+    // group's outputs are stored (distinct levels, so distinct addresses: the out stride in
+    // k is nonzero), so the loads overlap instead of each waiting behind a store.
     N x = dp_prev;
     if (active) po[(int64_t)(K - 1) * out.sk] = to_store<T, N>(dtr * addx<N, T>(x, -pup[(int64_t)(K - 1) * up.sk]));
-#pragma unroll 4
-    for (int k = K - 2; k >= 0; --k) {
-        const N dk = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : dpb[(size_t)k * cstride + cidx];
-        x = dk - cpb[(size_t)k * cstride + cidx] * x;
-        const N o = dtr * addx<N, T>(x, -pup[(int64_t)k * up.sk]);
-        if (active) po[(int64_t)k * out.sk] = to_store<T, N>(o);
+    constexpr int BG = 4;
+    N dq[BG], cq[BG];
+    T uq[BG];
+    auto load_group = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < BG; ++q) {
+            const int k = k0 - q;
+            if (k < 0) break;
+            dq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : dpb[(size_t)k * cstride + cidx];
+            cq[q] = cpb[(size_t)k * cstride + cidx];
+            uq[q] = pup[(int64_t)k * up.sk];
+        }
+    };
+    if (K >= 2) load_group(K - 2);
+    for (int k0 = K - 2; k0 >= 0; k0 -= BG) {
+        N dc[BG], cc[BG];
+        T uc[BG];
+#pragma unroll
+        for (int q = 0; q < BG; ++q) dc[q] = dq[q], cc[q] = cq[q], uc[q] = uq[q];
+        if (k0 - BG >= 0) load_group(k0 - BG);
+#pragma unroll
+        for (int q = 0; q < BG; ++q) {
+            const int k = k0 - q;
+            if (k < 0) break;
+            x = dc[q] - cc[q] * x;
+            const N o = dtr * addx<N, T>(x, -uc[q]);
+            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(o);
+        }
     }
 }
 
