@@ -332,20 +332,23 @@ def run_gtb(args):
         dbuf.append(extra)
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = hbuf[0][0].numel() * 8 + hbuf[0][1].numel() * 8
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    s_in = [torch.cuda.Stream() for _ in range(args.e2e_in_streams)]
+    s_out = torch.cuda.Stream()
     free = [torch.cuda.Event(), torch.cuda.Event()]  # buffer set b no longer read by a copy-out
+    names_in = list(host)
 
     def e2e_run(n):
         for q in range(n):
             b = q % 2
             d = dbuf[b]
-            s_in.wait_event(free[b])
-            with torch.cuda.stream(s_in):
-                for nm, hv in host.items():
-                    d[nm].data.copy_(hv, non_blocking=True)
-            e_in = torch.cuda.Event()
-            e_in.record(s_in)
-            stream.wait_event(e_in)
+            for si, st_ in enumerate(s_in):  # the inputs split over the copy-in streams
+                st_.wait_event(free[b])
+                with torch.cuda.stream(st_):
+                    for nm in names_in[si::len(s_in)]:
+                        d[nm].data.copy_(host[nm], non_blocking=True)
+                e_in = torch.cuda.Event()
+                e_in.record(st_)
+                stream.wait_event(e_in)
             step(d)
             e_c = torch.cuda.Event()
             e_c.record(stream)
@@ -365,7 +368,8 @@ def run_gtb(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    s_in.wait_event(e0)
+    for st_ in s_in:
+        st_.wait_event(e0)
     e2e_run(args.e2e_steps)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -634,6 +638,7 @@ def main():
     ap.add_argument("--impl", choices=("gtb", "reference"), default="gtb")
     ap.add_argument("--sets", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-in-streams", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-fused", action="store_true")

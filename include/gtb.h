@@ -118,7 +118,9 @@ int gtb_hdiff(const gtb_field *in, const gtb_field *coeff, const gtb_field *out,
  * (binary64); for GTB_F32 storage NATIVE is all-binary32, F64 and DF keep the
  * whole column computation in binary64 / double-float.
  * A zero pivot (singular leading minor) yields non-finite values in that column,
- * as the unpivoted method does.  Limit: K <= 448; larger K is GTB_ERR_UNSUPPORTED.
+ * as the unpivoted method does.  Limit without a workspace: K <= 448 (the column
+ * state then lives in shared memory); larger K is GTB_ERR_UNSUPPORTED unless a
+ * workspace of gtb_vadv_workspace_bytes() bytes is passed.
  *
  * workspace: optional caller-owned device scratch for the forward sweep's
  * eliminated coefficients (c', and d' when it cannot be parked in the output),
@@ -174,7 +176,8 @@ int gtb_hdiff_adj(const gtb_field *in, const gtb_field *coeff, const gtb_field *
  * with GTB_SAVE_FACTORS for the same wcon, dtr_stage, beta_v, prec, flags
  * and domain (c'_k, then 1/p_k); the forward sweep then reads them instead of
  * refactorising A (the same values, so the same results), and overwrites
- * them: each set of factors serves one adjoint.  Limit: K <= 448.
+ * them: each set of factors serves one adjoint.  Limit without a workspace:
+ * K <= 448 (GTB_ERR_UNSUPPORTED beyond).
  */
 int gtb_vadv_adj(const gtb_field *wcon, const gtb_field *y_bar, const gtb_field *u_stage_bar,
                  const gtb_field *u_pos_bar, const gtb_field *utens_bar, const gtb_field *utens_stage_bar,

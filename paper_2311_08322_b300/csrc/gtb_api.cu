@@ -562,8 +562,10 @@ extern "C" int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const g
         if (overlaps(utens_stage_out, f[q]))
             return fail(GTB_ERR_ALIAS, "gtb_vadv: utens_stage_out overlaps %s", names[q]);
     }
-    if (dom[2] > kVadvMaxK)
-        return fail(GTB_ERR_UNSUPPORTED, "gtb_vadv: K = %lld exceeds the limit %d", (long long)dom[2], kVadvMaxK);
+    // the shared-memory form holds K levels of column state per thread; a workspace lifts the limit
+    if (dom[2] > kVadvMaxK && !(workspace && workspace_bytes >= vadv_ws_bytes_for(dt, prec, dom)))
+        return fail(GTB_ERR_UNSUPPORTED, "gtb_vadv: K = %lld exceeds the limit %d without a workspace",
+                    (long long)dom[2], kVadvMaxK);
     if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();
 
     const VadvGeom g = make_vadv_geom(dom, literal, dtr_stage, beta_v);
@@ -892,8 +894,9 @@ extern "C" int gtb_vadv_adj(const gtb_field *wcon, const gtb_field *y_bar, const
             if (overlaps(f[q], f[r])) return fail(GTB_ERR_ALIAS, "gtb_vadv_adj: %s overlaps %s", names[q], names[r]);
         }
     }
-    if (dom[2] > kVadvMaxK)
-        return fail(GTB_ERR_UNSUPPORTED, "gtb_vadv_adj: K = %lld exceeds the limit %d", (long long)dom[2], kVadvMaxK);
+    if (dom[2] > kVadvMaxK && !(workspace && workspace_bytes >= vadv_adj_ws_bytes_for(dt, prec, dom)))
+        return fail(GTB_ERR_UNSUPPORTED, "gtb_vadv_adj: K = %lld exceeds the limit %d without a workspace",
+                    (long long)dom[2], kVadvMaxK);
     if (workspace && reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
         return fail(GTB_ERR_LAYOUT, "gtb_vadv_adj: workspace must be 16-byte aligned");
     if (dom[0] == 0 || dom[1] == 0 || dom[2] == 0) return ok();

@@ -71,11 +71,18 @@ def test_max_k_fp64(G, orc):
 
 
 def test_k_beyond_limit_rejected(G):
+    """Without a workspace the column state lives in shared memory: K <= 448."""
     f = draw(4, 2, 449, 1)
     st = {n: G.storage_from(f[n], (1, 1, 0)) for n in NAMES}
     with pytest.raises(G.GtbError) as e:
-        G.vadv(*[st[n] for n in NAMES], G.storage_from(np.zeros_like(f["utens"]), (1, 1, 0)))
+        G.vadv(*[st[n] for n in NAMES], G.storage_from(np.zeros_like(f["utens"]), (1, 1, 0)), workspace=None)
     assert e.value.code == -8
+
+
+def test_large_k_with_workspace_fp64(G, orc):
+    """With a workspace any K runs: K = 1000."""
+    got, ref = run_case(G, orc, 33, 3, 1000, seed=10, wamp=0.15)
+    assert rel_err(got, ref) <= F64_TOL
 
 
 def test_in_place(G, orc):
