@@ -215,11 +215,9 @@ __device__ __forceinline__ bool limited(T f, T g) {
     }
 }
 
-// The adjoint of one tile (staged in shared memory by the caller: in at
-// tile +- 3, q = coeff * out_bar at tile +- 2, in the 8-byte slots of S_x and
-// S_q) with the arithmetic of policy P: V is the value type of in, lap, fluxes
-// and cotangents; cvt_in / cvt_q bring in and q to V in place, lap /
-// limited_face / out_* do the rest.
+// The adjoint of one tile (staged in shared memory by the caller, in the
+// policy's value type V: in at tile +- 3 in S_x, q = coeff * out_bar at
+// tile +- 2 in S_q) with the arithmetic of policy P: lap / limited_face / out_*.
 //   faces:  keep = not (f * (in[+1] - in) > 0),  g = keep (q - q[+1])
 //   lb      = (gx[i-1] - gx[i]) + (gy[j-1] - gy[j])      (cotangent of lap)
 //   in_bar  = out_bar - (4 lb - sum of the 4 neighbours of lb)
@@ -237,11 +235,6 @@ __device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x,
     V *S_lb = S_q;                    // lap cotangents, tile +- 1 (q is dead by then)
     unsigned char *S_kx = S_keep, *S_ky = S_keep + H::GXX * H::GXY;
     const int tid = threadIdx.x, I = g.I, J = g.J;
-    if (P::kConvert) {  // in place: each slot converted by the thread that reads it
-        for (int idx = tid; idx < H::IX * H::IY; idx += NT) S_x[idx] = pol.cvt_in(S_x[idx]);
-        for (int idx = tid; idx < H::QX * H::QY; idx += NT) S_q[idx] = pol.cvt_q(S_q[idx]);
-        __syncthreads();
-    }
     auto X = [&](int a, int b) -> V { return S_x[(a + 3) + (b + 3) * H::IX]; };  // tile-relative
     auto GIN = [&](int a, int b) -> const T * {  // the binary64 value, for exact ties
         return in.p + (ti0 + a) + (int64_t)(tj0 + b) * in.sj + (int64_t)k * in.sk;
@@ -314,9 +307,6 @@ __device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x,
 template <typename T>
 struct AdjNative {
     using V = T;
-    static constexpr bool kConvert = false;
-    __device__ __forceinline__ V cvt_in(V x) const { return x; }
-    __device__ __forceinline__ V cvt_q(V x) const { return x; }
     __device__ __forceinline__ V lap(V c, V e, V w, V n, V s) const { return T(4) * c - (((e + w) + n) + s); }
     __device__ __forceinline__ bool limited_face(V f, V x1, V x0, const T *, const T *) const {
         return limited(f, x1 - x0);
@@ -326,16 +316,13 @@ struct AdjNative {
 };
 
 // Binary64 in exact int64 fixed point (the form of the forward kernels): in with
-// scale Ein, q with scale Eq (each converted in place from its binary64 bits);
+// scale Ein, q with scale Eq (converted when the tile is staged);
 // every add and subtract exact, the limiter takes the exact signs (the binary64
 // inputs are read back only when two cells truncate alike); the two outputs are
 // rounded once each on the way back.
 struct AdjFixed {
     using V = int64_t;
-    static constexpr bool kConvert = true;
     int Ein, Eq;
-    __device__ __forceinline__ V cvt_in(V raw) const { return to_fixed(__longlong_as_double(raw), Ein); }
-    __device__ __forceinline__ V cvt_q(V raw) const { return to_fixed(__longlong_as_double(raw), Eq); }
     __device__ __forceinline__ V lap(V c, V e, V w, V n, V s) const { return 4 * c - (((e + w) + n) + s); }
     __device__ __forceinline__ bool limited_face(V f, V x1, V x0, const double *p1, const double *p0) const {
         const int gsign = x1 != x0 ? (x1 > x0 ? 1 : -1) : exact_dir(x1, x0, *p1, *p0);
@@ -364,29 +351,37 @@ __global__ void __launch_bounds__(NT)
     const int I = g.I, J = g.J;
 
     // in on the cells the forward definition reads (zero elsewhere, including the
-    // unread halo corners), q = coeff * out_bar on the domain
+    // unread halo corners), q = coeff * out_bar on the domain; each thread keeps its
+    // cells in registers until the tile's scales are known
+    constexpr int CI = (H::IX * H::IY + NT - 1) / NT, CQ = (H::QX * H::QY + NT - 1) / NT;
+    T vin[CI], vq[CQ];
     unsigned ein = 0, eq = 0, qnz = 0, inz = 0;
-    for (int idx = tid; idx < H::IX * H::IY; idx += NT) {
+#pragma unroll
+    for (int c = 0; c < CI; ++c) {
+        const int idx = tid + c * NT;
         const int a = ti0 - 3 + idx % H::IX, b = tj0 - 3 + idx / H::IX;
         T v = T(0);
-        if (hdiff_reads(a, b, I, J)) v = in.p[a + (int64_t)b * in.sj + (int64_t)k * in.sk];
-        S_in[idx] = v;
+        if (idx < H::IX * H::IY && hdiff_reads(a, b, I, J)) v = in.p[a + (int64_t)b * in.sj + (int64_t)k * in.sk];
+        vin[c] = v;
         if constexpr (FIX) {
             ein = max(ein, ((unsigned)__double2hiint(v) >> 20) & 0x7FFu);
             inz |= (unsigned)((__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll) != 0);
         }
     }
-    for (int idx = tid; idx < H::QX * H::QY; idx += NT) {
+#pragma unroll
+    for (int c = 0; c < CQ; ++c) {
+        const int idx = tid + c * NT;
         const int a = ti0 - 2 + idx % H::QX, b = tj0 - 2 + idx / H::QX;
         T v = T(0);
-        if (a >= 0 && a < I && b >= 0 && b < J)
+        if (idx < H::QX * H::QY && a >= 0 && a < I && b >= 0 && b < J)
             v = coeff.p[a + (int64_t)b * coeff.sj + (int64_t)k * coeff.sk] * ob.p[a + (int64_t)b * ob.sj + (int64_t)k * ob.sk];
-        S_q[idx] = v;
+        vq[c] = v;
         if constexpr (FIX) {
             eq = max(eq, ((unsigned)__double2hiint(v) >> 20) & 0x7FFu);
             qnz |= (unsigned)((__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll) != 0);
         }
     }
+    bool fixed = false;
     if constexpr (FIX) {
         ein = __reduce_max_sync(0xffffffffu, ein);
         eq = __reduce_max_sync(0xffffffffu, eq);
@@ -394,9 +389,7 @@ __global__ void __launch_bounds__(NT)
         inz = __reduce_or_sync(0xffffffffu, inz);
         if ((tid & 31) == 0)
             s_e[tid >> 5][0] = ein, s_e[tid >> 5][1] = eq, s_e[tid >> 5][2] = qnz, s_e[tid >> 5][3] = inz;
-    }
-    __syncthreads();
-    if constexpr (FIX) {
+        __syncthreads();
         ein = eq = qnz = inz = 0;
 #pragma unroll
         for (int w = 0; w < NT / 32; ++w)
@@ -404,7 +397,34 @@ __global__ void __launch_bounds__(NT)
         // a field that is zero on the whole tile converts exactly at any scale
         if (ein == 0 && !inz) ein = 64;
         if (eq == 0 && !qnz) eq = 64;
-        if (ein >= 64 && ein <= 2040 && eq >= 64 && eq <= 2040) {
+        fixed = ein >= 64 && ein <= 2040 && eq >= 64 && eq <= 2040;
+    }
+    // stage the tile: fixed point straight from the registers, or the values themselves
+#pragma unroll
+    for (int c = 0; c < CI; ++c) {
+        const int idx = tid + c * NT;
+        if (idx >= H::IX * H::IY) break;
+        if constexpr (FIX) {
+            if (fixed) reinterpret_cast<int64_t *>(S_in)[idx] = to_fixed(vin[c], (int)ein);
+            else S_in[idx] = vin[c];
+        } else {
+            S_in[idx] = vin[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CQ; ++c) {
+        const int idx = tid + c * NT;
+        if (idx >= H::QX * H::QY) break;
+        if constexpr (FIX) {
+            if (fixed) reinterpret_cast<int64_t *>(S_q)[idx] = to_fixed(vq[c], (int)eq);
+            else S_q[idx] = vq[c];
+        } else {
+            S_q[idx] = vq[c];
+        }
+    }
+    __syncthreads();
+    if constexpr (FIX) {
+        if (fixed) {
             hdiff_adj_tile<T, TI, TJ, NT>(AdjFixed{(int)ein, (int)eq}, reinterpret_cast<int64_t *>(S_in),
                                           reinterpret_cast<int64_t *>(S_q), S_keep, in, ob, ib, cb, g, ti0, tj0, k);
             return;
