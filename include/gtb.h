@@ -334,6 +334,17 @@ int gtb_vadv_noalloc(const gtb_field *u_stage, const gtb_field *wcon, const gtb_
  */
 int gtb_device_status(void *stream);
 
+/*
+ * gtb_selftest_wait -- exercises the bounded-wait failure path that every
+ * kernel of the library relies on (the paper has no counterpart): one warp
+ * waits on an mbarrier; with arrive = 0 nobody completes it, the wait gives up
+ * after limit_ns (0 < limit_ns <= 2e9), sets the device error word and the
+ * kernel returns, so that gtb_device_status() then reports GTB_ERR_DEVICE and
+ * the context stays usable; with arrive = 1 one thread completes the phase
+ * first and nothing is reported.  Bad arguments: GTB_ERR_ARG.
+ */
+int gtb_selftest_wait(long long limit_ns, int arrive, void *stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *gtb_last_error(void);
 

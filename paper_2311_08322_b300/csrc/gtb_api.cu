@@ -732,6 +732,14 @@ extern "C" int gtb_device_status(void *stream) {
     return ok();
 }
 
+extern "C" int gtb_selftest_wait(long long limit_ns, int arrive, void *stream) {
+    if (limit_ns <= 0 || limit_ns > (long long)kWaitLimitNs)
+        return fail(GTB_ERR_ARG, "gtb_selftest_wait: limit %lld ns outside (0, %llu]", limit_ns, kWaitLimitNs);
+    if (arrive != 0 && arrive != 1) return fail(GTB_ERR_ARG, "gtb_selftest_wait: arrive must be 0 or 1");
+    selftest_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>((unsigned long long)limit_ns, arrive);
+    return launch_status("gtb_selftest_wait launch");
+}
+
 extern "C" const char *gtb_last_error(void) { return t_err; }
 
 extern "C" const char *gtb_version(void) { return "gtb 0.1 sm_103a"; }

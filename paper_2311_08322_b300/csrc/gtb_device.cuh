@@ -62,17 +62,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait: true when the phase completed, false (and the device error
-// word set) when kWaitLimitNs elapsed first.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// word set) when limit_ns (by default kWaitLimitNs) elapsed first.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        if (globaltimer_ns() - t0 > limit_ns) {
             atomicExch(&g_device_error, 1);
             return false;
         }
     }
     return true;
+}
+
+// The failure path of every bounded wait, exercised on purpose: one warp waits
+// on an mbarrier that nobody arrives at (arrive = 0: the wait runs out after
+// limit_ns, sets the device error word and the kernel returns normally) or that
+// one thread completes first (arrive = 1: no error).
+__global__ void selftest_wait_kernel(unsigned long long limit_ns, int arrive) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (arrive && threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    __syncwarp();
+    mbar_wait(&bar, 0, limit_ns);
 }
 
 // 3-D tiled TMA load of one box into shared memory, completing on `bar`.

@@ -55,7 +55,8 @@ _lib = None
 EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_hdiff_adj", "gtb_vadv_adj",
            "gtb_vadv_adj_workspace_bytes", "gtb_halo_periodic", "gtb_halo_periodic_adj", "gtb_device_status",
            "gtb_batch_plan", "gtb_batch_run", "gtb_plan_info", "gtb_plan_destroy", "gtb_hdiff_vadv",
-           "gtb_hdiff_vadv_workspace_bytes", "gtb_step", "gtb_last_error", "gtb_version")
+           "gtb_hdiff_vadv_workspace_bytes", "gtb_step", "gtb_selftest_wait", "gtb_last_error",
+           "gtb_version")
 GTB_ADJ_ACCUMULATE = 2
 GTB_SAVE_FACTORS = 4
 GTB_ADJ_FACTORS = 8
@@ -101,6 +102,8 @@ def lib() -> ctypes.CDLL:
         for n in ("gtb_batch_plan", "gtb_batch_run", "gtb_plan_info", "gtb_plan_destroy"):
             getattr(L, n).restype = ctypes.c_int
         L.gtb_device_status.argtypes = [vp]
+        L.gtb_selftest_wait.argtypes = [ctypes.c_longlong, ctypes.c_int, vp]
+        L.gtb_selftest_wait.restype = ctypes.c_int
         L.gtb_last_error.restype = ctypes.c_char_p
         L.gtb_version.restype = ctypes.c_char_p
         for n in ("gtb_hdiff", "gtb_vadv", "gtb_device_status"):
@@ -373,6 +376,12 @@ def halo_periodic_adj(f, hi=2, hj=2, *, domain=None, stream=None):
     """Adjoint of the refresh: fold the halo's values into the domain (gtb_halo_periodic_adj)."""
     _check(lib().gtb_halo_periodic_adj(_ptr(f), int(hi), int(hj), _dom(domain), _stream(stream)))
     return f
+
+
+def selftest_wait(limit_ns: int, arrive: bool, stream=None):
+    """Exercise the bounded-wait failure path (gtb_selftest_wait): with arrive=False the
+    wait runs out after limit_ns and device_status() then raises GTB_ERR_DEVICE."""
+    _check(lib().gtb_selftest_wait(int(limit_ns), 1 if arrive else 0, _stream(stream)))
 
 
 def device_status(stream=None):

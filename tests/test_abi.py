@@ -208,3 +208,10 @@ def test_step_validation(L):
     assert call(fs[:8] + [mk(8, o=(1, 2, 0))], **ok_ws) == -5      # shifted view of utens_stage
     fs_dt = fs[:6] + [fake(L, 10, 10, 6, origin=(1, 1, 0), dtype=1, ptr=7 * G)] + fs[7:]
     assert call(fs_dt, **ok_ws) == -2
+
+
+def test_selftest_wait_arguments(L):
+    """Argument checks run before any launch (no GPU needed)."""
+    lib = L.lib()
+    for limit, arrive in ((0, 0), (-1, 1), (2_000_000_001, 0), (1000, 3)):
+        assert lib.gtb_selftest_wait(limit, arrive, None) == -9
