@@ -23,6 +23,8 @@ Prints ONE JSON line (rank 0).
   binary64 and double-float column arithmetic) beside the FP64 path there.
 * batched: the 48-member ensemble of uneven domains, autotuned plan replayed
   from a CUDA graph vs the loop of single-domain launches.
+* call_overhead: the paper's split of Python-call vs compiled-call time, for
+  one step on the small 64x64x40 workload (device time, C-ABI call, Python call).
 * fused_chain: the chained step (vadv of hdiff's output) as two launches vs
   gtb_hdiff_vadv, one kernel that keeps h on chip.
 * adjoint_forward_ratio: backward / forward time of one chained step
@@ -313,6 +315,7 @@ def run_gtb(args):
     v_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
     sep_ms = float(np.mean([e[0].elapsed_time(e[2]) for e in evs]))
     chain = fused_chain_compare(gtb, f, sets) if rank == 0 and not args.no_fused else None
+    calls = call_overhead() if rank == 0 and not args.no_fused else None
     adj = adjoint_ratio(gtb, f, sets) if rank == 0 and not args.no_adjoint else None
     el_ms = max_over_ranks(el_ms, dist if world > 1 else None, "cuda")
     value = whole_job_mpoints(world, POINTS, args.steps, el_ms)
@@ -415,7 +418,7 @@ def run_gtb(args):
                        "l2": f"{args.sets} rotating input sets of "
                              f"{(hdiff_bytes(I, J, K, 8) + vadv_bytes(I, J, K, 8)) / 1e6:.0f} MB each (> 126 MB L2)"},
             "kernels": kern, "roofline": roof, "clocks": clk, "gpu_launches": args.steps,
-            "fused_chain": chain,
+            "fused_chain": chain, "call_overhead": calls,
             "adjoint_forward_ratio": None if adj is None else adj["ratio"], "adjoint": adj,
             "e2e": {"value": round(e2e_value, 1), "unit": "Mpoints/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}}
@@ -432,6 +435,64 @@ def run_gtb(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def call_overhead(reps=2000, host_reps=200):
+    """The paper's timing split (Python call vs the compiled call alone) for one step on
+    the small 64x64x40 FP64 workload, where launch and call costs show: device time per
+    step (CUDA events), host time per call of the C ABI with prepared descriptors, and
+    host time per call of the Python binding (descriptor marshalling included)."""
+    import ctypes
+    import torch
+    from paper_2311_08322_b300 import gtb, inputs
+    Is, Js, Ks = 64, 64, 40
+    f = inputs.hdiff_vadv(Is, Js, Ks, seed=0)
+    o2, o1 = (HDIFF_HALO, HDIFF_HALO, 0), (VADV_HALO, VADV_HALO, 0)
+    s = {"in": gtb.storage_from(f["in"], o2), "coeff": gtb.storage_from(f["coeff"], o2),
+         "hout": gtb.storage_from(np.zeros_like(f["coeff"]), o2),
+         "vout": gtb.storage_from(np.zeros_like(f["utens"]), o1)}
+    for n in VADV_NAMES:
+        s[n] = gtb.storage_from(f[n], o1)
+    args = [s["in"], s["coeff"], s["hout"], *[s[n] for n in VADV_NAMES], s["vout"]]
+    stream = torch.cuda.current_stream()
+    dom = (Is, Js, Ks)
+    ws = gtb.workspace(gtb.vadv_workspace_bytes(torch.float64, "native", dom))
+    fields = [gtb._as_field(x) for x in args]
+    refs = [ctypes.byref(x) for x in fields]
+    c_dom = (ctypes.c_int64 * 3)(*dom)
+    c_ws, c_st, lib = ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(stream.cuda_stream), gtb.lib()
+    nbytes = ws.numel()
+
+    def c_call():
+        lib.gtb_step(*refs, 0.15, 0.0, 0, 0, c_dom, c_ws, nbytes, c_st)
+
+    def py_call():
+        gtb.step(*args, domain=dom, stream=stream)
+
+    out = {"workload": "one hdiff+vadv step (gtb_step) at 64x64x40 FP64"}
+    # host time per call over fewer calls than the launch queue holds (so that the host
+    # never waits for the device), median of several bursts
+    for name, fn in (("c_abi_us_per_call", c_call), ("python_us_per_call", py_call)):
+        for _ in range(50):
+            fn()
+        torch.cuda.synchronize()
+        per = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            for _ in range(host_reps):
+                fn()
+            per.append((time.perf_counter() - t0) / host_reps * 1e6)
+            torch.cuda.synchronize()
+        out[name] = round(statistics.median(per), 2)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        c_call()
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["device_us_per_step"] = round(a.elapsed_time(b) / reps * 1e3, 2)
+    gtb.device_status()
+    return out
 
 
 def fused_chain_compare(gtb, f, sets, reps=50):

@@ -166,9 +166,20 @@ def storage_from(arr: np.ndarray, origin, *, device="cuda", dtype=None) -> Stora
 
 
 def field(t, origin=None) -> GtbField:
-    """gtb_field describing a CUDA tensor (or Storage) shaped (nk, nj, ni)."""
+    """gtb_field describing a CUDA tensor (or Storage) shaped (nk, nj, ni).  A Storage
+    keeps the descriptor it was last given and reuses it while its tensor's pointer,
+    dtype, shape and strides and its origin are unchanged (building the ctypes
+    structure is most of a call's Python cost)."""
     if isinstance(t, Storage):
-        origin = t.origin if origin is None else origin
+        if origin is None:
+            d = t.data
+            key = (d.data_ptr(), d.dtype, d.shape, d.stride(), t.origin)
+            memo = t.__dict__.get("_field_memo")
+            if memo is not None and memo[0] == key:
+                return memo[1]
+            f = field(d, t.origin)
+            t.__dict__["_field_memo"] = (key, f)
+            return f
         t = t.data
     if origin is None:
         origin = (0, 0, 0)
