@@ -26,10 +26,6 @@
 namespace gtb {
 
 // ------------------------------------------------------------------ vadv adjoint
-struct VadvAdjOut {
-    int64_t sj, sk;
-};
-
 // FACT: the workspace holds the forward solve's factors, c'_k then 1/p_k (kept by
 // gtb_hdiff_vadv with GTB_SAVE_FACTORS): the forward sweep reads them instead of
 // refactorising A, and v_k overwrites 1/p_k in place.

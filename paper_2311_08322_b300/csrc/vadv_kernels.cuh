@@ -61,19 +61,7 @@ template <> __device__ __forceinline__ df addx<df, float>(df a, float b) { retur
 template <typename N, typename T> __device__ __forceinline__ N add2(T a, T b) { return to_num<N, T>(a) + to_num<N, T>(b); }
 template <> __device__ __forceinline__ df add2<df, float>(float a, float b) { return df_add2(a, b); }
 
-// face-velocity sum s_m of level m for this lane's column (all lanes take part
-// in the shuffle, so it is called warp-uniformly)
-template <typename T, typename N>
-__device__ __forceinline__ N face_sum(const T *__restrict__ wcol, const T *__restrict__ wcol_next, int64_t off,
-                                      bool last_lane, int literal) {
-    const T lo = wcol[off];
-    if (literal) return to_num<N, T>(lo);
-    T hi = __shfl_down_sync(0xffffffffu, lo, 1);
-    if (last_lane) hi = wcol_next[off];
-    return to_num<N, T>(lo) + to_num<N, T>(hi);
-}
-
-// Inputs of one level k for this lane's column, loaded PD levels ahead.
+// Inputs of one level k for this lane's column (loaded one level ahead of their use).
 template <typename T>
 struct Level {
     T up, ut, uts, us1, w;  // u_pos_k, utens_k, utens_stage_k, u_stage_{k+1}, wcon_{k+1}(i)
