@@ -186,3 +186,46 @@ def test_workspace_required(G):
     with pytest.raises(G.GtbError) as e:
         G.hdiff_vadv(sin, scf, sv["wcon"], sv["utens"], sv["utens_stage"], workspace=None)
     assert e.value.code == -9
+
+
+def draw_padded(I, J, K, seed, pad):
+    """The same fields with extra storage beyond the halos (origins shifted by pad):
+    the TMA box of `in` then starts off the 16-byte boundary for odd i shifts."""
+    pi, pj, pk = pad
+    rng = np.random.default_rng(seed)
+    hs, vs = (K + 2 * pk, J + 4 + 2 * pj, I + 4 + 2 * pi), (K + 2 * pk, J + 2 + 2 * pj, I + 2 + 2 * pi)
+    return dict(inp=rng.uniform(-1, 1, hs), coeff=rng.uniform(0, 0.025, hs), wcon=rng.uniform(-0.5, 0.5, vs),
+                utens=rng.uniform(-1, 1, vs), utens_stage=rng.uniform(-1, 1, vs))
+
+
+@pytest.mark.parametrize("pad", [(1, 0, 0), (3, 2, 1), (5, 1, 2)])
+def test_origin_offsets_fp64(G, orc, pad):
+    I, J, K = 70, 21, 9
+    dom = (I, J, K)
+    pi, pj, pk = pad
+    f = draw_padded(I, J, K, 31, pad)
+    oh, ov = (2 + pi, 2 + pj, pk), (1 + pi, 1 + pj, pk)
+    sin, scf = G.storage_from(f["inp"], oh), G.storage_from(f["coeff"], oh)
+    sv = {k: G.storage_from(f[k], ov) for k in ("wcon", "utens", "utens_stage")}
+    out = G.storage_from(np.zeros_like(f["utens"]), ov)
+    G.hdiff_vadv(sin, scf, sv["wcon"], sv["utens"], sv["utens_stage"], out, domain=dom)
+    G.device_status()
+    h = region(orc.hdiff(f["inp"], f["coeff"], origin_in=oh, domain=dom), oh, dom)
+    hs = np.zeros_like(f["utens"])
+    hs[pk:pk + K, 1 + pj:1 + pj + J, 1 + pi:1 + pi + I] = h
+    ref = region(orc.vadv(hs, f["wcon"], hs, f["utens"], f["utens_stage"], origin=ov, domain=dom), ov, dom)
+    assert rel_err(region(out.numpy(), ov, dom), ref) <= F64_TOL
+
+
+@pytest.mark.parametrize("prec", ["native", "f64", "df"])
+@pytest.mark.parametrize("I,J,K", [(1, 1, 2), (17, 9, 3), (33, 24, 1)])
+def test_small_fp32(G, orc, prec, I, J, K):
+    """Ragged FP32 tiles (16 x 8) with partial rows and columns, K = 1."""
+    dom = (I, J, K)
+    f = draw(*dom, 13)
+    a = run_gpu(G, f, dom, np.float32, prec)
+    b = run_gpu(G, f, dom, np.float32, prec, fused=False)
+    f32 = {k: v.astype(np.float32).astype(np.float64) for k, v in f.items()}
+    ref = oracle_chain(orc, f32, dom)
+    ea, eb = rel_err(a, ref), rel_err(b, ref)
+    assert ea <= max(F32_TOL, 1.5 * eb) if prec == "native" else ea <= F32_TOL

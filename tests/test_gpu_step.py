@@ -146,3 +146,28 @@ def test_workspace_required(G):
     with pytest.raises(G.GtbError) as e:
         G.step(sin, scf, hout, *[sv[n] for n in VN], workspace=None)
     assert e.value.code == -9
+
+
+@pytest.mark.parametrize("pad", [(1, 0, 0), (3, 2, 1)])
+def test_origin_offsets_fp64(G, orc, pad):
+    """Origins beyond the halos (the TMA box of `in` off the 16-byte boundary)."""
+    I, J, K = 70, 21, 9
+    dom = (I, J, K)
+    pi, pj, pk = pad
+    rng = np.random.default_rng(41)
+    hs, vs = (K + 2 * pk, J + 4 + 2 * pj, I + 4 + 2 * pi), (K + 2 * pk, J + 2 + 2 * pj, I + 2 + 2 * pi)
+    f = dict(inp=rng.uniform(-1, 1, hs), coeff=rng.uniform(0, 0.025, hs))
+    for n in ("u_stage", "u_pos", "utens", "utens_stage"):
+        f[n] = rng.uniform(-1, 1, vs)
+    f["wcon"] = rng.uniform(-0.5, 0.5, vs)
+    oh, ov = (2 + pi, 2 + pj, pk), (1 + pi, 1 + pj, pk)
+    sin, scf = G.storage_from(f["inp"], oh), G.storage_from(f["coeff"], oh)
+    hout = G.storage_from(np.zeros_like(f["coeff"]), oh)
+    sv = {n: G.storage_from(f[n], ov) for n in VN}
+    vout = G.storage_from(np.zeros_like(f["utens"]), ov)
+    G.step(sin, scf, hout, *[sv[n] for n in VN], vout, domain=dom)
+    G.device_status()
+    rh = region(orc.hdiff(f["inp"], f["coeff"], origin_in=oh, domain=dom), oh, dom)
+    rv = region(orc.vadv(*[f[n] for n in VN], origin=ov, domain=dom), ov, dom)
+    assert rel_err(region(hout.numpy(), oh, dom), rh) <= F64_TOL
+    assert rel_err(region(vout.numpy(), ov, dom), rv) <= F64_TOL
