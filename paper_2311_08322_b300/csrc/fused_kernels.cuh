@@ -23,12 +23,13 @@
 // The two sides meet only through the ring's full / empty mbarriers (bounded
 // waits), so the producers run up to RING levels ahead and the consumers never
 // wait on a block barrier.
-// The back substitution runs on the shifted unknown z = x - h (u_pos = h), so
-// that h is not needed after the forward sweep:
-//   e_k = (d'_k - h_k) - c'_k h_{k+1},   z_{K-1} = e_{K-1},
-//   z_k = e_k - c'_k z_{k+1},            utens_stage_out_k = dtr z_k,
-// the same unknowns as x_k - h_k of the Thomas solution (a different rounding
-// order than dtr (x_k - u_pos_k)).  c'_k goes to the caller's workspace, e_k is
+// The column solve takes the system in the shifted unknown y = x + h (with
+// beta_v = 0 the explicit terms then fold into the matrix) and runs the back
+// substitution on z = x - h, so that h is not needed after the forward sweep:
+//   e_k = (d'_k - 2h_k) - c'_k 2h_{k+1},   z_{K-1} = e_{K-1},
+//   z_k = e_k - c'_k z_{k+1},              utens_stage_out_k = dtr z_k,
+// the same unknowns as x_k - h_k of the Thomas solution, in a different
+// rounding order (fused_consumer).  c'_k goes to the caller's workspace, e_k is
 // parked in the output array (or in the workspace when the arithmetic type is
 // wider than the storage type).
 #pragma once
@@ -279,42 +280,24 @@ __device__ __forceinline__ void hdiff_producer(const CUtensorMap *tmap, const Vi
         for (int s = 0; s < STAGES; ++s) mbar_wait(&tbar[s], 0), mbar_wait(&tbar[s], 1);
 }
 
+// The consumer warps of hdiff_vadv_kernel: the vadv column solve of the tile's
+// columns, level by level as the producers publish h.  With u_stage = u_pos = h
+// the system of Sec. 3.1 is solved in the shifted unknown y = x + h (the explicit
+// terms fold into the matrix when SYM, i.e. beta_v = 0):
+//   A y = 2 dtr h_k + utens_k + utens_stage_k [+ g_k (h_k - h_{k-1}) + g_{k+1} (h_{k+1} - h_k)]
+// with g = as - a, and the back substitution runs in z = x - h = y - 2h, the output
+// over dtr: z_k = e_k - c'_k z_{k+1}, e_k = d'_k - 2h_k - c'_k 2h_{k+1}.  SYM gets a
+// body of its own so that no FP64 instruction of the general case is issued.
 // ws: c'_k ([k][j*I + i]); rsave: 1/p_k in the same layout, or null (the factors
 // kept for the adjoint); ework: e_k when it is not parked in the output.
-template <typename T, typename N, int TI, int TJ, int PW, int STAGES, int RING, bool USE_TMA, bool DPG>
-__global__ void __launch_bounds__(TI * TJ + 32 * PW)
-    hdiff_vadv_kernel(const __grid_constant__ CUtensorMap tmap, const View<const T> in, const View<const T> coeff,
-                      const View<const T> wc, const View<const T> ut, const View<const T> uts, const View<T> out,
-                      const HdiffGeom hg, const VadvGeom g, N *__restrict__ ws, N *__restrict__ rsave,
-                      N *__restrict__ ework) {
-    using Lay = FusedLayout<T, TI, TJ, PW, STAGES, RING>;
-    using Tile = typename Lay::Tile;
-    constexpr int NC = Tile::NC, CW = Tile::CW;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char *base =
-        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    T *H = reinterpret_cast<T *>(base + Lay::h_off);  // H[slot][point]
-    uint64_t *tbar = reinterpret_cast<uint64_t *>(base + Lay::bar_off);
-    uint64_t *full = tbar + STAGES, *empty = full + RING;
-
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int ti0 = blockIdx.x * TI, tj0 = blockIdx.y * TJ;
+template <typename T, typename N, int TI, int TJ, int RING, bool DPG, bool SYM>
+__device__ __forceinline__ void fused_consumer(const View<const T> &wc, const View<const T> &ut,
+                                               const View<const T> &uts, const View<T> &out, const VadvGeom &g,
+                                               N *__restrict__ ws, N *__restrict__ rsave, N *__restrict__ ework,
+                                               const T *H, uint64_t *full, uint64_t *empty, int NC, int ti0, int tj0,
+                                               int tid) {
+    const int lane = tid & 31;
     const int I = g.I, J = g.J, K = g.K;
-
-    if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&tbar[s], 1);
-        for (int s = 0; s < RING; ++s) mbar_init(&full[s], PW), mbar_init(&empty[s], CW);
-        fence_mbar_init();
-    }
-    __syncthreads();  // the only block-wide barrier
-
-    if (w >= CW) {
-        hdiff_producer<T, TI, TJ, PW, STAGES, USE_TMA>(&tmap, in, coeff, hg, ti0, tj0, base, Lay::x_off, Lay::l_off,
-                                                       Lay::e_off, tbar, RingEmit<T>{H, full, empty, NC, RING});
-        return;
-    }
-
-    // ==================================================================== consumer warps
     const int ci = tid % TI, cj = tid / TI;
     const int i = ti0 + ci, j = tj0 + cj;
     const bool active = (i < I) && (j < J);
@@ -333,15 +316,17 @@ __global__ void __launch_bounds__(TI * TJ + 32 * PW)
 
     const N dtr = num_const<N>(g.dtr);
     const N ka = num_const<N>(g.ka);
-    const N kas = num_const<N>(g.kas);
+    const N kg = num_const<N>(g.kg);
     const N zero = num_const<N>(0.0);
     const int kexp = g.ka_pow2;
 
-    N dm = zero, a_cur = zero, as_cur = zero, cp_prev = zero, dp_prev = zero, e_last = zero;
+    N a_cur = zero, g_cur = zero, dpl_prev = zero, cp_prev = zero, dp_prev = zero, e_last = zero;
+    N s_cur = zero;  // 2 h_k
 
-    // forward elimination step of level k; hk = u_stage_k = u_pos_k, hk1 = u_stage_{k+1}
+    // forward elimination step of level k; hk = h_k, hk1 = h_{k+1}
     auto vstep = [&](int k, bool has_next, T hk, T hk1, T utk, T utsk, T wk1, T w1k1) {
-        N a_next = zero, as_next = zero, dpl = zero;
+        if (k == 0) s_cur = add2<N, T>(hk, hk);
+        N a_next = zero, g_next = zero, s_next = zero, dpl = zero;
         if (has_next) {
             N sface;
             if (lit) {
@@ -352,14 +337,18 @@ __global__ void __launch_bounds__(TI * TJ + 32 * PW)
                 sface = add2<N, T>(wk1, hi);
             }
             a_next = coef<N>(sface, ka, kexp);
-            as_next = g.sym ? a_next : kas * sface;
-            dpl = add2<N, T>(hk1, -hk);  // u_stage_{k+1} - u_stage_k
+            s_next = add2<N, T>(hk1, hk1);
+            if (!SYM) {
+                g_next = kg * sface;
+                dpl = add2<N, T>(hk1, -hk);  // h_{k+1} - h_k
+            }
         }
         const N b = (dtr - a_cur) + a_next;
-        N d = addx<N, T>(mulx<N, T>(dtr, hk), utk);
-        d = addx<N, T>(d, utsk);
-        if (k > 0) d = d - as_cur * dm;
-        if (has_next) d = d + as_next * dpl;
+        N d = addx<N, T>(addx<N, T>(dtr * s_cur, utk), utsk);
+        if (!SYM) {
+            if (k > 0) d = d + g_cur * dpl_prev;
+            if (has_next) d = d + g_next * dpl;
+        }
         N p = b, num = d;
         if (k > 0) {
             p = b - a_cur * cp_prev;
@@ -367,8 +356,7 @@ __global__ void __launch_bounds__(TI * TJ + 32 * PW)
         }
         const N r = recip(p);
         const N cpk = (-a_next) * r, dpk = num * r;
-        N e = addx<N, T>(dpk, -hk);
-        if (has_next) e = e - mulx<N, T>(cpk, hk1);
+        const N e = (dpk - s_cur) - cpk * s_next;  // s_K = 0 (c'_{K-1} = 0)
         if (active) {
             cpb[(size_t)k * cstride + cidx] = cpk;
             if (rsave) rsave[(size_t)k * cstride + cidx] = r;
@@ -376,8 +364,9 @@ __global__ void __launch_bounds__(TI * TJ + 32 * PW)
             else epb[(size_t)k * cstride + cidx] = e;
         }
         cp_prev = cpk, dp_prev = dpk, e_last = e;
-        dm = -dpl;
-        a_cur = a_next, as_cur = as_next;
+        s_cur = s_next;
+        if (!SYM) dpl_prev = dpl, g_cur = g_next;
+        a_cur = a_next;
     };
 
     // utens, utens_stage of level m-1 and wcon of level m, loaded one iteration ahead
@@ -433,6 +422,49 @@ __global__ void __launch_bounds__(TI * TJ + 32 * PW)
             }
         }
     }
+}
+
+// hdiff -> vadv of one tile: PW producer warps compute h level by level into a
+// shared ring, the consumer warps (fused_consumer) solve the columns from it.
+template <typename T, typename N, int TI, int TJ, int PW, int STAGES, int RING, bool USE_TMA, bool DPG>
+__global__ void __launch_bounds__(TI * TJ + 32 * PW)
+    hdiff_vadv_kernel(const __grid_constant__ CUtensorMap tmap, const View<const T> in, const View<const T> coeff,
+                      const View<const T> wc, const View<const T> ut, const View<const T> uts, const View<T> out,
+                      const HdiffGeom hg, const VadvGeom g, N *__restrict__ ws, N *__restrict__ rsave,
+                      N *__restrict__ ework) {
+    using Lay = FusedLayout<T, TI, TJ, PW, STAGES, RING>;
+    using Tile = typename Lay::Tile;
+    constexpr int NC = Tile::NC, CW = Tile::CW;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    T *H = reinterpret_cast<T *>(base + Lay::h_off);  // H[slot][point]
+    uint64_t *tbar = reinterpret_cast<uint64_t *>(base + Lay::bar_off);
+    uint64_t *full = tbar + STAGES, *empty = full + RING;
+
+    const int tid = threadIdx.x, w = tid >> 5;
+    const int ti0 = blockIdx.x * TI, tj0 = blockIdx.y * TJ;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&tbar[s], 1);
+        for (int s = 0; s < RING; ++s) mbar_init(&full[s], PW), mbar_init(&empty[s], CW);
+        fence_mbar_init();
+    }
+    __syncthreads();  // the only block-wide barrier
+
+    if (w >= CW) {
+        hdiff_producer<T, TI, TJ, PW, STAGES, USE_TMA>(&tmap, in, coeff, hg, ti0, tj0, base, Lay::x_off, Lay::l_off,
+                                                       Lay::e_off, tbar, RingEmit<T>{H, full, empty, NC, RING});
+        return;
+    }
+
+    // ==================================================================== consumer warps
+    if (g.sym)
+        fused_consumer<T, N, TI, TJ, RING, DPG, true>(wc, ut, uts, out, g, ws, rsave, ework, H, full, empty, NC, ti0,
+                                                      tj0, tid);
+    else
+        fused_consumer<T, N, TI, TJ, RING, DPG, false>(wc, ut, uts, out, g, ws, rsave, ework, H, full, empty, NC, ti0,
+                                                       tj0, tid);
 }
 
 // One step of the benchmark's two stencils on their own fields, co-scheduled:

@@ -193,6 +193,7 @@ static VadvGeom make_vadv_geom(const int64_t dom[3], bool literal, double dtr_st
     g.dtr = dtr_stage;
     g.ka = (literal ? -0.5 : -0.25) * bp;
     g.kas = (literal ? -0.5 : -0.25) * bm;
+    g.kg = g.kas - g.ka;
     int n = 0;
     const double m = std::frexp(-g.ka, &n);  // -ka = m 2^n, m in [0.5, 1)
     g.ka_pow2 = (m == 0.5 && n - 1 < 0 && n - 1 > -64) ? n - 1 : 0;

@@ -115,6 +115,14 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
 }
 
 // ---------------------------------------------------------------- reciprocal
+// a * b in binary64 (round to nearest) that stays inside its branch: volatile, so
+// the compiler does not hoist it onto the FP64 pipe ahead of a rarely taken test.
+__device__ __forceinline__ double mul_fp64(double a, double b) {
+    double r;
+    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+    return r;
+}
+
 // 1/p in binary64: hardware seed (rcp.approx.ftz.f64) refined by one cubic
 // Newton-Raphson step y <- y (1 + e + e^2), e = 1 - p y (the residual computed
 // with one FMA, as in Markstein's division algorithms).  A seed accurate to

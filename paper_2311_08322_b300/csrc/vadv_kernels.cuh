@@ -5,9 +5,10 @@
 // the specialised intervals).
 //
 // Mapping: one thread per column, 32 consecutive i per warp (coalesced loads
-// of every level), K streamed, inputs loaded one level ahead.  The forward sweep keeps the eliminated
-// coefficients c'_k and d'_k of its column in shared memory ([k][thread]
-// layout, conflict-free); the backward sweep reads them back.  wcon(i+1) comes
+// of every level), K streamed, inputs loaded one level ahead.  The forward sweep
+// keeps the eliminated coefficient c'_k and the back-substitution term e_k of
+// its column (vadv_columns_t) in shared memory ([k][thread] layout,
+// conflict-free) or a workspace; the backward sweep reads them back.  wcon(i+1) comes
 // from the neighbouring lane by a warp shuffle, the last lane loading its own.
 //
 // T is the storage type, N the arithmetic type (double, float, or df =
@@ -28,6 +29,7 @@ struct VadvGeom {
     double dtr;   // dtr_stage
     double ka;    // a_k  = ka  * s_k  (s_k = wcon(i)+wcon(i+1), or wcon(i) when literal)
     double kas;   // as_k = kas * s_k;  c_{k-1} = -a_k, cs_{k-1} = -as_k
+    double kg;    // kas - ka: the explicit-minus-implicit weight, zero when sym
     int ka_pow2;  // n < 0 when ka = -2^n exactly (a_k is then an exponent shift), else 0
 };
 
@@ -64,8 +66,8 @@ template <> __device__ __forceinline__ df add2<df, float>(float a, float b) { re
 // Inputs of one level k for this lane's column (loaded one level ahead of their use).
 template <typename T>
 struct Level {
-    T up, ut, uts, us1, w;  // u_pos_k, utens_k, utens_stage_k, u_stage_{k+1}, wcon_{k+1}(i)
-    T w1;                   // wcon_{k+1}(i+1) (last lane only; others take it by shuffle)
+    T ut, uts, us1, up1, w;  // utens_k, utens_stage_k, u_stage_{k+1}, u_pos_{k+1}, wcon_{k+1}(i)
+    T w1;                    // wcon_{k+1}(i+1) (last lane only; others take it by shuffle)
 };
 
 template <typename T>
@@ -73,12 +75,12 @@ __device__ __forceinline__ void load_level(Level<T> &L, int k, int K, const T *p
                                            const T *pus, const T *pw, const T *pw1, int64_t sk_up, int64_t sk_ut,
                                            int64_t sk_uts, int64_t sk_us, int64_t sk_w, bool last_lane) {
     if (k < K) {
-        L.up = pup[(int64_t)k * sk_up];
         L.ut = put[(int64_t)k * sk_ut];
         L.uts = puts[(int64_t)k * sk_uts];
     }
     if (k + 1 < K) {
         L.us1 = pus[(int64_t)(k + 1) * sk_us];
+        L.up1 = pup[(int64_t)(k + 1) * sk_up];
         L.w = pw[(int64_t)(k + 1) * sk_w];
         if (last_lane) L.w1 = pw1[(int64_t)(k + 1) * sk_w];
     }
@@ -86,12 +88,12 @@ __device__ __forceinline__ void load_level(Level<T> &L, int k, int K, const T *p
 
 // s * 2^n (n < 0) with a sign flip, exact for normal binary64 inputs: the
 // exponent field is adjusted on the integer pipe; inputs that would leave the
-// normal range take the FP64 multiply.
+// normal range take the FP64 multiply (mul_fp64: kept inside its branch).
 __device__ __forceinline__ double scale_pow2(double s, double k, int n) {
     const int hi = __double2hiint(s), lo = __double2loint(s);
     const int e = (hi >> 20) & 0x7FF;
     if (e + n >= 1 && e < 2047) return __hiloint2double((hi + (n << 20)) ^ 0x80000000, lo);
-    return k * s;
+    return mul_fp64(k, s);
 }
 
 template <typename N>
@@ -100,7 +102,7 @@ __device__ __forceinline__ N coef(N s, N k, int n) {
 }
 template <>
 __device__ __forceinline__ double coef<double>(double s, double k, int n) {
-    return n ? scale_pow2(s, k, n) : k * s;
+    return n ? scale_pow2(s, k, n) : mul_fp64(k, s);
 }
 // double-float: k = -2^n is exact in binary32, so scaling both parts is exact
 template <>
@@ -121,13 +123,16 @@ __device__ __forceinline__ df coef<df>(df s, df k, int n) {
 // The caller passes the base, the stride between levels and this thread's
 // column index; `wr` says whether this thread may write its slot (inactive
 // threads alias a real column in a domain-indexed workspace).
-// DPG: d'_k is parked in the output array (same element size as N) and read
+// DPG: e_k is parked in the output array (same element size as N) and read
 // back by the backward sweep from L2.
-template <typename T, typename N, int BJ, bool DPG>
-__device__ __forceinline__ void vadv_columns(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
-                                             const View<const T> &ut, const View<const T> &uts, const View<T> &out,
-                                             const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
-                                             size_t cidx_ws, bool ws_domain, int tx, int ty) {
+// SYM (beta_v = 0): the explicit weights equal the implicit ones and the explicit
+// terms vanish into the matrix (below); a separate body, so that no FP64 instruction
+// of the general case is issued, even predicated off (the FP64 pipe is the bound).
+template <typename T, typename N, int BJ, bool DPG, bool SYM>
+__device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
+                                               const View<const T> &ut, const View<const T> &uts, const View<T> &out,
+                                               const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
+                                               size_t cidx_ws, bool ws_domain, int tx, int ty) {
     const int i = bx * 32 + tx, j = by * BJ + ty;
     const bool active = (i < g.I) && (j < g.J);
     const int ic = min(i, g.I - 1), jc = min(j, g.J - 1);
@@ -150,10 +155,19 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
 
     const N dtr = num_const<N>(g.dtr);
     const N ka = num_const<N>(g.ka);
-    const N kas = num_const<N>(g.kas);
+    const N kg = num_const<N>(g.kg);
     const N zero = num_const<N>(0.0);
     const int kexp = g.ka_pow2;  // a = ka * s as an exact exponent shift when ka = -2^kexp
 
+    // The system of Sec. 3.1, A x = d, with d_k = dtr u_pos_k + utens_k + utens_stage_k
+    // + E_k and the explicit terms E_k = -as_k (us_{k-1} - us_k) + as_{k+1} (us_{k+1} - us_k),
+    // solved in the shifted unknown y = x + u_stage (us).  Since
+    //   dtr us_k - (A us)_k = -a_k (us_{k-1} - us_k) + a_{k+1} (us_{k+1} - us_k),
+    // A y = dtr s_k + utens_k + utens_stage_k - g_k (us_{k-1} - us_k) + g_{k+1} (us_{k+1} - us_k)
+    // with s = u_stage + u_pos and g = as - a (zero when beta_v = 0: the explicit terms then
+    // vanish into the matrix).  The back substitution runs in z = x - u_pos = y - s, the
+    // output over dtr:  z_k = e_k - c'_k z_{k+1},  e_k = d'_k - s_k - c'_k s_{k+1}.
+    // Exact algebra; u_pos is not read again by the backward sweep.
 #define GTB_LOAD(L, k) load_level<T>(L, k, K, pup, put, puts, pus, pw, pw1, up.sk, ut.sk, uts.sk, us.sk, wc.sk, last_lane)
     // level k's inputs in L0; level k+1's are loaded at the top of iteration k (one
     // level ahead: on B300 a deeper prefetch only costs registers, i.e. resident warps)
@@ -161,37 +175,42 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
     GTB_LOAD(L0, 0);
 
     T us_cur = pus[0];
-    N dm = zero;                    // u_stage_{k-1} - u_stage_k
-    N a_cur = zero, as_cur = zero;  // a_0 = as_0 = 0
-    N cp_prev = zero, dp_prev = zero;
+    N s_cur = add2<N, T>(us_cur, pup[0]);  // s_0
+    N dpl_prev = zero;                     // u_stage_k - u_stage_{k-1} (general case only)
+    N a_cur = zero, g_cur = zero;          // a_0 = g_0 = 0
+    N cp_prev = zero, dp_prev = zero, e_last = zero;
 
     // double-float: two levels per iteration let the compiler interleave one level's
-    // FP32-pipe assembly with the previous level's recurrence (6% faster, same
-    // results); binary64 gains nothing from it (its pipe is saturated)
+    // FP32-pipe assembly with the previous level's recurrence (same results); binary64
+    // gains nothing from it (its pipe is saturated)
 #pragma unroll(std::is_same<N, df>::value ? 2 : 1)
     for (int k = 0; k < K; ++k) {
         GTB_LOAD(L1, k + 1);
         const bool has_next = (k + 1 < K);
-        N a_next = zero, as_next = zero, dpl = zero;
+        N a_next = zero, g_next = zero, s_next = zero, dpl = zero;
         if (has_next) {
-            N s;
+            N sf;
             if (lit) {
-                s = to_num<N, T>(L0.w);
+                sf = to_num<N, T>(L0.w);
             } else {
                 T hi = __shfl_down_sync(0xffffffffu, L0.w, 1);
                 if (last_lane) hi = L0.w1;
-                s = add2<N, T>(L0.w, hi);
+                sf = add2<N, T>(L0.w, hi);
             }
-            a_next = coef<N>(s, ka, kexp);
-            as_next = g.sym ? a_next : kas * s;
-            dpl = add2<N, T>(L0.us1, -us_cur);  // u_stage_{k+1} - u_stage_k
-            us_cur = L0.us1;
+            a_next = coef<N>(sf, ka, kexp);
+            s_next = add2<N, T>(L0.us1, L0.up1);
+            if (!SYM) {
+                g_next = kg * sf;
+                dpl = add2<N, T>(L0.us1, -us_cur);  // u_stage_{k+1} - u_stage_k
+                us_cur = L0.us1;
+            }
         }
         const N b = (dtr - a_cur) + a_next;  // dtr - a_k - c_k with c_k = -a_{k+1}
-        N d = addx<N, T>(mulx<N, T>(dtr, L0.up), L0.ut);
-        d = addx<N, T>(d, L0.uts);
-        if (k > 0) d = d - as_cur * dm;
-        if (has_next) d = d + as_next * dpl;  // - cs_k (u_{k+1} - u_k), cs_k = -as_{k+1}
+        N d = addx<N, T>(addx<N, T>(dtr * s_cur, L0.ut), L0.uts);
+        if (!SYM) {  // + g_k (us_k - us_{k-1}) + g_{k+1} (us_{k+1} - us_k)
+            if (k > 0) d = d + g_cur * dpl_prev;
+            if (has_next) d = d + g_next * dpl;
+        }
         N p = b, num = d;
         if (k > 0) {
             p = b - a_cur * cp_prev;
@@ -199,54 +218,65 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
         }
         const N r = recip(p);
         const N cpk = (-a_next) * r, dpk = num * r;
+        const N ek = (dpk - s_cur) - cpk * s_next;  // s_K = 0 (c'_{K-1} = 0)
         if (wr) cpb[(size_t)k * cstride + cidx] = cpk;
         if (DPG) {
-            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(dpk);
+            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(ek);
         } else if (wr) {
-            dpb[(size_t)k * cstride + cidx] = dpk;
+            dpb[(size_t)k * cstride + cidx] = ek;
         }
-        cp_prev = cpk, dp_prev = dpk;
-        dm = -dpl;
-        a_cur = a_next, as_cur = as_next;
+        cp_prev = cpk, dp_prev = dpk, e_last = ek;
+        s_cur = s_next;
+        if (!SYM) dpl_prev = dpl, g_cur = g_next;
+        a_cur = a_next;
         L0 = L1;
     }
 #undef GTB_LOAD
 
-    // backward substitution and output, utens_stage_out = dtr (x - u_pos).  Levels go in
-    // groups of BG; a group's inputs (d'_k, c'_k, u_pos_k) are loaded before the previous
-    // group's outputs are stored (distinct levels, so distinct addresses: the out stride in
-    // k is nonzero), so the loads overlap instead of each waiting behind a store.
-    N x = dp_prev;
-    if (active) po[(int64_t)(K - 1) * out.sk] = to_store<T, N>(dtr * addx<N, T>(x, -pup[(int64_t)(K - 1) * up.sk]));
+    // backward substitution, utens_stage_out = dtr z.  Levels go in groups of BG; a
+    // group's inputs (e_k, c'_k) are loaded before the previous group's outputs are
+    // stored (distinct levels, so distinct addresses: the out stride in k is nonzero),
+    // so the loads overlap instead of each waiting behind a store.
+    N z = e_last;  // z_{K-1} = e_{K-1}
+    if (active) po[(int64_t)(K - 1) * out.sk] = to_store<T, N>(dtr * z);
     constexpr int BG = 4;
-    N dq[BG], cq[BG];
-    T uq[BG];
+    N eq[BG], cq[BG];
     auto load_group = [&](int k0) {
 #pragma unroll
         for (int q = 0; q < BG; ++q) {
             const int k = k0 - q;
             if (k < 0) break;
-            dq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : dpb[(size_t)k * cstride + cidx];
+            eq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : dpb[(size_t)k * cstride + cidx];
             cq[q] = cpb[(size_t)k * cstride + cidx];
-            uq[q] = pup[(int64_t)k * up.sk];
         }
     };
     if (K >= 2) load_group(K - 2);
     for (int k0 = K - 2; k0 >= 0; k0 -= BG) {
-        N dc[BG], cc[BG];
-        T uc[BG];
+        N ec[BG], cc[BG];
 #pragma unroll
-        for (int q = 0; q < BG; ++q) dc[q] = dq[q], cc[q] = cq[q], uc[q] = uq[q];
+        for (int q = 0; q < BG; ++q) ec[q] = eq[q], cc[q] = cq[q];
         if (k0 - BG >= 0) load_group(k0 - BG);
 #pragma unroll
         for (int q = 0; q < BG; ++q) {
             const int k = k0 - q;
             if (k < 0) break;
-            x = dc[q] - cc[q] * x;
-            const N o = dtr * addx<N, T>(x, -uc[q]);
-            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(o);
+            z = ec[q] - cc[q] * z;
+            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(dtr * z);
         }
     }
+}
+
+template <typename T, typename N, int BJ, bool DPG>
+__device__ __forceinline__ void vadv_columns(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
+                                             const View<const T> &ut, const View<const T> &uts, const View<T> &out,
+                                             const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
+                                             size_t cidx_ws, bool ws_domain, int tx, int ty) {
+    if (g.sym)
+        vadv_columns_t<T, N, BJ, DPG, true>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws, ws_domain,
+                                            tx, ty);
+    else
+        vadv_columns_t<T, N, BJ, DPG, false>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws, ws_domain,
+                                             tx, ty);
 }
 
 // Single domain: one CTA per 32 x BJ block of columns; WS selects a
