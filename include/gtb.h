@@ -123,7 +123,7 @@ int gtb_hdiff(const gtb_field *in, const gtb_field *coeff, const gtb_field *out,
  * workspace of gtb_vadv_workspace_bytes() bytes is passed.
  *
  * workspace: optional caller-owned device scratch for the forward sweep's
- * eliminated coefficients (c', and d' when it cannot be parked in the output),
+ * column state (c'_k, and s_k = u_stage_k + u_pos_k or a back-substitution term),
  * at least gtb_vadv_workspace_bytes() bytes, 16-byte aligned, overlapping no
  * field; its contents on entry are ignored and on exit unspecified, and two
  * calls that may run concurrently need distinct workspaces.  With it the
@@ -138,8 +138,9 @@ int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u
              void *workspace, size_t workspace_bytes, void *stream);
 
 /* Bytes of workspace gtb_vadv uses for this dtype, prec and domain (I,J,K):
- * K*I*J*8 for GTB_F64 storage, K*I*J*4 for GTB_F32 with GTB_PREC_NATIVE,
- * K*I*J*16 for GTB_F32 with GTB_PREC_F64 or GTB_PREC_DF; 0 for bad arguments. */
+ * two values per point in the arithmetic type, K*I*J*16 for GTB_F64 storage,
+ * K*I*J*8 for GTB_F32 with GTB_PREC_NATIVE, K*I*J*16 for GTB_F32 with
+ * GTB_PREC_F64 or GTB_PREC_DF; 0 for bad arguments. */
 size_t gtb_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain);
 
 /*
@@ -312,7 +313,7 @@ int gtb_plan_destroy(gtb_plan *plan);
  * array, held on every GPU that loads the library until the process exits).
  * Same arguments, results and errors as gtb_vadv, plus:
  *  - a domain whose workspace (gtb_vadv_workspace_bytes) exceeds 16 MiB
- *    (2,097,152 points for GTB_F64 storage) is rejected with
+ *    (1,048,576 points for GTB_F64 storage) is rejected with
  *    GTB_ERR_UNSUPPORTED and nothing is enqueued;
  *  - the first call on a device looks up the array's device address on that
  *    device (make it before any stream capture);

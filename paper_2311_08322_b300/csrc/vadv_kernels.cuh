@@ -123,16 +123,22 @@ __device__ __forceinline__ df coef<df>(df s, df k, int n) {
 // The caller passes the base, the stride between levels and this thread's
 // column index; `wr` says whether this thread may write its slot (inactive
 // threads alias a real column in a domain-indexed workspace).
-// DPG: e_k is parked in the output array (same element size as N) and read
-// back by the backward sweep from L2.
+// DPG: a term of the backward sweep is parked in the output array (same element
+// size as N) and read back by the backward sweep from L2.
+// YF (global state and DPG only): the backward sweep runs on y itself,
+// y_k = d'_k - c'_k y_{k+1}, out_k = dtr (y_k - s_k), with d'_k parked in the
+// output and s_k kept in the second state array: one FP64 operation per point
+// fewer than the e_k form below, for one more array of state.  The shared-memory
+// form keeps e_k (one slot per column and level fewer, twice the resident CTAs).
 // SYM (beta_v = 0): the explicit weights equal the implicit ones and the explicit
 // terms vanish into the matrix (below); a separate body, so that no FP64 instruction
 // of the general case is issued, even predicated off (the FP64 pipe is the bound).
-template <typename T, typename N, int BJ, bool DPG, bool SYM>
+template <typename T, typename N, int BJ, bool DPG, bool YF, bool SYM>
 __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                                const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                                const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
                                                size_t cidx_ws, bool ws_domain, int tx, int ty) {
+    static_assert(!YF || DPG, "the y form parks d'_k in the output");
     const int i = bx * 32 + tx, j = by * BJ + ty;
     const bool active = (i < g.I) && (j < g.J);
     const int ic = min(i, g.I - 1), jc = min(j, g.J - 1);
@@ -165,9 +171,10 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     //   dtr us_k - (A us)_k = -a_k (us_{k-1} - us_k) + a_{k+1} (us_{k+1} - us_k),
     // A y = dtr s_k + utens_k + utens_stage_k - g_k (us_{k-1} - us_k) + g_{k+1} (us_{k+1} - us_k)
     // with s = u_stage + u_pos and g = as - a (zero when beta_v = 0: the explicit terms then
-    // vanish into the matrix).  The back substitution runs in z = x - u_pos = y - s, the
-    // output over dtr:  z_k = e_k - c'_k z_{k+1},  e_k = d'_k - s_k - c'_k s_{k+1}.
-    // Exact algebra; u_pos is not read again by the backward sweep.
+    // vanish into the matrix).  The output is dtr (x - u_pos) = dtr (y - s): YF back-
+    // substitutes y and keeps s; otherwise the back substitution runs in z = x - u_pos =
+    // y - s, z_k = e_k - c'_k z_{k+1}, e_k = d'_k - s_k - c'_k s_{k+1}.  Exact algebra;
+    // u_pos is not read again by the backward sweep.
 #define GTB_LOAD(L, k) load_level<T>(L, k, K, pup, put, puts, pus, pw, pw1, up.sk, ut.sk, uts.sk, us.sk, wc.sk, last_lane)
     // level k's inputs in L0; level k+1's are loaded at the top of iteration k (one
     // level ahead: on B300 a deeper prefetch only costs registers, i.e. resident warps)
@@ -218,12 +225,19 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
         }
         const N r = recip(p);
         const N cpk = (-a_next) * r, dpk = num * r;
-        const N ek = (dpk - s_cur) - cpk * s_next;  // s_K = 0 (c'_{K-1} = 0)
         if (wr) cpb[(size_t)k * cstride + cidx] = cpk;
-        if (DPG) {
-            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(ek);
-        } else if (wr) {
-            dpb[(size_t)k * cstride + cidx] = ek;
+        N ek;  // the backward sweep's term of level k: d'_k (YF) or e_k
+        if constexpr (YF) {
+            ek = dpk;
+            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(dpk);
+            if (wr) dpb[(size_t)k * cstride + cidx] = s_cur;
+        } else {
+            ek = (dpk - s_cur) - cpk * s_next;  // s_K = 0 (c'_{K-1} = 0)
+            if (DPG) {
+                if (active) po[(int64_t)k * out.sk] = to_store<T, N>(ek);
+            } else if (wr) {
+                dpb[(size_t)k * cstride + cidx] = ek;
+            }
         }
         cp_prev = cpk, dp_prev = dpk, e_last = ek;
         s_cur = s_next;
@@ -233,14 +247,21 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     }
 #undef GTB_LOAD
 
-    // backward substitution, utens_stage_out = dtr z.  Levels go in groups of BG; a
-    // group's inputs (e_k, c'_k) are loaded before the previous group's outputs are
-    // stored (distinct levels, so distinct addresses: the out stride in k is nonzero),
-    // so the loads overlap instead of each waiting behind a store.
-    N z = e_last;  // z_{K-1} = e_{K-1}
-    if (active) po[(int64_t)(K - 1) * out.sk] = to_store<T, N>(dtr * z);
+    // backward substitution, utens_stage_out = dtr (y - s) (YF) or dtr z.  Levels go in
+    // groups of BG; a group's inputs (d'_k or e_k, c'_k, s_k) are loaded before the
+    // previous group's outputs are stored (distinct levels, so distinct addresses: the
+    // out stride in k is nonzero), so the loads overlap instead of each waiting behind a
+    // store.
+    auto result = [&](N v, N sk) -> N {
+        if constexpr (YF) return dtr * (v - sk);
+        else return dtr * v;
+    };
+    N z = e_last;  // y_{K-1} = d'_{K-1} (YF) or z_{K-1} = e_{K-1}
+    if (active)
+        po[(int64_t)(K - 1) * out.sk] =
+            to_store<T, N>(result(z, YF ? dpb[(size_t)(K - 1) * cstride + cidx] : zero));
     constexpr int BG = 4;
-    N eq[BG], cq[BG];
+    N eq[BG], cq[BG], sq[BG];
     auto load_group = [&](int k0) {
 #pragma unroll
         for (int q = 0; q < BG; ++q) {
@@ -248,35 +269,36 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
             if (k < 0) break;
             eq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : dpb[(size_t)k * cstride + cidx];
             cq[q] = cpb[(size_t)k * cstride + cidx];
+            sq[q] = YF ? dpb[(size_t)k * cstride + cidx] : zero;
         }
     };
     if (K >= 2) load_group(K - 2);
     for (int k0 = K - 2; k0 >= 0; k0 -= BG) {
-        N ec[BG], cc[BG];
+        N ec[BG], cc[BG], sc[BG];
 #pragma unroll
-        for (int q = 0; q < BG; ++q) ec[q] = eq[q], cc[q] = cq[q];
+        for (int q = 0; q < BG; ++q) ec[q] = eq[q], cc[q] = cq[q], sc[q] = sq[q];
         if (k0 - BG >= 0) load_group(k0 - BG);
 #pragma unroll
         for (int q = 0; q < BG; ++q) {
             const int k = k0 - q;
             if (k < 0) break;
             z = ec[q] - cc[q] * z;
-            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(dtr * z);
+            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(result(z, sc[q]));
         }
     }
 }
 
-template <typename T, typename N, int BJ, bool DPG>
+template <typename T, typename N, int BJ, bool DPG, bool YF>
 __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                              const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                              const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
                                              size_t cidx_ws, bool ws_domain, int tx, int ty) {
     if (g.sym)
-        vadv_columns_t<T, N, BJ, DPG, true>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws, ws_domain,
-                                            tx, ty);
+        vadv_columns_t<T, N, BJ, DPG, YF, true>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
+                                                ws_domain, tx, ty);
     else
-        vadv_columns_t<T, N, BJ, DPG, false>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws, ws_domain,
-                                             tx, ty);
+        vadv_columns_t<T, N, BJ, DPG, YF, false>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
+                                                 ws_domain, tx, ty);
 }
 
 // Single domain: one CTA per 32 x BJ block of columns; WS selects a
@@ -290,12 +312,12 @@ __global__ void __launch_bounds__(32 * BJ)
     const int t = threadIdx.y * 32 + threadIdx.x;
     if (WS) {
         const size_t cstride = (size_t)g.I * g.J;
-        vadv_columns<T, N, BJ, DPG>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws, ws + (size_t)g.K * cstride,
-                                    cstride, 0, true, threadIdx.x, threadIdx.y);
+        vadv_columns<T, N, BJ, DPG, DPG>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
+                                         ws + (size_t)g.K * cstride, cstride, 0, true, threadIdx.x, threadIdx.y);
     } else {
         N *cpb = reinterpret_cast<N *>(smem_raw);
-        vadv_columns<T, N, BJ, DPG>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, cpb, cpb + (size_t)g.K * NT,
-                                    NT, t, false, threadIdx.x, threadIdx.y);
+        vadv_columns<T, N, BJ, DPG, false>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, cpb,
+                                           cpb + (size_t)g.K * NT, NT, t, false, threadIdx.x, threadIdx.y);
     }
 }
 

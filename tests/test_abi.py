@@ -110,11 +110,11 @@ def test_vadv_validation(L):
 
 
 def test_vadv_workspace_bytes(L):
-    """c' (and d' when it cannot be parked in the output) per domain point."""
+    """Two values of the arithmetic type per domain point (c'_k, and s_k or e_k)."""
     dom = (10, 7, 5)
     n = 10 * 7 * 5
-    assert L.vadv_workspace_bytes(2, 0, dom) == 8 * n
-    assert L.vadv_workspace_bytes(1, 0, dom) == 4 * n
+    assert L.vadv_workspace_bytes(2, 0, dom) == 16 * n
+    assert L.vadv_workspace_bytes(1, 0, dom) == 8 * n
     assert L.vadv_workspace_bytes(1, 1, dom) == 16 * n
     assert L.vadv_workspace_bytes(1, 2, dom) == 16 * n
     assert L.vadv_workspace_bytes(3, 0, dom) == 0

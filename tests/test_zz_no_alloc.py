@@ -52,7 +52,9 @@ def call_noalloc(G, st, out, prec=0, domain=None):
                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-@pytest.mark.parametrize("dtype,prec,shape", [(np.float64, "native", (128, 128, 64)),
+# the deduced domain reaches one row into the halo (J + 1); 128 x 113 x 64 binary64 needs
+# 14.8 MB of the 16 MiB array (two values per point)
+@pytest.mark.parametrize("dtype,prec,shape", [(np.float64, "native", (128, 112, 64)),
                                               (np.float32, "df", (100, 70, 80))])
 def test_matches_workspace_entry_point_twice(G, dtype, prec, shape):
     I, J, K = shape
@@ -75,7 +77,7 @@ def test_matches_workspace_entry_point_twice(G, dtype, prec, shape):
 def test_rejects_domains_beyond_the_fixed_array(G):
     st = fields(G, 8, 4, 3, 13)
     out = G.storage_from(np.zeros(st["utens"].shape), (1, 1, 0))
-    # 256 x 256 x 80 binary64 needs 40 MiB of scratch; only the domain is checked
+    # 256 x 256 x 80 binary64 needs 80 MiB of scratch; only the domain is checked
     rc = call_noalloc(G, st, out, domain=(256, 256, 80))
     assert rc == -8
     assert "16777216" in G.lib().gtb_last_error().decode()
