@@ -138,9 +138,8 @@ int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const gtb_field *u
              void *workspace, size_t workspace_bytes, void *stream);
 
 /* Bytes of workspace gtb_vadv uses for this dtype, prec and domain (I,J,K):
- * two values per point in the arithmetic type, K*I*J*16 for GTB_F64 storage,
- * K*I*J*8 for GTB_F32 with GTB_PREC_NATIVE, K*I*J*16 for GTB_F32 with
- * GTB_PREC_F64 or GTB_PREC_DF; 0 for bad arguments. */
+ * K*I*J*16 for GTB_F64 storage, K*I*J*4 for GTB_F32 with GTB_PREC_NATIVE,
+ * K*I*J*16 for GTB_F32 with GTB_PREC_F64 or GTB_PREC_DF; 0 for bad arguments. */
 size_t gtb_vadv_workspace_bytes(int dtype, int prec, const int64_t *domain);
 
 /*

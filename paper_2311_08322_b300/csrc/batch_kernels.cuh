@@ -88,8 +88,9 @@ __global__ void __launch_bounds__(32 * BJ)
         const int m = member_of(mem, n_mem, item);
         const BatchVadvMember<T> M = mem[m];
         const int local = item - M.item0;
-        vadv_columns<T, N, BJ, DPG, DPG>(M.us, M.wc, M.up, M.ut, M.uts, M.out, M.g, local % M.blocks_x,
-                                         local / M.blocks_x, cpb, dpb, NT, t, false, threadIdx.x, threadIdx.y);
+        vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>()>(M.us, M.wc, M.up, M.ut, M.uts, M.out, M.g,
+                                                        local % M.blocks_x, local / M.blocks_x, cpb, dpb, NT, t,
+                                                        false, threadIdx.x, threadIdx.y);
     }
 }
 

@@ -500,8 +500,8 @@ __global__ void __launch_bounds__(32 * (BJ + PW), 7 * 4 / (BJ + PW))
         return;
     }
     const size_t cstride = (size_t)g.I * g.J;
-    vadv_columns<T, N, BJ, DPG, DPG>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
-                                     ws + (size_t)g.K * cstride, cstride, 0, true, tid & 31, w);
+    vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>()>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
+                                                    ws + (size_t)g.K * cstride, cstride, 0, true, tid & 31, w);
 }
 
 }  // namespace gtb

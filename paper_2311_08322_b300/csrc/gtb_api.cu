@@ -313,10 +313,9 @@ static int launch_vadv_t(const gtb_field *const f[6], const VadvGeom &g, void *w
     return launch_status("vadv launch");
 }
 
-// Two arrays of column state: c'_k, then s_k (d'_k parked in the output) or e_k.
 template <typename T, typename N>
 static size_t vadv_ws_bytes(const int64_t dom[3]) {
-    return (size_t)2 * sizeof(N) * (size_t)dom[0] * (size_t)dom[1] * (size_t)dom[2];
+    return (size_t)vadv_state_arrays<T, N>() * sizeof(N) * (size_t)dom[0] * (size_t)dom[1] * (size_t)dom[2];
 }
 
 // With a large enough workspace: column state in global memory (L2), two warps
@@ -1097,7 +1096,7 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
     P->h_grid = std::max(1, std::min(hitems, hslots));
     P->v_grid = std::max(1, std::min(vitems, vslots));
     P->points = pts;
-    const size_t slice = (size_t)2 * k_max * 32 * BJ;  // c'_k, then s_k or e_k
+    const size_t slice = (size_t)vadv_state_arrays<T, N>() * k_max * 32 * BJ;
     cudaError_t e;
     if ((e = cudaMalloc(&P->d_maps, sizeof(CUtensorMap) * n)) || (e = cudaMalloc(&P->d_hmem, sizeof(BatchHdiffMember<T>) * n)) ||
         (e = cudaMalloc(&P->d_vmem, sizeof(BatchVadvMember<T>) * n)) || (e = cudaMalloc(&P->d_counters, 2 * sizeof(int))) ||

@@ -110,6 +110,32 @@ __device__ __forceinline__ df coef<df>(df s, df k, int n) {
     return n ? df{__fmul_rn(s.hi, k.hi), __fmul_rn(s.lo, k.hi)} : k * s;
 }
 
+template <typename T, typename N>
+__host__ __device__ constexpr bool vadv_dp_global() {
+    return sizeof(T) == sizeof(N);
+}
+
+// The y back substitution (one FP64 operation per point fewer, one more array of
+// state) where the column state is in global memory: binary64 arithmetic only,
+// whose pipe bounds the solve.  In binary32 it is slower (memory-bound there) and
+// the y - s cancellation costs accuracy.
+template <typename T, typename N>
+__host__ __device__ constexpr bool vadv_yform() {
+    return vadv_dp_global<T, N>() && std::is_same<N, double>::value;
+}
+
+// Arrays of column state per point: c'_k, and s_k (y form) or e_k when it cannot
+// be parked in the output.
+template <typename T, typename N>
+__host__ __device__ constexpr int vadv_state_arrays() {
+    return (vadv_dp_global<T, N>() && !vadv_yform<T, N>()) ? 1 : 2;
+}
+
+template <typename T, typename N>
+__host__ __device__ constexpr size_t vadv_smem_per_col_level() {
+    return (vadv_dp_global<T, N>() ? 1 : 2) * sizeof(N);
+}
+
 // Where the forward sweep keeps its eliminated coefficients:
 //  * shared memory, [K][block columns]: the K x 32 x BJ state caps the
 //    resident warps per SM;
@@ -125,7 +151,7 @@ __device__ __forceinline__ df coef<df>(df s, df k, int n) {
 // threads alias a real column in a domain-indexed workspace).
 // DPG: a term of the backward sweep is parked in the output array (same element
 // size as N) and read back by the backward sweep from L2.
-// YF (global state and DPG only): the backward sweep runs on y itself,
+// YF (global state, binary64 arithmetic, DPG): the backward sweep runs on y itself,
 // y_k = d'_k - c'_k y_{k+1}, out_k = dtr (y_k - s_k), with d'_k parked in the
 // output and s_k kept in the second state array: one FP64 operation per point
 // fewer than the e_k form below, for one more array of state.  The shared-memory
@@ -312,23 +338,14 @@ __global__ void __launch_bounds__(32 * BJ)
     const int t = threadIdx.y * 32 + threadIdx.x;
     if (WS) {
         const size_t cstride = (size_t)g.I * g.J;
-        vadv_columns<T, N, BJ, DPG, DPG>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
-                                         ws + (size_t)g.K * cstride, cstride, 0, true, threadIdx.x, threadIdx.y);
+        vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>()>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
+                                                        ws + (size_t)g.K * cstride, cstride, 0, true, threadIdx.x,
+                                                        threadIdx.y);
     } else {
         N *cpb = reinterpret_cast<N *>(smem_raw);
         vadv_columns<T, N, BJ, DPG, false>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, cpb,
                                            cpb + (size_t)g.K * NT, NT, t, false, threadIdx.x, threadIdx.y);
     }
-}
-
-template <typename T, typename N>
-__host__ __device__ constexpr bool vadv_dp_global() {
-    return sizeof(T) == sizeof(N);
-}
-
-template <typename T, typename N>
-__host__ __device__ constexpr size_t vadv_smem_per_col_level() {
-    return (vadv_dp_global<T, N>() ? 1 : 2) * sizeof(N);
 }
 
 }  // namespace gtb

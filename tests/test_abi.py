@@ -110,11 +110,12 @@ def test_vadv_validation(L):
 
 
 def test_vadv_workspace_bytes(L):
-    """Two values of the arithmetic type per domain point (c'_k, and s_k or e_k)."""
+    """c' and, unless it can be parked in the output, a second term per domain point
+    (binary64: s = u_stage + u_pos for the y back substitution)."""
     dom = (10, 7, 5)
     n = 10 * 7 * 5
     assert L.vadv_workspace_bytes(2, 0, dom) == 16 * n
-    assert L.vadv_workspace_bytes(1, 0, dom) == 8 * n
+    assert L.vadv_workspace_bytes(1, 0, dom) == 4 * n
     assert L.vadv_workspace_bytes(1, 1, dom) == 16 * n
     assert L.vadv_workspace_bytes(1, 2, dom) == 16 * n
     assert L.vadv_workspace_bytes(3, 0, dom) == 0
