@@ -261,3 +261,32 @@ def test_chain_gradient_with_and_without_factors(G):
     l2, gf2, gc2 = gpu_chain(G, field, coeff, fixed, 4)
     assert l1 == l2
     assert torch.equal(gf1, gf2) and torch.equal(gc1, gc2)
+
+
+@pytest.mark.parametrize("beta_v,literal,merge", [(0.3, False, False), (-0.2, True, False), (0.3, False, True),
+                                                  (0.0, True, False), (0.0, False, True)])
+def test_vadv_adj_weights(G, orc, beta_v, literal, merge):
+    """Both bodies of the backward sweep: beta_v = 0 (u_stage_bar = dtr (z - y_bar), no
+    wcon read) and general weights (the E^T z stencil), separate and merged cotangents,
+    against the oracle's adjoint.  A literal face velocity is wcon(i) itself, not an average
+    of two: |wcon| <= 0.25 keeps its columns as well conditioned as the averaged draws (at
+    0.5 some diagonals turn negative and the binary64 oracle itself is 8e-12 from a
+    long-double solve, so no other rounding order can meet 1e-12 against it)."""
+    I, J, K = 70, 11, 37
+    o = (1, 1, 0)
+    shp = (K, J + 2, I + 2)
+    amp = 0.25 if literal else 0.5
+    wcon, yb = rnd(shp, 21, -amp, amp), rnd(shp, 22)
+    us, up, ut, uts = orc.vadv_adj(wcon, yb, beta_v=beta_v, wmode=1 if literal else 0)
+    kw = dict(beta_v=beta_v, literal=literal)
+    if merge:
+        s = G.storage_from(np.full(shp, np.nan), o)
+        G.vadv_adj(G.storage_from(wcon, o), G.storage_from(yb, o), s, s, **kw)
+        G.device_status()
+        assert rel_err(region(s.numpy(), o, (I, J, K)), region(us + up, o, (I, J, K))) <= F64_TOL
+        return
+    outs = [G.storage_from(np.full(shp, np.nan), o) for _ in range(4)]
+    G.vadv_adj(G.storage_from(wcon, o), G.storage_from(yb, o), *outs, **kw)
+    G.device_status()
+    for name, st, r in zip(("u_stage_bar", "u_pos_bar", "utens_bar", "utens_stage_bar"), outs, (us, up, ut, uts)):
+        assert rel_err(region(st.numpy(), o, (I, J, K)), region(r, o, (I, J, K))) <= F64_TOL, name

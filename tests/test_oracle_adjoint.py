@@ -135,3 +135,23 @@ def test_hdiff_coeff_bar_exactly_linear(orc):
     lhs = np.sum(dv * w[:, 2:-2, 2:-2])
     rhs = np.sum(cb * v)
     assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1e-3)
+
+
+@pytest.mark.parametrize("wmode", [0, 1])
+def test_vadv_adjoint_stage_identity(orc, wmode):
+    """With beta_v = 0 the explicit operator is E = dtr I - A, and the adjoint solve
+    A^T z = dtr y_bar then gives u_stage_bar = E^T z = dtr (z - y_bar) = u_pos_bar, with
+    z = utens_bar: a closed form the oracle's stencil form of E^T z must reproduce (a
+    dropped or mis-signed weight breaks it), while beta_v != 0 must not."""
+    I, J, K = 11, 6, 24
+    shp = (K, J + 2, I + 2)
+    amp = 0.25 if wmode else 0.5
+    wcon, yb = rnd(shp, 31, -amp, amp), rnd(shp, 32)
+    us_b, up_b, ut_b, _ = orc.vadv_adj(wcon, yb, wmode=wmode)
+    d = (slice(None), slice(1, -1), slice(1, -1))
+    closed = DTR * (ut_b[d] - yb[d])
+    scale = np.max(np.abs(closed))
+    assert np.max(np.abs(us_b[d] - closed)) <= 1e-13 * scale
+    assert np.max(np.abs(up_b[d] - closed)) <= 1e-13 * scale
+    us_g, _, ut_g, _ = orc.vadv_adj(wcon, yb, wmode=wmode, beta_v=0.3)
+    assert np.max(np.abs(us_g[d] - DTR * (ut_g[d] - yb[d]))) > 1e-6 * scale
