@@ -28,9 +28,51 @@
 namespace gtb {
 
 // ------------------------------------------------------------------ vadv adjoint
+// One column's outputs after the adjoint solve, for beta_v = 0: E^T z = dtr (z - y_bar)
+// makes u_stage_bar equal to u_pos_bar (their sum when merged), and utens_bar =
+// utens_stage_bar = z.  The sweep runs on Z = z / dtr: Z_k = V_k + c'_k Z_{k+1}.  WANT_Z:
+// a utens or utens_stage cotangent is asked for; ACC: add to the cotangent fields.
+// Compile-time cases, so that no FP64 instruction of another case is issued.
+template <typename T, typename N, bool WANT_Z, bool ACC>
+__device__ __forceinline__ void vadv_adj_back_sym(const View<const T> &yb, const View<T> &usb, const View<T> &upb,
+                                                  const View<T> &utb, const View<T> &utsb, const N *cpb, const N *vb,
+                                                  size_t cstride, size_t cidx, const T *py, int K, int ic, int jc,
+                                                  bool active, N dtr, bool merge_us_up) {
+    auto store = [&](const View<T> &o, int k, N val) {
+        if (!o.p || !active) return;
+        T *q = o.p + ic + (int64_t)jc * o.sj + (int64_t)k * o.sk;
+        if (ACC) *q = to_store<T, N>(to_num<N, T>(*q) + val);
+        else *q = to_store<T, N>(val);
+    };
+    const N m = merge_us_up ? dtr + dtr : dtr;
+    const N zero = num_const<N>(0.0);
+    N Z1 = zero;
+    N v_n = vb[(size_t)(K - 1) * cstride + cidx], cp_n = zero;
+    T y_n = py[(int64_t)(K - 1) * yb.sk];
+    for (int k = K - 1; k >= 0; --k) {
+        const N vk = v_n, cpk = cp_n;
+        const T yk = y_n;
+        if (k > 0) {
+            v_n = vb[(size_t)(k - 1) * cstride + cidx];
+            cp_n = cpb[(size_t)(k - 1) * cstride + cidx];
+            y_n = py[(int64_t)(k - 1) * yb.sk];
+        }
+        const N Z = (k == K - 1) ? vk : vk + cpk * Z1;
+        if (WANT_Z) {
+            const N z = dtr * Z;
+            store(utb, k, z);
+            store(utsb, k, z);
+        }
+        const N u = m * addx<N, T>(dtr * Z, -yk);  // one FMA: dtr Z - y_bar
+        store(usb, k, u);
+        if (!merge_us_up) store(upb, k, u);
+        Z1 = Z;
+    }
+}
+
 // FACT: the workspace holds the forward solve's factors, c'_k then 1/p_k (kept by
 // gtb_hdiff_vadv with GTB_SAVE_FACTORS): the forward sweep reads them instead of
-// refactorising A, and v_k overwrites 1/p_k in place.
+// refactorising A, and V_k overwrites 1/p_k in place.
 template <typename T, typename N, int BJ, bool WS, bool FACT>
 __global__ void __launch_bounds__(32 * BJ)
     vadv_adj_kernel(const View<const T> wc, const View<const T> yb, const View<T> usb, const View<T> upb,
@@ -85,78 +127,79 @@ __global__ void __launch_bounds__(32 * BJ)
         if (last_lane) hi = pw1[(int64_t)m * wc.sk];
     };
 
-    // forward sweep: the pivots of A, c'_k, and v (U^T v = dtr y_bar); every input of
-    // level k+1 is loaded during level k
-    N a_cur = zero, cp_prev = zero, v_prev = zero;
-    T y_n = py[0], w_n = T(0), w1_n = T(0);
-    N r_n = zero;
-    if (K > 1) wload(1, w_n, w1_n);
-    if constexpr (FACT) r_n = vb[cidx];
-    for (int k = 0; k < K; ++k) {
-        const T yk = y_n, wk1 = w_n, w1k1 = w1_n;
-        const N rk = r_n;
-        if (k + 1 < K) {
-            y_n = py[(int64_t)(k + 1) * yb.sk];
-            if constexpr (FACT) r_n = vb[(size_t)(k + 1) * cstride + cidx];
+    // forward sweep, U^T v = dtr y_bar: (U^T v)_k = c_{k-1} v_{k-1} + p_k v_k, and with
+    // v_{k-1} = u_{k-1} / p_{k-1} and c'_{k-1} = c_{k-1} / p_{k-1},
+    //   v_k = u_k / p_k,   u_k = dtr y_bar_k - c'_{k-1} u_{k-1}:
+    // once c' is known no a_k is needed (FACT reads no wcon).  Carried in units of dtr,
+    // U = u / dtr and V = v / dtr.  Every input of level k+1 is loaded during level k.
+    N cp_prev = zero, U_prev = zero;
+    T y_n = py[0];
+    if constexpr (FACT) {
+        N r_n = vb[cidx], c_n = cpb[cidx];
+        for (int k = 0; k < K; ++k) {
+            const T yk = y_n;
+            const N rk = r_n, ck = c_n;
+            if (k + 1 < K) {
+                y_n = py[(int64_t)(k + 1) * yb.sk];
+                r_n = vb[(size_t)(k + 1) * cstride + cidx];
+                c_n = cpb[(size_t)(k + 1) * cstride + cidx];
+            }
+            const N U = (k > 0) ? addx<N, T>(-(cp_prev * U_prev), yk) : to_num<N, T>(yk);
+            if (wr) vb[(size_t)k * cstride + cidx] = U * rk;
+            cp_prev = ck, U_prev = U;
         }
-        if (k + 2 < K) wload(k + 2, w_n, w1_n);
-        N a_next = zero;
-        if (k + 1 < K) a_next = coef<N>(face_of(wk1, w1k1), ka, kexp);
-        const N x = dtr * to_num<N, T>(yk);
-        if constexpr (FACT) {
-            const N v = (k > 0) ? (x + a_cur * v_prev) * rk : x * rk;
-            if (wr) vb[(size_t)k * cstride + cidx] = v;
-            v_prev = v;
-        } else {
+    } else {
+        N a_cur = zero;
+        T w_n = T(0), w1_n = T(0);
+        if (K > 1) wload(1, w_n, w1_n);
+        for (int k = 0; k < K; ++k) {
+            const T yk = y_n, wk1 = w_n, w1k1 = w1_n;
+            if (k + 1 < K) y_n = py[(int64_t)(k + 1) * yb.sk];
+            if (k + 2 < K) wload(k + 2, w_n, w1_n);
+            N a_next = zero;
+            if (k + 1 < K) a_next = coef<N>(face_of(wk1, w1k1), ka, kexp);
             const N b = (dtr - a_cur) + a_next;
             const N p = (k > 0) ? b - a_cur * cp_prev : b;
             const N r = recip(p);
-            const N v = (k > 0) ? (x + a_cur * v_prev) * r : x * r;
+            const N U = (k > 0) ? addx<N, T>(-(cp_prev * U_prev), yk) : to_num<N, T>(yk);
             const N cpk = (-a_next) * r;
             if (wr) {
                 cpb[(size_t)k * cstride + cidx] = cpk;
-                vb[(size_t)k * cstride + cidx] = v;
+                vb[(size_t)k * cstride + cidx] = U * r;
             }
-            cp_prev = cpk, v_prev = v;
+            cp_prev = cpk, U_prev = U;
+            a_cur = a_next;
         }
-        a_cur = a_next;
     }
 
-    // backward sweep: z = L^-T v, outputs
+    // backward sweep, L^T z = v: Z_k = V_k + c'_k Z_{k+1} (Z = z / dtr), and the outputs
+    if (g.sym) {
+        const bool want_z = utb.p || utsb.p;
+        if (want_z) {
+            if (accumulate)
+                vadv_adj_back_sym<T, N, true, true>(yb, usb, upb, utb, utsb, cpb, vb, cstride, cidx, py, K, ic, jc,
+                                                    active, dtr, merge_us_up);
+            else
+                vadv_adj_back_sym<T, N, true, false>(yb, usb, upb, utb, utsb, cpb, vb, cstride, cidx, py, K, ic, jc,
+                                                     active, dtr, merge_us_up);
+        } else {
+            if (accumulate)
+                vadv_adj_back_sym<T, N, false, true>(yb, usb, upb, utb, utsb, cpb, vb, cstride, cidx, py, K, ic, jc,
+                                                     active, dtr, merge_us_up);
+            else
+                vadv_adj_back_sym<T, N, false, false>(yb, usb, upb, utb, utsb, cpb, vb, cstride, cidx, py, K, ic,
+                                                      jc, active, dtr, merge_us_up);
+        }
+        return;
+    }
+    // general weights: u_stage_bar = E^T z, emitted for level m once z_{m-1} is known
     auto store = [&](const View<T> &o, int k, N val) {
         if (!o.p || !active) return;
         T *q = o.p + ic + (int64_t)jc * o.sj + (int64_t)k * o.sk;
         *q = accumulate ? to_store<T, N>(to_num<N, T>(*q) + val) : to_store<T, N>(val);
     };
-    if (g.sym) {
-        // beta_v = 0: the explicit weights equal the implicit ones, E = dtr I - A, and
-        // A^T z = dtr y_bar gives E^T z = dtr (z - y_bar): the u_stage cotangent equals the
-        // u_pos one and needs neither wcon nor z's neighbours (3 FP64 operations per level
-        // instead of 7)
-        const N m = merge_us_up ? dtr + dtr : dtr;
-        N z1 = zero;
-        N vb_n = vb[(size_t)(K - 1) * cstride + cidx], cp_n = zero;
-        T yb_n = py[(int64_t)(K - 1) * yb.sk];
-        for (int k = K - 1; k >= 0; --k) {
-            const N vk = vb_n, cpk = cp_n;
-            const T ykr = yb_n;
-            if (k > 0) {
-                vb_n = vb[(size_t)(k - 1) * cstride + cidx];
-                cp_n = cpb[(size_t)(k - 1) * cstride + cidx];
-                yb_n = py[(int64_t)(k - 1) * yb.sk];
-            }
-            const N z = (k == K - 1) ? vk : vk + cpk * z1;
-            store(utb, k, z);
-            store(utsb, k, z);
-            const N u = m * addx<N, T>(z, -ykr);
-            store(usb, k, u);  // merged: u_stage_bar + u_pos_bar = 2 dtr (z - y_bar)
-            if (!merge_us_up) store(upb, k, u);
-            z1 = z;
-        }
-        return;
-    }
-    // general weights: u_stage_bar = E^T z, emitted for level m once z_{m-1} is known
     // carried from the previous (higher) level, so that nothing is formed or loaded twice:
+    N Z1 = zero;               // Z_{k+1}
     N z1 = zero;               // z_{k+1}
     N zz1 = zero;              // z_{k+1} + z_{k+2}
     N y1 = zero;               // y_bar_{k+1}
@@ -174,12 +217,10 @@ __global__ void __launch_bounds__(32 * BJ)
             yb_n = py[(int64_t)(k - 1) * yb.sk];
             if (k - 1 > 0) wload(k - 1, wb_n, wb1_n);
         }
-        const N z = (k == K - 1) ? vk : vk + cpk * z1;
+        const N Z = (k == K - 1) ? vk : vk + cpk * Z1;
+        const N z = dtr * Z;
         N ask = zero;
-        if (k > 0) {
-            const N s = face_of(wk, w1k);
-            ask = g.sym ? coef<N>(s, ka, kexp) : kas * s;
-        }
+        if (k > 0) ask = kas * face_of(wk, w1k);
         const N yk = to_num<N, T>(ykr);
         store(utb, k, z);
         store(utsb, k, z);
@@ -190,7 +231,7 @@ __global__ void __launch_bounds__(32 * BJ)
             // u_stage_bar and u_pos_bar as one field: level k+1 gets both
             store(usb, k + 1, merge_us_up ? usb1 + dtr * (z1 - y1) : usb1);
         }
-        z1 = z, zz1 = zz, y1 = yk;
+        Z1 = Z, z1 = z, zz1 = zz, y1 = yk;
         as2 = as1, as1 = ask;
     }
     {  // level 0: as_0 = 0
