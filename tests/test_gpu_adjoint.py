@@ -217,13 +217,13 @@ def test_chain_gradient_central_differences(G):
 
 @pytest.mark.parametrize("dtype,prec", [(np.float64, "native"), (np.float32, "df"), (np.float32, "f64"),
                                         (np.float32, "native")])
-def test_adjoint_from_kept_factors(G, dtype, prec):
+@pytest.mark.parametrize("I,J,K", [(70, 33, 41), (33, 7, 1), (31, 5, 2)])
+def test_adjoint_from_kept_factors(G, dtype, prec, I, J, K):
     """gtb_hdiff_vadv with GTB_SAVE_FACTORS returns the same output, and gtb_vadv_adj
     on the kept factors (GTB_ADJ_FACTORS) the same cotangents as the refactorising
     adjoint, bit for bit (the same pivots and c' values), merged and separate."""
     import torch
     from paper_2311_08322_b300 import inputs
-    I, J, K = 70, 33, 41
     f = inputs.hdiff_vadv(I, J, K, seed=12)
     dom = (I, J, K)
     s = {n: G.storage_from(f[n].astype(dtype), (2, 2, 0) if n in ("in", "coeff") else (1, 1, 0))
