@@ -116,7 +116,7 @@ __device__ __forceinline__ void fused_hdiff_level(const P &pol, const C &c, type
         const V fyn = pol.limit(c.lap(ci, cj + 1) - l0, pol.grad(c.x(ci, cj + 1), x0, c.sp(ci, cj + 1), c.sp(ci, cj)));
         const V fys = pol.limit(l0 - c.lap(ci, cj - 1), pol.grad(x0, c.x(ci, cj - 1), c.sp(ci, cj), c.sp(ci, cj - 1)));
         const V D = (fxe - fxw) + (fyn - fys);
-        em.put(m, p, pol.out(*c.sp(ci, cj), cf[q], D));
+        em.put(m, p, pol.outx(*c.sp(ci, cj), x0, cf[q], D));
     }
 }
 

@@ -36,6 +36,7 @@ struct Native {
     __device__ __forceinline__ Gd grad(V x1, V x0, const T *, const T *) const { return x1 - x0; }
     __device__ __forceinline__ V limit(V f, Gd g) const { return (f * g > T(0)) ? T(0) : f; }
     __device__ __forceinline__ T out(T in, T c, V D) const { return in - c * D; }
+    __device__ __forceinline__ T outx(T in, V, T c, V D) const { return out(in, c, D); }
 };
 
 // ICVT: convert the flux divergence back to binary64 on the integer pipe
@@ -55,6 +56,36 @@ struct FixedF64T {
     __device__ __forceinline__ V limit(V f, Gd g) const { return ((f > 0 && g > 0) || (f < 0 && g < 0)) ? 0 : f; }
     __device__ __forceinline__ double out(double in, double c, V D) const {
         return fma(-c, ICVT ? from_fixed_int(D, E) : from_fixed(D, E), in);
+    }
+    // The update given in's fixed-point value X as well.  ICVT (the kernels whose FP64
+    // pipe is the bottleneck) keeps it on the integer pipe: c D in units of the level's
+    // fixed point 2^(E-1078), from the exact product of c's significand and D (at most
+    // 115 bits) rounded to the unit, is subtracted from X and the result rounded once
+    // to binary64.  X's truncation and the product's rounding add at most a unit each,
+    // the size of the fixed point's own truncation (below 2^-54 of the level's largest
+    // input).  A zero product returns in itself; |c| >= 1 or non-finite c (the product
+    // could leave the int64 range) and levels with E > 1984 (the result's exponent
+    // could overflow) take the binary64 FMA.
+    __device__ __forceinline__ double outx(double in, V X, double c, V D) const {
+        if constexpr (ICVT) {
+            const int hi = __double2hiint(c);
+            const int ec = (hi >> 20) & 0x7FF;
+            if (ec <= 1022 && E <= 1984) {
+                const uint64_t mc = ((uint64_t)((unsigned)hi & 0xFFFFFu) << 32 | (unsigned)__double2loint(c)) |
+                                    (ec ? (1ull << 52) : 0ull);
+                const uint64_t d = D < 0 ? 0ull - (uint64_t)D : (uint64_t)D;
+                const uint64_t plo = mc * d, phi = __umul64hi(mc, d);  // mc d < 2^115
+                const int sh = 1075 - max(ec, 1);                        // >= 53
+                uint64_t r = 0;
+                if (sh < 64) r = ((phi << (64 - sh)) | (plo >> sh)) + ((plo >> (sh - 1)) & 1ull);
+                else if (sh == 64) r = phi + (plo >> 63);
+                else if (sh < 116) r = (phi >> (sh - 64)) + ((phi >> (sh - 65)) & 1ull);
+                if (r == 0) return in;
+                const bool neg = (hi < 0) != (D < 0);
+                return from_fixed_int(neg ? X + (int64_t)r : X - (int64_t)r, E);
+            }
+        }
+        return out(in, c, D);
     }
 };
 using FixedF64 = FixedF64T<false>;

@@ -171,3 +171,30 @@ def test_origin_offsets_fp64(G, orc, pad):
     rv = region(orc.vadv(*[f[n] for n in VN], origin=ov, domain=dom), ov, dom)
     assert rel_err(region(hout.numpy(), oh, dom), rh) <= F64_TOL
     assert rel_err(region(vout.numpy(), ov, dom), rv) <= F64_TOL
+
+
+def test_update_paths_fp64(G, orc):
+    """Every branch of the producers' update out = in - coeff D (integer pipe in the
+    co-scheduled kernel): coeff rows of 0, negative, subnormal, normal and >= 1 (the
+    binary64 fallback); levels of ordinary values, huge values (the fallback for a
+    large fixed-point scale), small values (fixed point at a small scale; 1e-140, so
+    that the oracle's binary64 limiter product cannot underflow: below about 1e-154
+    it can, and then it keeps fluxes that the exact sign test limits) and a constant
+    (D = 0: out equals in exactly).  Each level against the oracle, relative to its
+    own size."""
+    I, J, K = 40, 30, 4
+    dom = (I, J, K)
+    f = draw(*dom, 17)
+    cf = f["coeff"]
+    cf[:, 2:8, :] = 0.0
+    cf[:, 8:13, :] = -cf[:, 8:13, :]
+    cf[:, 13:17, :] = 3e-310
+    cf[:, 28:32, :] = 1.5
+    f["inp"][1] *= 1e295
+    f["inp"][2] *= 1e-140
+    f["inp"][3] = 0.625
+    h, _, _ = run(G, f, dom)
+    rh, _ = oracle(orc, f, dom)
+    for k in range(3):
+        assert rel_err(h[k], rh[k]) <= F64_TOL, k
+    assert np.array_equal(h[3], np.full_like(h[3], 0.625))
