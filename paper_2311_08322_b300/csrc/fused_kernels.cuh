@@ -265,7 +265,7 @@ __device__ __forceinline__ void hdiff_producer(const CUtensorMap *tmap, const Vi
             if (fixed) {
                 producer_sync<PW>();  // X complete
                 const FusedCells<T, int64_t, TI, TJ, true> c{S, Xs, reinterpret_cast<const int64_t *>(Lraw), xs};
-                fused_hdiff_level<TI, TJ, PW>(FixedF64T<true>{(int)E}, c, reinterpret_cast<int64_t *>(Lraw), pt, cf,
+                fused_hdiff_level<TI, TJ, PW>(FixedF64T<true>{(int)E, hg.int_update}, c, reinterpret_cast<int64_t *>(Lraw), pt, cf,
                                               m, em);
                 done = true;
             }

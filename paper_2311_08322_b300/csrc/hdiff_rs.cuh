@@ -46,6 +46,7 @@ struct FixedF64T {
     using V = int64_t;
     using Gd = int;
     int E;
+    int iu = 0;  // ICVT: the update on the integer pipe (outx)
     __device__ __forceinline__ V conv(double x) const { return to_fixed(x, E); }
     __device__ __forceinline__ V lap(V c, V e, V w, V n, V s) const { return 4 * c - (((e + w) + n) + s); }
     // exact sign of in1 - in0; the binary64 values are read only when X1 == X0
@@ -65,12 +66,14 @@ struct FixedF64T {
     // the size of the fixed point's own truncation (below 2^-54 of the level's largest
     // input).  A zero product returns in itself; |c| >= 1 or non-finite c (the product
     // could leave the int64 range) and levels with E > 1984 (the result's exponent
-    // could overflow) take the binary64 FMA.
+    // could overflow) take the binary64 FMA, and so does everything unless iu: the
+    // integer form lengthens the producers' per-level path, which pays only when the
+    // grid fills the GPU and the FP64 pipe is the bound.
     __device__ __forceinline__ double outx(double in, V X, double c, V D) const {
         if constexpr (ICVT) {
             const int hi = __double2hiint(c);
             const int ec = (hi >> 20) & 0x7FF;
-            if (ec <= 1022 && E <= 1984) {
+            if (iu && ec <= 1022 && E <= 1984) {
                 const uint64_t mc = ((uint64_t)((unsigned)hi & 0xFFFFFu) << 32 | (unsigned)__double2loint(c)) |
                                     (ec ? (1ull << 52) : 0ull);
                 const uint64_t d = D < 0 ? 0ull - (uint64_t)D : (uint64_t)D;

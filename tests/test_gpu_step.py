@@ -173,16 +173,18 @@ def test_origin_offsets_fp64(G, orc, pad):
     assert rel_err(region(vout.numpy(), ov, dom), rv) <= F64_TOL
 
 
-def test_update_paths_fp64(G, orc):
-    """Every branch of the producers' update out = in - coeff D (integer pipe in the
-    co-scheduled kernel): coeff rows of 0, negative, subnormal, normal and >= 1 (the
-    binary64 fallback); levels of ordinary values, huge values (the fallback for a
+@pytest.mark.parametrize("I,J", [(40, 30), (256, 240)])
+def test_update_paths_fp64(G, orc, I, J):
+    """Every branch of the producers' update out = in - coeff D, in both forms: a
+    small grid keeps the binary64 FMA, 256 x 240 (960 CTAs, over 90% of what the GPU
+    holds at once) takes the integer pipe.  coeff rows of 0, negative, subnormal,
+    normal and >= 1 (the binary64 fallback); levels of ordinary values, huge values (the fallback for a
     large fixed-point scale), small values (fixed point at a small scale; 1e-140, so
     that the oracle's binary64 limiter product cannot underflow: below about 1e-154
     it can, and then it keeps fluxes that the exact sign test limits) and a constant
     (D = 0: out equals in exactly).  Each level against the oracle, relative to its
     own size."""
-    I, J, K = 40, 30, 4
+    K = 4
     dom = (I, J, K)
     f = draw(*dom, 17)
     cf = f["coeff"]
