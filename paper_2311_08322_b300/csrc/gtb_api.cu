@@ -161,11 +161,13 @@ static int resident_blocks(K kernel, int threads, int smem_bytes) {
     return nb;
 }
 
-// Whether a co-scheduled or fused launch fills the GPU (at least 90% of the CTAs it
+// Whether a co-scheduled or fused launch fills the GPU (at least 85% of the CTAs it
 // can hold at once): then its FP64 pipe is the bound and the producers' update goes
 // to the integer pipe; a smaller grid is bound by the producers' per-level path and
-// keeps the binary64 FMA (measured: 256x256 gains 4%, 224x224 and below lose 6-15%).
-// Cached per (kernel, device).
+// keeps the binary64 FMA.  Measured at K = 80, step: 256x256 (99% of capacity) 4%
+// faster, 224x224 (76%) and below 6-15% slower; fused chain: 256x256 (86%) 2%,
+// 512x512 5% faster, 240x240 (81%) even, 224x224 and below 6-14% slower.
+// Capacity cached per (kernel, device).
 static std::mutex g_fill_mu;
 static std::unordered_map<const void *, std::vector<int>> g_fill_cap;  // per device: resident CTAs, 0 = unknown
 
@@ -180,7 +182,7 @@ static int fills_gpu(K kernel, int threads, int smem_bytes, int64_t ctas) {
         if (!v[dev]) v[dev] = resident_blocks(kernel, threads, smem_bytes) * sm_count();
         cap = v[dev];
     }
-    return ctas * 10 >= (int64_t)cap * 9 ? 1 : 0;
+    return ctas * 20 >= (int64_t)cap * 17 ? 1 : 0;
 }
 
 static int launch_status(const char *what) {

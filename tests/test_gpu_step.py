@@ -176,7 +176,7 @@ def test_origin_offsets_fp64(G, orc, pad):
 @pytest.mark.parametrize("I,J", [(40, 30), (256, 240)])
 def test_update_paths_fp64(G, orc, I, J):
     """Every branch of the producers' update out = in - coeff D, in both forms: a
-    small grid keeps the binary64 FMA, 256 x 240 (960 CTAs, over 90% of what the GPU
+    small grid keeps the binary64 FMA, 256 x 240 (960 CTAs, over 85% of what the GPU
     holds at once) takes the integer pipe.  coeff rows of 0, negative, subnormal,
     normal and >= 1 (the binary64 fallback); levels of ordinary values, huge values (the fallback for a
     large fixed-point scale), small values (fixed point at a small scale; 1e-140, so
