@@ -206,8 +206,9 @@ int gtb_halo_periodic_adj(const gtb_field *f, int hi, int hj, const int64_t *dom
  *   utens_stage_out = vadv(u_stage = h, wcon, u_pos = h, utens, utens_stage)
  * in one kernel; h is formed level by level on chip and never written to
  * memory.  The back substitution runs on z = x - h (the same unknowns,
- * utens_stage_out = dtr_stage z), so results agree with gtb_hdiff followed by
- * gtb_vadv to rounding, not bit for bit.
+ * utens_stage_out = dtr_stage z), and h's update may be formed in fixed point
+ * as in gtb_step, so results agree with gtb_hdiff followed by gtb_vadv to
+ * rounding, not bit for bit.
  * Fields: in needs 2 halo points in I and J (as gtb_hdiff), wcon one point
  * above I unless GTB_WCON_LITERAL (as gtb_vadv); coeff, utens, utens_stage
  * and utens_stage_out cover the domain.  utens_stage_out may be the very same
@@ -244,7 +245,9 @@ size_t gtb_hdiff_vadv_workspace_bytes(int dtype, int prec, unsigned flags, const
  * the same tile on two others (binary64 hdiff runs on the integer pipe and the
  * solve on the FP64 pipe, so the two overlap in every SM); hdiff_out then
  * equals gtb_hdiff's to rounding (the fixed-point scale is chosen per tile and
- * level, not per strip).  For GTB_F32 storage (HBM-bound hdiff, FP32-pipe
+ * level, not per strip; and when the grid fills the GPU the update
+ * in - coeff D is formed in that fixed point too, on the integer pipe, within
+ * 2^-54 of the level's largest input).  For GTB_F32 storage (HBM-bound hdiff, FP32-pipe
  * solve) the two kernels run back to back, which is faster there, and
  * hdiff_out equals gtb_hdiff's.  utens_stage_out always equals gtb_vadv's
  * result (workspace form) bit for bit.
