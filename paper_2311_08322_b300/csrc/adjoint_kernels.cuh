@@ -46,27 +46,45 @@ __device__ __forceinline__ void vadv_adj_back_sym(const View<const T> &yb, const
     };
     const N m = merge_us_up ? dtr + dtr : dtr;
     const N zero = num_const<N>(0.0);
-    N Z1 = zero;
-    N v_n = vb[(size_t)(K - 1) * cstride + cidx], cp_n = zero;
-    T y_n = py[(int64_t)(K - 1) * yb.sk];
-    for (int k = K - 1; k >= 0; --k) {
-        const N vk = v_n, cpk = cp_n;
-        const T yk = y_n;
-        if (k > 0) {
-            v_n = vb[(size_t)(k - 1) * cstride + cidx];
-            cp_n = cpb[(size_t)(k - 1) * cstride + cidx];
-            y_n = py[(int64_t)(k - 1) * yb.sk];
+    // levels in groups of G, each group's inputs loaded while the previous group is
+    // computed: in binary64, with 5 FP64 operations per point, the sweep waits on memory
+    // otherwise (the FP32-pipe forms are compute-bound: one level ahead)
+    constexpr int G = std::is_same<N, double>::value ? 4 : 1;
+    N vq[G], cq[G];
+    T yq[G];
+    auto load_group = [&](int k0) {  // levels k0, k0-1, ..., k0-G+1
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int k = k0 - q;
+            if (k < 0) break;
+            vq[q] = vb[(size_t)k * cstride + cidx];
+            cq[q] = k < K - 1 ? cpb[(size_t)k * cstride + cidx] : zero;
+            yq[q] = py[(int64_t)k * yb.sk];
         }
-        const N Z = (k == K - 1) ? vk : vk + cpk * Z1;
-        if (WANT_Z) {
-            const N z = dtr * Z;
-            store(utb, k, z);
-            store(utsb, k, z);
+    };
+    N Z1 = zero;  // Z_K = 0
+    load_group(K - 1);
+    for (int k0 = K - 1; k0 >= 0; k0 -= G) {
+        N vc[G], cc[G];
+        T yc[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) vc[q] = vq[q], cc[q] = cq[q], yc[q] = yq[q];
+        if (k0 - G >= 0) load_group(k0 - G);
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int k = k0 - q;
+            if (k < 0) break;
+            const N Z = vc[q] + cc[q] * Z1;  // c'_{K-1} = 0
+            if (WANT_Z) {
+                const N z = dtr * Z;
+                store(utb, k, z);
+                store(utsb, k, z);
+            }
+            const N u = m * addx<N, T>(dtr * Z, -yc[q]);  // one FMA: dtr Z - y_bar
+            store(usb, k, u);
+            if (!merge_us_up) store(upb, k, u);
+            Z1 = Z;
         }
-        const N u = m * addx<N, T>(dtr * Z, -yk);  // one FMA: dtr Z - y_bar
-        store(usb, k, u);
-        if (!merge_us_up) store(upb, k, u);
-        Z1 = Z;
     }
 }
 
@@ -133,24 +151,42 @@ __global__ void __launch_bounds__(32 * BJ)
     // once c' is known no a_k is needed (FACT reads no wcon).  Carried in units of dtr,
     // U = u / dtr and V = v / dtr.  Every input of level k+1 is loaded during level k.
     N cp_prev = zero, U_prev = zero;
-    T y_n = py[0];
     if constexpr (FACT) {
-        N r_n = vb[cidx], c_n = cpb[cidx];
-        for (int k = 0; k < K; ++k) {
-            const T yk = y_n;
-            const N rk = r_n, ck = c_n;
-            if (k + 1 < K) {
-                y_n = py[(int64_t)(k + 1) * yb.sk];
-                r_n = vb[(size_t)(k + 1) * cstride + cidx];
-                c_n = cpb[(size_t)(k + 1) * cstride + cidx];
+        // levels in groups of G, each group's inputs loaded while the previous group is
+        // computed (V_k overwrites 1/p_k only after level k's group was read); binary64
+        // only, as in the backward sweep
+        constexpr int G = std::is_same<N, double>::value ? 4 : 1;
+        T yq[G];
+        N rq[G], cq[G];
+        auto load_group = [&](int k0) {
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const int k = k0 + q;
+                if (k >= K) break;
+                yq[q] = py[(int64_t)k * yb.sk];
+                rq[q] = vb[(size_t)k * cstride + cidx];
+                cq[q] = cpb[(size_t)k * cstride + cidx];
             }
-            const N U = (k > 0) ? addx<N, T>(-(cp_prev * U_prev), yk) : to_num<N, T>(yk);
-            if (wr) vb[(size_t)k * cstride + cidx] = U * rk;
-            cp_prev = ck, U_prev = U;
+        };
+        load_group(0);
+        for (int k0 = 0; k0 < K; k0 += G) {
+            T yc[G];
+            N rc[G], cc[G];
+#pragma unroll
+            for (int q = 0; q < G; ++q) yc[q] = yq[q], rc[q] = rq[q], cc[q] = cq[q];
+            if (k0 + G < K) load_group(k0 + G);
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const int k = k0 + q;
+                if (k >= K) break;
+                const N U = (k > 0) ? addx<N, T>(-(cp_prev * U_prev), yc[q]) : to_num<N, T>(yc[q]);
+                if (wr) vb[(size_t)k * cstride + cidx] = U * rc[q];
+                cp_prev = cc[q], U_prev = U;
+            }
         }
     } else {
         N a_cur = zero;
-        T w_n = T(0), w1_n = T(0);
+        T y_n = py[0], w_n = T(0), w1_n = T(0);
         if (K > 1) wload(1, w_n, w1_n);
         for (int k = 0; k < K; ++k) {
             const T yk = y_n, wk1 = w_n, w1k1 = w1_n;
