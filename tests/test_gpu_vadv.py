@@ -163,3 +163,16 @@ def test_explicit_workspace_tensor_and_inplace(G, orc):
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     got, ref = run_case(G, orc, 60, 20, 50, seed=77, inplace=True, workspace=ws)
     assert rel_err(got, ref) <= F64_TOL
+
+
+@pytest.mark.parametrize("workspace", ["auto", None])
+@pytest.mark.parametrize("dtype,prec", [(np.float64, "native"), (np.float32, "df"), (np.float32, "f64")])
+def test_general_weights_every_form(G, orc, workspace, dtype, prec):
+    """beta_v != 0 (the general-weight body of the column solve) and the literal face
+    velocity in every state form (workspace: the y back substitution in binary64, e_k
+    otherwise; shared memory: e_k) and column arithmetic."""
+    tol = F64_TOL if dtype == np.float64 else F32_TOL
+    for literal, beta in ((False, 0.3), (True, -0.2), (True, 0.0)):
+        got, ref = run_case(G, orc, 67, 13, 41, seed=9, dtype=dtype, prec=prec, literal=literal, beta_v=beta,
+                            wamp=0.25, workspace=workspace)
+        assert rel_err(got, ref) <= tol, (literal, beta)
