@@ -321,11 +321,10 @@ __device__ __forceinline__ void fused_consumer(const View<const T> &wc, const Vi
     const int kexp = g.ka_pow2;
 
     N a_cur = zero, g_cur = zero, dpl_prev = zero, cp_prev = zero, dp_prev = zero, e_last = zero;
-    N s_cur = zero;  // 2 h_k
 
-    // forward elimination step of level k; hk = h_k, hk1 = h_{k+1}
-    auto vstep = [&](int k, bool has_next, T hk, T hk1, T utk, T utsk, T wk1, T w1k1) {
-        if (k == 0) s_cur = add2<N, T>(hk, hk);
+    // forward elimination step of level k; hk = h_k, hk1 = h_{k+1}, s_cur = 2 h_k,
+    // s_nx = 2 h_{k+1} (each formed once, when its level arrives)
+    auto vstep = [&](int k, bool has_next, T hk, T hk1, N s_cur, N s_nx, T utk, T utsk, T wk1, T w1k1) {
         N a_next = zero, g_next = zero, s_next = zero, dpl = zero;
         if (has_next) {
             N sface;
@@ -337,7 +336,7 @@ __device__ __forceinline__ void fused_consumer(const View<const T> &wc, const Vi
                 sface = add2<N, T>(wk1, hi);
             }
             a_next = coef<N>(sface, ka, kexp);
-            s_next = add2<N, T>(hk1, hk1);
+            s_next = s_nx;
             if (!SYM) {
                 g_next = kg * sface;
                 dpl = add2<N, T>(hk1, -hk);  // h_{k+1} - h_k
@@ -364,7 +363,6 @@ __device__ __forceinline__ void fused_consumer(const View<const T> &wc, const Vi
             else epb[(size_t)k * cstride + cidx] = e;
         }
         cp_prev = cpk, dp_prev = dpk, e_last = e;
-        s_cur = s_next;
         if (!SYM) dpl_prev = dpl, g_cur = g_next;
         a_cur = a_next;
     };
@@ -372,6 +370,7 @@ __device__ __forceinline__ void fused_consumer(const View<const T> &wc, const Vi
     // utens, utens_stage of level m-1 and wcon of level m, loaded one iteration ahead
     T ut_n = T(0), uts_n = T(0), w_n = T(0), w1_n = T(0);
     T h_prev = T(0);
+    N h2_prev = zero;
     for (int m = 0; m < K; ++m) {
         const T ut_k = ut_n, uts_k = uts_n, w_m = w_n, w1_m = w1_n;
         if (m + 1 < K) {
@@ -386,10 +385,11 @@ __device__ __forceinline__ void fused_consumer(const View<const T> &wc, const Vi
         const T h = H[slot * NC + tid];
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
-        if (m >= 1) vstep(m - 1, true, h_prev, h, ut_k, uts_k, w_m, w1_m);
-        h_prev = h;
+        const N h2 = add2<N, T>(h, h);  // s_m = 2 h_m, exact
+        if (m >= 1) vstep(m - 1, true, h_prev, h, h2_prev, h2, ut_k, uts_k, w_m, w1_m);
+        h_prev = h, h2_prev = h2;
     }
-    vstep(K - 1, false, h_prev, T(0), ut_n, uts_n, T(0), T(0));
+    vstep(K - 1, false, h_prev, T(0), h2_prev, zero, ut_n, uts_n, T(0), T(0));
 
     // back substitution in z = x - h; levels in groups of BG, a group's inputs loaded
     // before the previous group's outputs are stored (distinct levels, distinct addresses)
