@@ -453,18 +453,40 @@ __global__ void __launch_bounds__(NT)
     const int k = blockIdx.y;
     const int I = g.I, J = g.J;
 
-    // in on the cells the forward definition reads (zero elsewhere, including the
-    // unread halo corners), q = coeff * out_bar on the domain; each thread keeps its
-    // cells in registers until the tile's scales are known
+    // Staging by asynchronous element copies (every copy of the block in flight at once,
+    // no register round trip): in on the cells the forward definition reads, coeff and
+    // out_bar on the domain cells of the q box, zero-filled elsewhere (including the
+    // unread halo corners).  out_bar lands in the Laplacian region, written only after
+    // the staging.  Each thread copies the cells tid + c NT and reads back only those.
     constexpr int CI = (H::IX * H::IY + NT - 1) / NT, CQ = (H::QX * H::QY + NT - 1) / NT;
+    T *S_ob = S_q + H::QX * H::QY;
+#pragma unroll
+    for (int c = 0; c < CI; ++c) {
+        const int idx = tid + c * NT;
+        if (idx >= H::IX * H::IY) break;
+        const int a = ti0 - 3 + idx % H::IX, b = tj0 - 3 + idx / H::IX;
+        const bool rd = hdiff_reads(a, b, I, J);
+        cp_async_elem(S_in + idx, rd ? in.p + a + (int64_t)b * in.sj + (int64_t)k * in.sk : in.p, rd);
+    }
+#pragma unroll
+    for (int c = 0; c < CQ; ++c) {
+        const int idx = tid + c * NT;
+        if (idx >= H::QX * H::QY) break;
+        const int a = ti0 - 2 + idx % H::QX, b = tj0 - 2 + idx / H::QX;
+        const bool dom = a >= 0 && a < I && b >= 0 && b < J;
+        cp_async_elem(S_q + idx, dom ? coeff.p + a + (int64_t)b * coeff.sj + (int64_t)k * coeff.sk : coeff.p, dom);
+        cp_async_elem(S_ob + idx, dom ? ob.p + a + (int64_t)b * ob.sj + (int64_t)k * ob.sk : ob.p, dom);
+    }
+    cp_async_wait_all();
+
+    // in, and q = coeff * out_bar, of this thread's cells in registers until the tile's
+    // scales are known
     T vin[CI], vq[CQ];
     unsigned ein = 0, eq = 0, qnz = 0, inz = 0;
 #pragma unroll
     for (int c = 0; c < CI; ++c) {
         const int idx = tid + c * NT;
-        const int a = ti0 - 3 + idx % H::IX, b = tj0 - 3 + idx / H::IX;
-        T v = T(0);
-        if (idx < H::IX * H::IY && hdiff_reads(a, b, I, J)) v = in.p[a + (int64_t)b * in.sj + (int64_t)k * in.sk];
+        const T v = idx < H::IX * H::IY ? S_in[idx] : T(0);
         vin[c] = v;
         if constexpr (FIX) {
             ein = max(ein, ((unsigned)__double2hiint(v) >> 20) & 0x7FFu);
@@ -474,10 +496,7 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
     for (int c = 0; c < CQ; ++c) {
         const int idx = tid + c * NT;
-        const int a = ti0 - 2 + idx % H::QX, b = tj0 - 2 + idx / H::QX;
-        T v = T(0);
-        if (idx < H::QX * H::QY && a >= 0 && a < I && b >= 0 && b < J)
-            v = coeff.p[a + (int64_t)b * coeff.sj + (int64_t)k * coeff.sk] * ob.p[a + (int64_t)b * ob.sj + (int64_t)k * ob.sk];
+        const T v = idx < H::QX * H::QY ? S_q[idx] * S_ob[idx] : T(0);  // zero-filled off the domain
         vq[c] = v;
         if constexpr (FIX) {
             eq = max(eq, ((unsigned)__double2hiint(v) >> 20) & 0x7FFu);

@@ -114,6 +114,23 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// ---------------------------------------------------------------- async element copies
+// One element global -> shared without a register round trip (cp.async): a block can
+// have every copy of its staging in flight at once.  When !valid nothing is read and
+// the destination is zero-filled (src-size 0); src must still be a valid address.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool valid) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned n = valid ? (unsigned)sizeof(T) : 0u;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src),
+                 "n"((int)sizeof(T)), "r"(n)
+                 : "memory");
+}
+
+// Wait for this thread's async element copies; they are then visible to this thread
+// (other threads need a barrier as well).
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // ---------------------------------------------------------------- reciprocal
 // a * b in binary64 (round to nearest) that stays inside its branch: volatile, so
 // the compiler does not hoist it onto the FP64 pipe ahead of a rarely taken test.
