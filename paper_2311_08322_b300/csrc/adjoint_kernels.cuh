@@ -325,6 +325,19 @@ __device__ __forceinline__ bool limited(T f, T g) {
 //   lb      = (gx[i-1] - gx[i]) + (gy[j-1] - gy[j])      (cotangent of lap)
 //   in_bar  = out_bar - (4 lb - sum of the 4 neighbours of lb)
 //   coeff_bar = -D out_bar,  D = (fx[i] - fx[i-1]) + (fy[j] - fy[j-1]),  f = keep (lap[+1] - lap)
+// f(idx, a, b) for the cells idx = tid, tid + NT, ... of a W x H region, a = idx % W,
+// b = idx / W, the coordinates stepped by NT from cell to cell instead of divided anew.
+template <int W, int H, int NT, typename F>
+__device__ __forceinline__ void for_cells(int tid, F &&f) {
+    constexpr int DA = NT % W, DB = NT / W;
+    int a = tid % W, b = tid / W;
+    for (int idx = tid; idx < W * H; idx += NT) {
+        f(idx, a, b);
+        a += DA, b += DB;
+        if (a >= W) a -= W, ++b;
+    }
+}
+
 template <typename T, int TI, int TJ, int NT, typename P>
 __device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x, typename P::V *S_q,
                                                unsigned char *S_keep, const View<const T> &in,
@@ -342,17 +355,17 @@ __device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x,
     auto GIN = [&](int a, int b) -> const T * {  // the binary64 value, for exact ties
         return in.p + (ti0 + a) + (int64_t)(tj0 + b) * in.sj + (int64_t)k * in.sk;
     };
-    for (int idx = tid; idx < H::QX * H::QY; idx += NT) {
-        const int a = idx % H::QX - 2, b = idx / H::QX - 2;
+    for_cells<H::QX, H::QY, NT>(tid, [&](int idx, int ca, int cb_) {
+        const int a = ca - 2, b = cb_ - 2;
         S_lap[idx] = pol.lap(X(a, b), X(a + 1, b), X(a - 1, b), X(a, b + 1), X(a, b - 1));
-    }
+    });
     __syncthreads();
     auto LAP = [&](int a, int b) -> V { return S_lap[(a + 2) + (b + 2) * H::QX]; };
     auto Q = [&](int a, int b) -> V { return S_q[(a + 2) + (b + 2) * H::QX]; };
     // every face once: keep/zero from the forward values and its cotangent
     // (a face exists for domain-relative i in [-1, I-1], j in [0, J) in x, and likewise in y)
-    for (int idx = tid; idx < H::GXX * H::GXY; idx += NT) {
-        const int a = idx % H::GXX - 2, b = idx / H::GXX - 1;  // face between cells a and a+1, row b
+    for_cells<H::GXX, H::GXY, NT>(tid, [&](int idx, int ca, int cb_) {
+        const int a = ca - 2, b = cb_ - 1;  // face between cells a and a+1, row b
         const int da = ti0 + a, db = tj0 + b;
         V gv = V(0);
         bool keep = false;
@@ -362,9 +375,9 @@ __device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x,
         }
         S_gx[idx] = gv;
         S_kx[idx] = keep;
-    }
-    for (int idx = tid; idx < H::GYX * H::GYY; idx += NT) {
-        const int a = idx % H::GYX - 1, b = idx / H::GYX - 2;  // face between rows b and b+1, column a
+    });
+    for_cells<H::GYX, H::GYY, NT>(tid, [&](int idx, int ca, int cb_) {
+        const int a = ca - 1, b = cb_ - 2;  // face between rows b and b+1, column a
         const int da = ti0 + a, db = tj0 + b;
         V gv = V(0);
         bool keep = false;
@@ -374,14 +387,14 @@ __device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x,
         }
         S_gy[idx] = gv;
         S_ky[idx] = keep;
-    }
+    });
     __syncthreads();
     auto GX = [&](int a, int b) -> V { return S_gx[(a + 2) + (b + 1) * H::GXX]; };
     auto GY = [&](int a, int b) -> V { return S_gy[(a + 1) + (b + 2) * H::GYX]; };
-    for (int idx = tid; idx < H::LX * H::LY; idx += NT) {
-        const int a = idx % H::LX - 1, b = idx / H::LX - 1;
+    for_cells<H::LX, H::LY, NT>(tid, [&](int idx, int ca, int cb_) {
+        const int a = ca - 1, b = cb_ - 1;
         S_lb[idx] = (GX(a - 1, b) - GX(a, b)) + (GY(a, b - 1) - GY(a, b));
-    }
+    });
     __syncthreads();
     auto LB = [&](int a, int b) -> V { return S_lb[(a + 1) + (b + 1) * H::LX]; };
     auto FX = [&](int a, int b) -> V {  // forward x-flux of face (a, a+1) in row b, 0 where limited
@@ -390,10 +403,9 @@ __device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x,
     auto FY = [&](int a, int b) -> V {
         return S_ky[(a + 1) + (b + 2) * H::GYX] ? LAP(a, b + 1) - LAP(a, b) : V(0);
     };
-    for (int idx = tid; idx < TI * TJ; idx += NT) {
-        const int a = idx % TI, b = idx / TI;
+    for_cells<TI, TJ, NT>(tid, [&](int idx, int a, int b) {
         const int da = ti0 + a, db = tj0 + b;
-        if (da < -2 || da >= I + 2 || db < -2 || db >= J + 2) continue;
+        if (da < -2 || da >= I + 2 || db < -2 || db >= J + 2) return;
         const V tr = pol.lap(LB(a, b), LB(a + 1, b), LB(a - 1, b), LB(a, b + 1), LB(a, b - 1));
         const bool dom = da >= 0 && da < I && db >= 0 && db < J;
         const T o = dom ? ob.p[da + (int64_t)db * ob.sj + (int64_t)k * ob.sk] : T(0);
@@ -403,7 +415,7 @@ __device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x,
             T *c = cb.p + da + (int64_t)db * cb.sj + (int64_t)k * cb.sk;
             *c = g.accumulate_coeff_bar ? *c - D * o : -D * o;
         }
-    }
+    });
 }
 
 // The definition in the storage type.
@@ -460,22 +472,32 @@ __global__ void __launch_bounds__(NT)
     // the staging.  Each thread copies the cells tid + c NT and reads back only those.
     constexpr int CI = (H::IX * H::IY + NT - 1) / NT, CQ = (H::QX * H::QY + NT - 1) / NT;
     T *S_ob = S_q + H::QX * H::QY;
+    {
+        int ca = tid % H::IX, cb_ = tid / H::IX;  // cell coordinates, stepped by NT
 #pragma unroll
-    for (int c = 0; c < CI; ++c) {
-        const int idx = tid + c * NT;
-        if (idx >= H::IX * H::IY) break;
-        const int a = ti0 - 3 + idx % H::IX, b = tj0 - 3 + idx / H::IX;
-        const bool rd = hdiff_reads(a, b, I, J);
-        cp_async_elem(S_in + idx, rd ? in.p + a + (int64_t)b * in.sj + (int64_t)k * in.sk : in.p, rd);
+        for (int c = 0; c < CI; ++c) {
+            const int idx = tid + c * NT;
+            if (idx >= H::IX * H::IY) break;
+            const int a = ti0 - 3 + ca, b = tj0 - 3 + cb_;
+            const bool rd = hdiff_reads(a, b, I, J);
+            cp_async_elem(S_in + idx, rd ? in.p + a + (int64_t)b * in.sj + (int64_t)k * in.sk : in.p, rd);
+            ca += NT % H::IX, cb_ += NT / H::IX;
+            if (ca >= H::IX) ca -= H::IX, ++cb_;
+        }
     }
+    {
+        int ca = tid % H::QX, cb_ = tid / H::QX;
 #pragma unroll
-    for (int c = 0; c < CQ; ++c) {
-        const int idx = tid + c * NT;
-        if (idx >= H::QX * H::QY) break;
-        const int a = ti0 - 2 + idx % H::QX, b = tj0 - 2 + idx / H::QX;
-        const bool dom = a >= 0 && a < I && b >= 0 && b < J;
-        cp_async_elem(S_q + idx, dom ? coeff.p + a + (int64_t)b * coeff.sj + (int64_t)k * coeff.sk : coeff.p, dom);
-        cp_async_elem(S_ob + idx, dom ? ob.p + a + (int64_t)b * ob.sj + (int64_t)k * ob.sk : ob.p, dom);
+        for (int c = 0; c < CQ; ++c) {
+            const int idx = tid + c * NT;
+            if (idx >= H::QX * H::QY) break;
+            const int a = ti0 - 2 + ca, b = tj0 - 2 + cb_;
+            const bool dom = a >= 0 && a < I && b >= 0 && b < J;
+            cp_async_elem(S_q + idx, dom ? coeff.p + a + (int64_t)b * coeff.sj + (int64_t)k * coeff.sk : coeff.p, dom);
+            cp_async_elem(S_ob + idx, dom ? ob.p + a + (int64_t)b * ob.sj + (int64_t)k * ob.sk : ob.p, dom);
+            ca += NT % H::QX, cb_ += NT / H::QX;
+            if (ca >= H::QX) ca -= H::QX, ++cb_;
+        }
     }
     cp_async_wait_all();
 
