@@ -325,19 +325,6 @@ __device__ __forceinline__ bool limited(T f, T g) {
 //   lb      = (gx[i-1] - gx[i]) + (gy[j-1] - gy[j])      (cotangent of lap)
 //   in_bar  = out_bar - (4 lb - sum of the 4 neighbours of lb)
 //   coeff_bar = -D out_bar,  D = (fx[i] - fx[i-1]) + (fy[j] - fy[j-1]),  f = keep (lap[+1] - lap)
-// f(idx, a, b) for the cells idx = tid, tid + NT, ... of a W x H region, a = idx % W,
-// b = idx / W, the coordinates stepped by NT from cell to cell instead of divided anew.
-template <int W, int H, int NT, typename F>
-__device__ __forceinline__ void for_cells(int tid, F &&f) {
-    constexpr int DA = NT % W, DB = NT / W;
-    int a = tid % W, b = tid / W;
-    for (int idx = tid; idx < W * H; idx += NT) {
-        f(idx, a, b);
-        a += DA, b += DB;
-        if (a >= W) a -= W, ++b;
-    }
-}
-
 template <typename T, int TI, int TJ, int NT, typename P>
 __device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x, typename P::V *S_q,
                                                unsigned char *S_keep, const View<const T> &in,

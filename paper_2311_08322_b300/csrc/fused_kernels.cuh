@@ -100,10 +100,10 @@ __device__ __forceinline__ void fused_hdiff_level(const P &pol, const C &c, type
     using V = typename P::V;
     using Tile = FusedTile<T, TI, TJ>;
     constexpr int NPT = 32 * PW, PPT = (Tile::NC + NPT - 1) / NPT;
-    for (int idx = pt; idx < Tile::LW * Tile::LH; idx += NPT) {
-        const int li = idx % Tile::LW - 1, lj = idx / Tile::LW - 1;
+    for_cells<Tile::LW, Tile::LH, NPT>(pt, [&](int idx, int la, int lb) {
+        const int li = la - 1, lj = lb - 1;
         Lw[idx] = pol.lap(c.x(li, lj), c.x(li + 1, lj), c.x(li - 1, lj), c.x(li, lj + 1), c.x(li, lj - 1));
-    }
+    });
     producer_sync<PW>();
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {

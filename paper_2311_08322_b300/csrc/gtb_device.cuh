@@ -114,6 +114,19 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// f(idx, a, b) for the cells idx = tid, tid + NT, ... of a W x H region, a = idx % W,
+// b = idx / W, the coordinates stepped by NT from cell to cell instead of divided anew.
+template <int W, int H, int NT, typename F>
+__device__ __forceinline__ void for_cells(int tid, F &&f) {
+    constexpr int DA = NT % W, DB = NT / W;
+    int a = tid % W, b = tid / W;
+    for (int idx = tid; idx < W * H; idx += NT) {
+        f(idx, a, b);
+        a += DA, b += DB;
+        if (a >= W) a -= W, ++b;
+    }
+}
+
 // ---------------------------------------------------------------- async element copies
 // One element global -> shared without a register round trip (cp.async): a block can
 // have every copy of its staging in flight at once.  When !valid nothing is read and
