@@ -442,7 +442,7 @@ def run_gtb(args):
     return 0
 
 
-def call_overhead(reps=2000, host_reps=200):
+def call_overhead(reps=2000, host_reps=64):
     """The paper's timing split (Python call vs the compiled call alone) for one step on
     the small 64x64x40 FP64 workload, where launch and call costs show: device time per
     step (CUDA events), host time per call of the C ABI with prepared descriptors, and
@@ -475,14 +475,15 @@ def call_overhead(reps=2000, host_reps=200):
         gtb.step(*args, domain=dom, stream=stream)
 
     out = {"workload": "one hdiff+vadv step (gtb_step) at 64x64x40 FP64"}
-    # host time per call over fewer calls than the launch queue holds (so that the host
-    # never waits for the device), median of several bursts
+    # host time per call over bursts short enough that the launch queue never fills (a
+    # full queue makes the host wait for the device inside the timed region: bursts of
+    # 200 calls of this 45 us kernel did), median of several bursts
     for name, fn in (("c_abi_us_per_call", c_call), ("python_us_per_call", py_call)):
         for _ in range(50):
             fn()
         torch.cuda.synchronize()
         per = []
-        for _ in range(5):
+        for _ in range(9):
             t0 = time.perf_counter()
             for _ in range(host_reps):
                 fn()
