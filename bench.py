@@ -17,19 +17,30 @@ Prints ONE JSON line (rank 0).
   (from pinned host memory) and of its two outputs inside the timed region;
   consecutive steps are pipelined (copy-in, compute, copy-out on three streams
   over two device buffer sets).
-* roofline: the dominant kernel's achieved rate against its binding peak.
-* cpu_baseline: the FP64 CPU oracle (single thread) on a bounded sample.
+* roofline: the step kernel's algorithmic HBM bytes per launch over its
+  average launch time, against the measured HBM copy bandwidth; beside it an
+  "fp64" block: the binary64 operations the kernel executes per point (from its
+  ncu summary), their rate, and the GPU's FP64 FMA issue rate measured in the
+  same run by an FMA-chain probe kernel (the pipe that binds the column solve).
+* cpu_baseline: the FP64 CPU oracle on the host cores (one thread per J-slab,
+  every core the process may run on) on a bounded sample, with the
+  single-thread figure beside it.
 * precision: FP32 storage at 512x512x80 (binary32 hdiff; vadv in binary32,
-  binary64 and double-float column arithmetic) beside the FP64 path there.
+  binary64 and double-float column arithmetic) beside the FP64 path there,
+  with each form's error against the FP64 oracle (checked after the timing).
 * batched: the 48-member ensemble of uneven domains, autotuned plan replayed
-  from a CUDA graph vs the loop of single-domain launches.
+  from a CUDA graph vs the loop of single-domain launches, with its algorithmic
+  HBM bytes and their rate.
 * call_overhead: the paper's split of Python-call vs compiled-call time, for
-  one step on the small 64x64x40 workload (device time, C-ABI call, Python call).
+  one step on the small 64x64x40 workload (device time, C-ABI call, Python call),
+  and hdiff alone at 64x64x40 FP64 in microseconds.
 * fused_chain: the chained step (vadv of hdiff's output) as two launches vs
   gtb_hdiff_vadv, one kernel that keeps h on chip.
 * adjoint_forward_ratio: backward / forward time of one chained step
   (periodic halo + hdiff + vadv) through the adjoint kernels.
-* --impl reference: the oracle itself as the reference arm.
+* literal_chain: the 10-step chain at 256x256x80 FP64 with wcon ~ U(-0.5, 0.5)
+  as drawn, whose field grows without bound: max |field| after every step.
+* --impl reference: the oracle itself (all host cores) as the reference arm.
 Per-kernel times come from a second pass with an event around each kernel.
 Under torchrun every rank runs its own replica (independent problems, no
 collective): weak scaling.
@@ -58,7 +69,6 @@ POINTS = I * J * K
 HDIFF_HALO, VADV_HALO = 2, 1
 VADV_NAMES = ("u_stage", "wcon", "u_pos", "utens", "utens_stage")
 WORKLOAD = "hdiff+vadv FP64 256x256x80 (hdiff halo 2, vadv halo 1 in I/J), dtr_stage=3/20, beta_v=0"
-FP64_NOMINAL_GFLOPS = 1250.0  # B300 dense FP64, nominal (no FP64 tensor path is used)
 
 
 def hdiff_bytes(I, J, K, es):
@@ -71,9 +81,11 @@ def vadv_bytes(I, J, K, es):
     return es * (5 * I * J * K + (I + 1) * J * K)
 
 
-# FP64 operations per grid point as the definition states them (divisions count one each)
-HDIFF_FLOPS_PER_PT = 16  # lap 5, fx 3 (diff, gradient, product), fy 3, update 5
-VADV_FLOPS_PER_PT = 25   # face average 2, a 1, c 1, b 2, rhs 9, pivot 2, c' 1, d' 3, back-subst 2, out 2
+def batched_bytes(shapes, es):
+    """Compulsory HBM bytes of the batched form: per member, hdiff reads in on the domain
+    and its 2-ring and coeff and writes h; vadv reads h (as u_stage and u_pos), wcon on
+    I+1 columns, utens, utens_stage and writes out."""
+    return sum(es * ((I + 4) * (J + 4) * K + 7 * I * J * K + J * K) for I, J, K in shapes)
 
 
 def kernel_source_hash():
@@ -100,6 +112,48 @@ def profile_traffic(kernel):
         if m and t and m.group(1) == src:
             return float(t.group(1))
     return None
+
+
+def profile_field(kernel, pattern):
+    """A figure from the ncu summary of `kernel` (profiles/ncu_*.txt) captured on this
+    source, by regular expression (first group), or None."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    src = kernel_source_hash()
+    for n in sorted(os.listdir(pdir)):
+        if not n.endswith(".txt"):
+            continue
+        txt = open(os.path.join(pdir, n)).read()
+        m = re.search(r"^kernel_source_sha: (\w+)", txt, re.M)
+        t = re.search(r"^dram_bytes_per_launch\[%s\]" % kernel, txt, re.M)
+        v = re.search(pattern, txt, re.M)
+        if m and t and v and m.group(1) == src:
+            return float(v.group(1))
+    return None
+
+
+def fp64_fma_rate(reps=5):
+    """The GPU's binary64 FMA issue rate (G FMA/s): gtb_probe_fp64_fma, 8 resident CTAs of
+    256 threads per SM, each thread 8 independent FMA chains, timed with CUDA events;
+    best of `reps` launches of ~10 G FMAs."""
+    import torch
+    from paper_2311_08322_b300 import gtb
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    gtb.probe_fp64_fma(sms * 8, 64, sink, stream)
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n = gtb.probe_fp64_fma(sms * 8, 4096, sink, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, n / (a.elapsed_time(b) / 1e3))
+    gtb.device_status()
+    return best / 1e9
 
 
 def measured_peaks():
@@ -172,26 +226,109 @@ def whole_job_mpoints(world: int, points_per_rank: int, steps: int, max_ms: floa
     return world * points_per_rank * steps / (max_ms / 1e3) / 1e6
 
 
-def oracle_step(f, jrows=None):
-    """One oracle hdiff + vadv pass (optionally on the first `jrows` rows of J); returns points."""
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def oracle_slabs(fn, J_, n):
+    """Run fn(j0, nj) over n contiguous J-slabs of [0, J_) on n threads (the oracle's C
+    calls release the GIL, so the slabs run on n cores), returning when all are done."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = max(1, min(n, J_))
+    bounds = [(J_ * q // n, J_ * (q + 1) // n) for q in range(n)]
+    if n == 1:
+        fn(0, J_)
+        return
+    with ThreadPoolExecutor(n) as ex:
+        list(ex.map(lambda b: fn(b[0], b[1] - b[0]), bounds))
+
+
+def oracle_hdiff_par(inp, coeff, out, dom, threads):
+    """The oracle's hdiff, unchanged, on J-slabs of the domain in parallel (origin 2, 2, 0)."""
     import oracle
+    I_, J_, K_ = dom
+
+    def slab(j0, nj):
+        o = (2, 2 + j0, 0)
+        oracle.hdiff(inp, coeff, out, origin_in=o, origin_coeff=o, origin_out=o, domain=(I_, nj, K_))
+    oracle_slabs(slab, J_, threads)
+    return out
+
+
+def oracle_vadv_par(fields, out, dom, threads):
+    """The oracle's vadv, unchanged, on J-slabs of the domain in parallel (origin 1, 1, 0)."""
+    import oracle
+    I_, J_, K_ = dom
+
+    def slab(j0, nj):
+        oracle.vadv(*fields, out, origin=(1, 1 + j0, 0), domain=(I_, nj, K_))
+    oracle_slabs(slab, J_, threads)
+    return out
+
+
+def oracle_step(f, jrows=None, threads=1, outs=None):
+    """One oracle hdiff + vadv pass (optionally on the first `jrows` rows of J) on
+    `threads` J-slabs in parallel; returns points."""
     Jr = J if jrows is None else jrows
-    oracle.hdiff(f["in"], f["coeff"], domain=(I, Jr, K))
-    oracle.vadv(*[f[n] for n in VADV_NAMES], domain=(I, Jr, K))
+    ho, vo = outs if outs is not None else (np.zeros_like(f["coeff"]), np.zeros_like(f["utens"]))
+    oracle_hdiff_par(f["in"], f["coeff"], ho, (I, Jr, K), threads)
+    oracle_vadv_par([f[n] for n in VADV_NAMES], vo, (I, Jr, K), threads)
     return I * Jr * K
 
 
-def cpu_baseline(f, min_seconds=10.0):
-    """The oracle as it stands, one host thread, full 256x256x80 steps until >= min_seconds."""
+def cpu_rate(f, threads, min_seconds):
+    outs = (np.zeros_like(f["coeff"]), np.zeros_like(f["utens"]))
+    oracle_step(f, threads=threads, outs=outs)  # warm-up (page faults, thread start)
     reps, t0 = 0, time.perf_counter()
     while True:
-        oracle_step(f)
+        oracle_step(f, threads=threads, outs=outs)
         reps += 1
         el = time.perf_counter() - t0
         if el >= min_seconds and reps >= 2:
             break
-    return {"value": round(POINTS * reps / el / 1e6, 3), "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full hdiff+vadv steps at 256x256x80 FP64 ({el:.1f} s, single-threaded C oracle)"}
+    return POINTS * reps / el / 1e6, reps, el
+
+
+def cpu_baseline(f, precision=None, prec_outs=None, min_seconds=10.0):
+    """The oracle as it stands (C, binary64) on every host core this process may use, one
+    thread per J-slab: full 256x256x80 hdiff+vadv steps for >= min_seconds (the line's
+    value), the single-thread rate beside it, hdiff alone at 64x64x40 and one hdiff+vadv
+    pass at 512x512x80.  The 512x512x80 runs (FP64 inputs, and the same draws rounded to
+    FP32) also check the GPU outputs that the precision leg kept: each form's error is
+    written into that block."""
+    from paper_2311_08322_b300 import inputs
+    cores = host_cores()
+    v, reps, el = cpu_rate(f, cores, min_seconds)
+    v1, reps1, el1 = cpu_rate(f, 1, min_seconds / 2)
+    c1 = inputs.hdiff_small(0)
+    c1_out = np.zeros_like(c1["coeff"])
+    t0, n1 = time.perf_counter(), 0
+    while time.perf_counter() - t0 < 1.0:
+        oracle_hdiff_par(c1["in"], c1["coeff"], c1_out, (64, 64, 40), 1)
+        n1 += 1
+    c1_ms = (time.perf_counter() - t0) / n1 * 1e3
+    out = {"value": round(v, 3), "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+           "sample": f"{reps} full hdiff+vadv steps at 256x256x80 FP64 ({el:.1f} s), the C oracle on {cores} "
+                     f"threads, one J-slab each",
+           "single_thread": {"value": round(v1, 3), "unit": "Mpoints/s", "cores": 1,
+                             "sample": f"{reps1} full steps ({el1:.1f} s)"},
+           "hdiff_64x64x40_ms": round(c1_ms, 3)}
+    I3, J3, K3 = 512, 512, 80
+    f3 = inputs.hdiff_vadv(I3, J3, K3, seed=0)
+    for name, dt in (("fp64", np.float64), ("fp32", np.float32)):
+        fin = {k: a.astype(dt).astype(np.float64) for k, a in f3.items()}
+        t0 = time.perf_counter()
+        ref_h = oracle_hdiff_par(fin["in"], fin["coeff"], np.zeros_like(fin["coeff"]), (I3, J3, K3), cores)
+        ref_v = oracle_vadv_par([fin[n] for n in VADV_NAMES], np.zeros_like(fin["utens"]), (I3, J3, K3), cores)
+        if name == "fp64":
+            out["step_512x512x80_s"] = round(time.perf_counter() - t0, 3)
+        if precision is not None and prec_outs is not None and name in prec_outs:
+            errs = {}
+            for key, got in prec_outs[name].items():
+                ref = ref_h[:, 2:-2, 2:-2] if key == "hdiff" else ref_v[:, 1:-1, 1:-1]
+                errs[key] = field_errors(got, ref)
+            precision[name]["error_vs_fp64_oracle"] = errs
+    return out
 
 
 def run_reference(args):
@@ -202,18 +339,21 @@ def run_reference(args):
     import oracle
     oracle.build()
     f = inputs.hdiff_vadv(I, J, K, seed=0)
+    cores = host_cores()
+    outs = (np.zeros_like(f["coeff"]), np.zeros_like(f["utens"]))
     # size each step so that warmup + steps finish in about two minutes
+    oracle_step(f, jrows=min(J, 4 * cores), threads=cores, outs=outs)
     t0 = time.perf_counter()
-    oracle_step(f, jrows=16)
-    t16 = time.perf_counter() - t0
+    oracle_step(f, jrows=min(J, 4 * cores), threads=cores, outs=outs)
+    tq = time.perf_counter() - t0
     per_step_budget = 120.0 / max(1, args.steps + args.warmup)
-    jrows = int(max(1, min(J, 16 * per_step_budget / max(t16, 1e-6))))
+    jrows = int(max(1, min(J, min(J, 4 * cores) * per_step_budget / max(tq, 1e-6))))
     for _ in range(args.warmup):
-        oracle_step(f, jrows)
+        oracle_step(f, jrows, threads=cores, outs=outs)
     t0 = time.perf_counter()
     pts = 0
     for _ in range(args.steps):
-        pts += oracle_step(f, jrows)
+        pts += oracle_step(f, jrows, threads=cores, outs=outs)
     el = time.perf_counter() - t0
     v = pts / el / 1e6
     line = {"metric": METRIC, "value": round(v, 3), "unit": "Mpoints/s", "n_gpus": args.gpus,
@@ -221,8 +361,9 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "sample_rows_j": jrows},
-            "cpu_baseline": {"value": round(v, 3), "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: hdiff+vadv on 256x{jrows}x80 of the 256x256x80 fields"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: hdiff+vadv on 256x{jrows}x80 of the 256x256x80 fields, "
+                                       f"{cores} threads (one J-slab each)"},
             "e2e": {"value": round(v, 3), "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -386,34 +527,36 @@ def run_gtb(args):
 
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6400.0))
-    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs, torch copy)" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"
+    fma_gops = fp64_fma_rate() if rank == 0 else None
     kern = {}
     hb, vb = hdiff_bytes(I, J, K, 8), vadv_bytes(I, J, K, 8)
-    hf, vf = HDIFF_FLOPS_PER_PT * POINTS, VADV_FLOPS_PER_PT * POINTS
-    for name, ms, nbytes, flops in (("step", st_ms, hb + vb, hf + vf), ("hdiff", h_ms, hb, hf), ("vadv", v_ms, vb, vf)):
+    for name, ms, nbytes in (("step", st_ms, hb + vb), ("hdiff", h_ms, hb), ("vadv", v_ms, vb)):
         gbs = nbytes / (ms / 1e3) / 1e9
-        gfl = flops / (ms / 1e3) / 1e9
         kern[name] = {"ms": round(ms, 4), "mpoints_s": round(POINTS / (ms / 1e3) / 1e6, 1),
                       "algorithmic_bytes": nbytes, "hbm_gbs": round(gbs, 1),
-                      "frac_of_measured_hbm": round(gbs / hbm, 4), "frac_of_8tbs": round(gbs / 8000.0, 4),
-                      "fp64_gflops": round(gfl, 1), "frac_of_nominal_fp64": round(gfl / FP64_NOMINAL_GFLOPS, 4)}
+                      "frac_of_measured_hbm": round(gbs / hbm, 4), "frac_of_8tbs": round(gbs / 8000.0, 4)}
     kern["step"]["kernel"] = "hdiff_vadv_pair_kernel (hdiff and vadv co-scheduled in one launch)"
     kern["step"]["event_bracketed_ms"] = round(st_ev_ms, 4)
     kern["separate_step_ms"] = round(sep_ms, 4)
-    dom = "step"  # the step is one launch: the dominant (only) kernel of the timed region
-    kd = kern[dom]
+    kd = kern["step"]  # the step is one launch: the dominant (only) kernel of the timed region
     traffic = profile_traffic("hdiff_vadv_pair_kernel")
-    if kd["frac_of_nominal_fp64"] > kd["frac_of_measured_hbm"]:
-        roof = {"bound": "alu", "kernel": "hdiff_vadv_pair_kernel", "achieved": kd["fp64_gflops"],
-                "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s", "frac": kd["frac_of_nominal_fp64"],
-                "traffic": traffic,
-                "peak_source": "nominal B300 FP64 1.25 TFLOP/s (148 SMs); algorithmic FP64 flops of both "
-                               "stencils (hdiff 16/pt, vadv 25/pt)",
-                "hbm_frac_of_measured": kd["frac_of_measured_hbm"]}
-    else:
-        roof = {"bound": "hbm", "kernel": "hdiff_vadv_pair_kernel", "achieved": kd["hbm_gbs"], "peak": hbm,
-                "unit": "GB/s",
-                "frac": kd["frac_of_measured_hbm"], "traffic": traffic, "peak_source": hbm_src}
+    roof = {"bound": "hbm", "kernel": "hdiff_vadv_pair_kernel", "achieved": kd["hbm_gbs"], "peak": hbm,
+            "unit": "GB/s", "frac": kd["frac_of_measured_hbm"], "traffic": traffic, "peak_source": hbm_src,
+            "algorithmic_bytes_per_launch": hb + vb,
+            "note": "HBM fraction of the step kernel; the binary64 column solve binds it on the FP64 pipe (fp64 block)"}
+    ops = profile_field("hdiff_vadv_pair_kernel", r"^fp64 ops per domain point .* total ([0-9.]+)")
+    pipe = profile_field("hdiff_vadv_pair_kernel", r"^sm__pipe_fp64_cycles_active\S* = ([0-9.]+)")
+    fp64 = {"kernel": "hdiff_vadv_pair_kernel", "executed_ops_per_point": ops,
+            "ops_source": "ncu smsp__sass_thread_inst_executed_op_{dadd,dfma,dmul}_pred_on of the committed summary "
+                          "(null when the kernel changed since it was captured)",
+            "peak_gops": None if fma_gops is None else round(fma_gops, 1),
+            "peak_source": "gtb_probe_fp64_fma in this run: independent binary64 FMA chains, 8 CTAs x 256 threads "
+                           "per SM, CUDA events, best of 5 (DADD and DMUL issue on the same pipe at the same rate)",
+            "pipe_active_pct_ncu": pipe}
+    if ops is not None and fma_gops:
+        fp64["achieved_gops"] = round(ops * POINTS / (st_ms / 1e3) / 1e9, 1)
+        fp64["frac"] = round(fp64["achieved_gops"] / fma_gops, 4)
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "Mpoints/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el_ms / args.steps, 4),
@@ -422,19 +565,22 @@ def run_gtb(args):
             "config": {"workload": WORKLOAD, "I": I, "J": J, "K": K, "parallelism": f"replicas{world}",
                        "l2": f"{args.sets} rotating input sets of "
                              f"{(hdiff_bytes(I, J, K, 8) + vadv_bytes(I, J, K, 8)) / 1e6:.0f} MB each (> 126 MB L2)"},
-            "kernels": kern, "roofline": roof, "clocks": clk, "gpu_launches": args.steps,
+            "kernels": kern, "roofline": roof, "fp64": fp64, "clocks": clk, "gpu_launches": args.steps,
             "fused_chain": chain, "call_overhead": calls,
             "adjoint_forward_ratio": None if adj is None else adj["ratio"], "adjoint": adj,
             "e2e": {"value": round(e2e_value, 1), "unit": "Mpoints/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}}
+    prec_outs = None
     if rank == 0 and not args.no_precision:
-        line["precision"] = precision_compare()
+        line["precision"], prec_outs = precision_compare(hbm)
     if rank == 0 and not args.no_batched:
-        line["batched"] = batched_compare()
+        line["batched"] = batched_compare(hbm)
+    if rank == 0 and not args.no_adjoint:
+        line["literal_chain"] = literal_chain()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        line["cpu_baseline"] = cpu_baseline(f)
+        line["cpu_baseline"] = cpu_baseline(f, line.get("precision"), prec_outs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -474,6 +620,11 @@ def call_overhead(reps=2000, host_reps=64):
     def py_call():
         gtb.step(*args, domain=dom, stream=stream)
 
+    # the timed bursts discard the return code: check once that the call enqueues work
+    rc = lib.gtb_step(*refs, 0.15, 0.0, 0, 0, c_dom, c_ws, nbytes, c_st)
+    if rc != 0:
+        raise RuntimeError(f"gtb_step failed in call_overhead: {rc} {lib.gtb_last_error().decode()}")
+    gtb.device_status()
     out = {"workload": "one hdiff+vadv step (gtb_step) at 64x64x40 FP64"}
     # host time per call over bursts short enough that the launch queue never fills (a
     # full queue makes the host wait for the device inside the timed region: bursts of
@@ -497,6 +648,15 @@ def call_overhead(reps=2000, host_reps=64):
     b.record(stream)
     torch.cuda.synchronize()
     out["device_us_per_step"] = round(a.elapsed_time(b) / reps * 1e3, 2)
+    # hdiff alone at 64x64x40 FP64 (its launch-bound smallest configuration)
+    for _ in range(20):
+        gtb.hdiff(s["in"], s["coeff"], s["hout"], stream=stream)
+    a.record(stream)
+    for _ in range(reps):
+        gtb.hdiff(s["in"], s["coeff"], s["hout"], stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["hdiff_64x64x40_fp64_us"] = round(a.elapsed_time(b) / reps * 1e3, 2)
     gtb.device_status()
     return out
 
@@ -592,7 +752,29 @@ def adjoint_ratio(gtb, f, sets, reps=50):
                         "column factors vs the adjoints)"}
 
 
-def batched_compare(reps=20):
+def literal_chain(steps=10):
+    """The 10-step chain at 256x256x80 FP64 exactly as drawn (wcon ~ U(-0.5, 0.5), seed 0):
+    field <- vadv(hdiff(field)) with the periodic 2-point halo, forward only.  Its
+    ill-conditioned columns amplify the field every step; the line records max |field|
+    after each step (the gradient checks draw wcon from U(-0.3, 0.3) instead)."""
+    import torch
+    from paper_2311_08322_b300.autograd import chain, chain_inputs
+    field, coeff, fixed, _ = chain_inputs(I, J, K, seed=0, dtype=torch.float64, wcon_amp=0.5)
+    fixed.save_factors = False
+    growth = []
+    with torch.no_grad():
+        x = field
+        for _ in range(steps):
+            x = chain(x, coeff, fixed, 1)
+            growth.append(float(x.abs().max()))
+    from paper_2311_08322_b300 import gtb
+    gtb.device_status()
+    return {"workload": "10-step chain field <- vadv(hdiff(field)) at 256x256x80 FP64, wcon ~ U(-0.5, 0.5) (seed 0), "
+                        "periodic halo", "max_abs_per_step": [float(f"{g:.4e}") for g in growth],
+            "initial_max_abs": round(float(field.abs().max()), 4)}
+
+
+def batched_compare(hbm, reps=20):
     """The batched form: a 48-member ensemble of uneven domains (I=J in
     {48..384}, K in {40, 60, 80, 137}, seed-fixed), FP32 storage with
     double-float vadv, each member hdiff then vadv (h fed to vadv as u_stage and
@@ -629,19 +811,34 @@ def batched_compare(reps=20):
     info = plan.info()
     pts = info["points"]
     plan.close()
+    nbytes = batched_bytes(shapes, 4)
+    gbs = nbytes / (g_ms / 1e3) / 1e9
     return {"workload": "48-member ensemble, I=J in {48,96,128,192,256,384}, K in {40,60,80,137}, FP32 storage, "
                         "double-float vadv", "points": pts, "graph_ms": round(g_ms, 4), "loop_ms": round(l_ms, 4),
             "speedup_vs_loop": round(l_ms / g_ms, 3), "mpoints_s": round(pts / (g_ms / 1e3) / 1e6, 1),
+            "algorithmic_bytes": nbytes, "hbm_gbs": round(gbs, 1), "frac": round(gbs / hbm, 4),
             "config": cfg, "autotune_cached": log.get("cached"), "launches_graph": 2,
             "launches_loop": 2 * len(members)}
 
 
-def precision_compare(reps=20):
+def field_errors(got, ref):
+    """Max-norm relative error and the worst column's relative error of one output field."""
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    d = np.abs(got - ref)
+    den = np.max(np.abs(ref))
+    col = np.max(d, axis=0) / np.maximum(np.max(np.abs(ref), axis=0), 1e-300)
+    return {"max_norm": float(f"{float(d.max() / (den if den > 0 else 1.0)):.3e}"),
+            "worst_column": float(f"{float(col.max()):.3e}")}
+
+
+def precision_compare(hbm, reps=20):
     """The precision form at 512x512x80 (same generators): FP32 storage with binary32
     hdiff and vadv in its three column-arithmetic forms (binary32, binary64 on the
     FP64 pipe, double-float on the FP32 pipe), beside the FP64 path at the same size
-    on the same GPU.  Two input sets alternate (each larger than L2).  The error of
-    each form against the FP64 oracle is measured by tests/test_gpu_precision.py."""
+    on the same GPU.  Two input sets alternate (each larger than L2).  After the timing,
+    every form's outputs are kept on the host; the cpu_baseline leg, which runs the FP64
+    oracle on this workload (on the inputs the GPU saw: FP32-rounded for the FP32 forms),
+    adds each form's error (max-norm and worst column per output field)."""
     import torch
     from paper_2311_08322_b300 import gtb, inputs
     I3, J3, K3 = 512, 512, 80
@@ -675,6 +872,7 @@ def precision_compare(reps=20):
 
     pts = I3 * J3 * K3
     res = {"workload": "hdiff + vadv at 512x512x80 (same generators as the FP64 path)"}
+    outs = {}
     for name, dt in (("fp64", np.float64), ("fp32", np.float32)):
         sets = make(dt)
         es = 8 if dt == np.float64 else 4
@@ -686,15 +884,28 @@ def precision_compare(reps=20):
         r["hdiff_gbs"] = round(hdiff_bytes(I3, J3, K3, es) / (r["hdiff_ms"] / 1e3) / 1e9, 1)
         for pr in precs:
             r[f"vadv_{pr}_gbs"] = round(vadv_bytes(I3, J3, K3, es) / (r[f"vadv_{pr}_ms"] / 1e3) / 1e9, 1)
+        r["hdiff_frac_of_measured_hbm"] = round(r["hdiff_gbs"] / hbm, 4)
+        for pr in precs:
+            r[f"vadv_{pr}_frac_of_measured_hbm"] = round(r[f"vadv_{pr}_gbs"] / hbm, 4)
         best_v = min(r[f"vadv_{pr}_ms"] for pr in precs if pr != "native" or dt == np.float64)
         r["step_mpoints_s"] = round(pts / ((r["hdiff_ms"] + best_v) / 1e3) / 1e6, 1)
         res[name] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+        # the outputs of one more call of every form, kept on the host: the cpu_baseline leg
+        # checks them against the oracle (its 512x512x80 runs) after all GPU timing
+        st = sets[0]
+        gtb.hdiff(st["in"], st["coeff"], st["hout"])
+        kept = {"hdiff": st["hout"].numpy()[:, 2:-2, 2:-2]}
+        for pr in precs:
+            gtb.vadv(*[st[n] for n in VADV_NAMES], st["vout"], prec=pr)
+            kept[f"vadv_{pr}"] = st["vout"].numpy()[:, 1:-1, 1:-1]
+        gtb.device_status()
+        outs[name] = kept
         del sets
         torch.cuda.empty_cache()
     gtb.device_status()
     res["note"] = ("fp32 step uses the fastest vadv form that meets the 1e-5 bound (f64 or df); all-binary32 vadv "
                    "does not meet it on ill-conditioned columns")
-    return res
+    return res, outs
 
 
 def main():

@@ -317,8 +317,11 @@ int gtb_plan_destroy(gtb_plan *plan);
  *  - a domain whose workspace (gtb_vadv_workspace_bytes) exceeds 16 MiB
  *    (1,048,576 points for GTB_F64 storage) is rejected with
  *    GTB_ERR_UNSUPPORTED and nothing is enqueued;
- *  - the first call on a device looks up the array's device address on that
- *    device (make it before any stream capture);
+ *  - every call looks up the array's device address in the current device's
+ *    context (cudaGetSymbolAddress, which allocates nothing), so a context
+ *    that was reset and re-created is never handed a stale address; the
+ *    first call on a device may also load the library's kernels there, so
+ *    make that first call before any stream capture;
  *  - every call on a device shares the one array, and its contents carry
  *    over between calls (nothing needs to start at zero): calls that may
  *    overlap on the GPU (different streams, or other threads) race and must
@@ -347,6 +350,17 @@ int gtb_device_status(void *stream);
  * first and nothing is reported.  Bad arguments: GTB_ERR_ARG.
  */
 int gtb_selftest_wait(long long limit_ns, int arrive, void *stream);
+
+/*
+ * gtb_probe_fp64_fma -- a measurement kernel, not a step of the method (the
+ * paper has no counterpart): `blocks` CTAs of 256 threads, each thread running
+ * 8 independent binary64 FMA chains of `iters` FMAs, i.e. blocks * 256 * 8 *
+ * iters FMA instructions.  Timed by the caller (CUDA events on `stream`), it
+ * gives the GPU's FP64 FMA issue rate, the peak that the binary64 column solve
+ * is reported against.  `sink`: 8 bytes of device memory, never written in
+ * practice.  Bad arguments: GTB_ERR_ARG / GTB_ERR_NULL / GTB_ERR_LAYOUT.
+ */
+int gtb_probe_fp64_fma(int blocks, int iters, void *sink, void *stream);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char *gtb_last_error(void);

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(32 * W)
         const int m = member_of(mem, n_mem, item);
         const BatchHdiffMember<T> M = mem[m];
         const int local = item - M.item0;
-        hdiff_rs_item<T, CPL, W, R, STAGES, true, FIXED>(&maps[m], M.in, M.coeff, M.out, M.g, M.vec_ok,
+        hdiff_rs_item<T, CPL, W, R, STAGES, true, FIXED>(&maps[m], &maps[m], M.in, M.coeff, M.out, M.g, M.vec_ok,
                                                           local % M.g.n_tiles, local / M.g.n_tiles, base, bars);
     }
 }

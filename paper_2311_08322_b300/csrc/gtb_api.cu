@@ -22,6 +22,7 @@
 #include "adjoint_kernels.cuh"
 #include "batch_kernels.cuh"
 #include "fused_kernels.cuh"
+#include "probe_kernels.cuh"
 
 namespace gtb {
 
@@ -236,17 +237,20 @@ template <> struct HdiffCfg<double> {  // 64 x 64 tile, 4 warps of 16 rows, 2 co
 template <> struct HdiffCfg<float> {   // 128 x 64 tile, 8 warps of 8 rows, 4 columns per lane
     static constexpr int CPL = 4, W = 8, R = 8, STAGES = 2;
 };
+// binary32 with coeff staged by TMA beside in (when coeff's layout allows a tensor map)
+struct HdiffF32CoeffTmaCfg {
+    static constexpr int CPL = 4, W = 4, R = 8, STAGES = 2;
+};
 
-template <typename T, bool TMA>
-static int launch_hdiff_t(const CUtensorMap &map, const View<T> &in, const View<T> &cf, const View<T> &out,
-                          HdiffGeom g, int vec_ok, cudaStream_t st) {
-    using C = HdiffCfg<T>;
+template <typename T, bool TMA, typename C = HdiffCfg<T>, bool CTMA = false>
+static int launch_hdiff_t(const CUtensorMap &map, const CUtensorMap &cmap, const View<T> &in, const View<T> &cf,
+                          const View<T> &out, HdiffGeom g, int vec_ok, cudaStream_t st) {
     constexpr int STG = TMA ? C::STAGES : 1;
     // binary64: exact fixed-point lap/flux chain on the integer pipe; binary32: the definition
     constexpr bool FIXED = sizeof(T) == 8;
-    constexpr int smem = hdiff_rs_smem_bytes<T, C::CPL, C::W, C::R, STG>();
+    constexpr int smem = hdiff_rs_smem_bytes<T, C::CPL, C::W, C::R, STG, CTMA>();
     constexpr int NT = 32 * C::W;
-    auto kern = hdiff_rs_kernel<T, C::CPL, C::W, C::R, STG, TMA, FIXED>;
+    auto kern = hdiff_rs_kernel<T, C::CPL, C::W, C::R, STG, TMA, FIXED, CTMA>;
     if (prepare_kernel(kern, smem) != cudaSuccess) return launch_status("hdiff: shared-memory attribute");
     static int slots_cache[64] = {0};
     const int dev = current_device();
@@ -259,8 +263,37 @@ static int launch_hdiff_t(const CUtensorMap &map, const View<T> &in, const View<
     const int chunks = std::max(1, std::min(g.K, slots / std::max(1, g.n_tiles)));
     g.kc = (g.K + chunks - 1) / chunks;
     const int items = g.n_tiles * ((g.K + g.kc - 1) / g.kc);
-    kern<<<items, NT, smem, st>>>(map, in, cf, out, g, vec_ok);
+    kern<<<items, NT, smem, st>>>(map, cmap, in, cf, out, g, vec_ok);
     return launch_status("hdiff launch");
+}
+
+// TMA descriptor of coeff for (bx x by x 1) boxes whose corner is a tile's first domain
+// point: the tile corner's i coordinate must start on a 16-byte boundary (every tile's
+// does when the domain's first point does, tiles being multiples of 16 bytes wide).
+// Sets g.CX0/CY0/CZ0; false when the layout, the alignment or the driver rules it out.
+template <typename T>
+static bool encode_coeff_map(const gtb_field *fc, int bx, int by, HdiffGeom &g, CUtensorMap &map) {
+    const size_t es = sizeof(T);
+    const uintptr_t base = reinterpret_cast<uintptr_t>(fc->ptr);
+    const uintptr_t abase = base & ~uintptr_t(15);
+    const int shift = (int)((base - abase) / es);
+    constexpr int kAlign = 16 / (int)sizeof(T);
+    const int x0 = (int)fc->origin[0] + shift;
+    bool ok = encode_fn() != nullptr && (fc->strides[1] * es) % 16 == 0 && (fc->strides[2] * es) % 16 == 0 &&
+              fc->strides[2] * es < (1ull << 40) && fc->shape[0] + shift < (1ll << 31) && x0 % kAlign == 0 &&
+              (bx * (int)es) % 16 == 0;
+    memset(&map, 0, sizeof(map));
+    if (!ok) return false;
+    g.CX0 = x0, g.CY0 = (int)fc->origin[1], g.CZ0 = (int)fc->origin[2];
+    cuuint64_t gdim[3] = {(cuuint64_t)(fc->shape[0] + shift), (cuuint64_t)fc->shape[1], (cuuint64_t)fc->shape[2]};
+    cuuint64_t gstride[2] = {(cuuint64_t)(fc->strides[1] * es), (cuuint64_t)(fc->strides[2] * es)};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&map, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                             reinterpret_cast<void *>(abase), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 // TMA descriptor of hdiff's input for a (bx x by x 1) box whose column 0 is
@@ -297,27 +330,42 @@ static bool encode_in_map(const gtb_field *fin, int bx, int by, HdiffGeom &g, CU
     return tma;
 }
 
-template <typename T>
-static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field *fout, const int64_t dom[3],
-                     cudaStream_t st) {
-    using C = HdiffCfg<T>;
+template <typename T, typename C>
+static HdiffGeom hdiff_geom(const int64_t dom[3]) {
     using Tile = RsTile<T, C::CPL, C::W, C::R>;
-    const View<T> in = view_of<T>(fin), cf = view_of<T>(fcf), out = view_of<T>(fout);
     HdiffGeom g{};
     g.I = (int)dom[0], g.J = (int)dom[1], g.K = (int)dom[2];
     g.tiles_i = (g.I + Tile::TI - 1) / Tile::TI;
     g.tiles_j = (g.J + Tile::TJ - 1) / Tile::TJ;
     g.n_tiles = g.tiles_i * g.tiles_j;
+    return g;
+}
 
-    CUtensorMap map;
-    const bool tma = encode_in_map<T>(fin, Tile::BX, Tile::BY, g, map);
+template <typename T>
+static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field *fout, const int64_t dom[3],
+                     cudaStream_t st) {
+    const View<T> in = view_of<T>(fin), cf = view_of<T>(fcf), out = view_of<T>(fout);
     const size_t es = sizeof(T);
     auto aligned = [&](const View<T> &v) {
         return reinterpret_cast<uintptr_t>(v.p) % 16 == 0 && (v.sj * es) % 16 == 0 && (v.sk * es) % 16 == 0;
     };
+    CUtensorMap map, cmap;
+    if constexpr (sizeof(T) == 4) {
+        // binary32: in and coeff both by TMA when both layouts allow it, out by vector stores
+        using C = HdiffF32CoeffTmaCfg;
+        using Tile = RsTile<T, C::CPL, C::W, C::R, true>;
+        HdiffGeom g = hdiff_geom<T, C>(dom);
+        if (aligned(out) && encode_in_map<T>(fin, Tile::BX, Tile::BY, g, map) &&
+            encode_coeff_map<T>(fcf, Tile::TI, Tile::TJ, g, cmap))
+            return launch_hdiff_t<T, true, C, true>(map, cmap, in, cf, out, g, 1, st);
+    }
+    using C = HdiffCfg<T>;
+    using Tile = RsTile<T, C::CPL, C::W, C::R>;
+    HdiffGeom g = hdiff_geom<T, C>(dom);
+    const bool tma = encode_in_map<T>(fin, Tile::BX, Tile::BY, g, map);
     const int vec = (aligned(cf) && aligned(out)) ? 1 : 0;
-    return tma ? launch_hdiff_t<T, true>(map, in, cf, out, g, vec, st)
-               : launch_hdiff_t<T, false>(map, in, cf, out, g, vec, st);
+    return tma ? launch_hdiff_t<T, true>(map, map, in, cf, out, g, vec, st)
+               : launch_hdiff_t<T, false>(map, map, in, cf, out, g, vec, st);
 }
 
 // ------------------------------------------------------------------ vadv
@@ -769,6 +817,16 @@ extern "C" int gtb_selftest_wait(long long limit_ns, int arrive, void *stream) {
     return launch_status("gtb_selftest_wait launch");
 }
 
+extern "C" int gtb_probe_fp64_fma(int blocks, int iters, void *sink, void *stream) {
+    if (blocks < 1 || blocks > (1 << 20) || iters < 1 || iters > (1 << 24))
+        return fail(GTB_ERR_ARG, "gtb_probe_fp64_fma: blocks %d or iters %d out of range", blocks, iters);
+    if (!sink) return fail(GTB_ERR_NULL, "gtb_probe_fp64_fma: NULL sink");
+    if (reinterpret_cast<uintptr_t>(sink) % 8 != 0) return fail(GTB_ERR_LAYOUT, "gtb_probe_fp64_fma: sink not 8-byte aligned");
+    fp64_fma_probe_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(iters, 0.999999, 1e-7,
+                                                                                static_cast<double *>(sink));
+    return launch_status("gtb_probe_fp64_fma launch");
+}
+
 extern "C" const char *gtb_last_error(void) { return t_err; }
 
 extern "C" const char *gtb_version(void) { return "gtb 0.1 sm_103a"; }
@@ -778,33 +836,24 @@ extern "C" const char *gtb_version(void) { return "gtb 0.1 sm_103a"; }
 // library instead of caller memory (declared in include/gtb.h; the paper has no
 // counterpart).  The array is a file-scope __device__ variable, so it exists
 // on every GPU that loads the library, from load until exit, and no call ever
-// allocates.  Host code cannot use the array's name as a device address: the
-// address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, on the first call made there.
+// allocates.  Host code cannot use the array's name as a device address: every
+// call looks the address up with cudaGetSymbolAddress on the current device.
+// The lookup allocates nothing and is not cached, so a context torn down and
+// re-created (cudaDeviceReset by this or another library), in which the array
+// may sit at another address, never receives a stale pointer.
 namespace gtb {
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char g_vadv_noalloc_scratch[kNoAllocScratchBytes];
 
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_ptr[64] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array in the current device's context.
 static int noalloc_scratch(void **ptr) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(GTB_ERR_LAUNCH, "gtb_vadv_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= 64) return fail(GTB_ERR_UNSUPPORTED, "gtb_vadv_noalloc: device ordinal %d >= 64", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_vadv_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(GTB_ERR_LAUNCH, "gtb_vadv_noalloc: cudaGetSymbolAddress of the scratch array failed: %s",
-                        cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = p;
-    }
-    *ptr = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_vadv_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(GTB_ERR_LAUNCH, "gtb_vadv_noalloc: cudaGetSymbolAddress of the scratch array failed: %s",
+                    cudaGetErrorString(e));
+    *ptr = p;
     return GTB_OK;
 }
 

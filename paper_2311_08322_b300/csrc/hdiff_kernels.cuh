@@ -32,6 +32,7 @@ struct HdiffGeom {
     int kc;          // K levels per work item
     int X0, Y0, Z0;  // tensor-map coordinate of box column/row 0 for tile (0,0), level 0
     int xs;          // box column of domain i = -2 (alignment shift, < 16/sizeof(T))
+    int CX0, CY0, CZ0;  // coeff tensor-map coordinate of domain point (0,0,0) (coeff staged by TMA)
     int int_update;  // co-scheduled / fused producers: the update on the integer pipe (FixedF64T<true>::outx)
 };
 

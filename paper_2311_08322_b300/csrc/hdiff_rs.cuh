@@ -93,7 +93,9 @@ struct FixedF64T {
 };
 using FixedF64 = FixedF64T<false>;
 
-template <typename T, int CPL, int W, int R>
+// Stage layout: the level's `in` box, then (CTMA) the tile's coeff block of TI x TJ
+// values, which the same TMA transaction brings in (one mbarrier per stage).
+template <typename T, int CPL, int W, int R, bool CTMA = false>
 struct RsTile {
     static constexpr int TI = 32 * CPL, TJ = W * R;
     static constexpr int kAlign = 16 / (int)sizeof(T);
@@ -101,19 +103,23 @@ struct RsTile {
     static constexpr int BY = TJ + 4;
     static constexpr int box_elems = BX * BY;
     static constexpr int box_bytes = box_elems * (int)sizeof(T);
-    static constexpr int stage_stride = ((box_bytes + 127) / 128) * 128;
+    static constexpr int cf_offset = ((box_bytes + 127) / 128) * 128;
+    static constexpr int cf_bytes = CTMA ? TI * TJ * (int)sizeof(T) : 0;
+    static constexpr int tx_bytes = box_bytes + cf_bytes;
+    static constexpr int stage_stride = ((cf_offset + cf_bytes + 127) / 128) * 128;
 };
 
-template <typename T, int CPL, int W, int R, int STAGES>
+template <typename T, int CPL, int W, int R, int STAGES, bool CTMA = false>
 constexpr int hdiff_rs_smem_bytes() {
-    return STAGES * RsTile<T, CPL, W, R>::stage_stride + STAGES * 8 + 128;
+    return STAGES * RsTile<T, CPL, W, R, CTMA>::stage_stride + STAGES * 8 + 128;
 }
 
 // One warp's R-row strip of one level.  S: the level's box; bx(ci) = ci+2+xs,
 // by(cj) = cj+2 (tile-relative ci, cj).  cf: this lane's coeff rows.
 template <typename T, int CPL, int R, int BX, typename P>
 __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int cj0, int ncols, int nrows,
-                                         const T *cfp, int64_t cf_sj, T *op, int64_t out_sj, bool vec_ok) {
+                                         const T *cfp, int64_t cf_sj, T *op, int64_t out_sj, bool cf_vec,
+                                         bool vec_ok) {
     using V = typename P::V;
     using Gd = typename P::Gd;
     const int lane = threadIdx.x & 31;
@@ -166,7 +172,7 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
     auto load_cf = [&](int rw, T (&v)[CPL]) {
         if (rw >= 0 && rw < nrows) {
             const T *c = cfp + (int64_t)(cj0 + rw) * cf_sj;
-            if (vec_ok && ncols == CPL) {
+            if (cf_vec && ncols == CPL) {
                 load_vec<T, CPL>(c, v);
                 return;
             }
@@ -262,11 +268,16 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
 
 // One work item: tile `tile` of the launch geometry g, K-chunk `kchunk`.
 // Block-uniform; the caller provides the shared-memory stages and barriers.
-template <typename T, int CPL, int W, int R, int STAGES, bool USE_TMA, bool FIXED>
-__device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const View<T> &in, const View<T> &coeff,
-                                              const View<T> &out, const HdiffGeom &g, int vec_ok, int tile,
-                                              int kchunk, unsigned char *base, uint64_t *bars) {
-    using G = RsTile<T, CPL, W, R>;
+// CTMA (with USE_TMA): coeff arrives with each level's box by a second tiled
+// TMA load (cmap, box TI x TJ at g.CX0 + ti0, g.CY0 + tj0, g.CZ0 + k) instead
+// of being loaded from global memory row by row inside the strip.
+template <typename T, int CPL, int W, int R, int STAGES, bool USE_TMA, bool FIXED, bool CTMA = false>
+__device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const CUtensorMap *cmap, const View<T> &in,
+                                              const View<T> &coeff, const View<T> &out, const HdiffGeom &g,
+                                              int vec_ok, int tile, int kchunk, unsigned char *base,
+                                              uint64_t *bars) {
+    static_assert(!CTMA || USE_TMA, "coeff by TMA needs the TMA ring");
+    using G = RsTile<T, CPL, W, R, CTMA>;
     constexpr int NT = 32 * W;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ti0 = (tile % g.tiles_i) * G::TI, tj0 = (tile / g.tiles_i) * G::TJ;
@@ -279,18 +290,22 @@ __device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const Vie
     const int ncols = max(0, min(CPL, g.I - ti0 - lane * CPL));
 
     // TMA ring: (re)initialised per item; no load is in flight between items
+    auto issue = [&](int s, int k) {  // one level's box (and coeff block) into stage s
+        mbar_arrive_expect_tx(&bars[s], G::tx_bytes);
+        tma_load_3d(base + s * G::stage_stride, tmap, &bars[s], g.X0 + ti0, g.Y0 + tj0, g.Z0 + k);
+        if constexpr (CTMA)
+            tma_load_3d(base + s * G::stage_stride + G::cf_offset, cmap, &bars[s], g.CX0 + ti0, g.CY0 + tj0, g.CZ0 + k);
+    };
     if (USE_TMA) {
         if (tid == 0) {
             prefetch_tensormap(tmap);
+            if constexpr (CTMA) prefetch_tensormap(cmap);
             for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
             fence_mbar_init();
         }
         __syncthreads();
         if (tid == 0)
-            for (int p = 0; p < STAGES && p < nk; ++p) {
-                mbar_arrive_expect_tx(&bars[p], G::box_bytes);
-                tma_load_3d(base + p * G::stage_stride, tmap, &bars[p], g.X0 + ti0, g.Y0 + tj0, g.Z0 + k0 + p);
-            }
+            for (int p = 0; p < STAGES && p < nk; ++p) issue(p, k0 + p);
     }
     bool failed = false;
     for (int p = 0; p < nk; ++p) {
@@ -312,7 +327,12 @@ __device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const Vie
         }
         if (__syncthreads_or(failed)) break;
         if (nrows > 0) {
-            const T *cfp = coeff.p + (int64_t)(ti0 + lane * CPL) + (int64_t)tj0 * coeff.sj + (int64_t)k * coeff.sk;
+            // this lane's coeff at tile row 0: the staged block (row pitch TI) or global memory
+            const T *cfp = CTMA ? reinterpret_cast<const T *>(reinterpret_cast<const unsigned char *>(S) + G::cf_offset) +
+                                      lane * CPL
+                                : coeff.p + (int64_t)(ti0 + lane * CPL) + (int64_t)tj0 * coeff.sj + (int64_t)k * coeff.sk;
+            const int64_t cf_sj = CTMA ? (int64_t)G::TI : coeff.sj;
+            const int cf_vec = CTMA ? 1 : vec_ok;
             T *op = out.p + (int64_t)(ti0 + lane * CPL) + (int64_t)tj0 * out.sj + (int64_t)k * out.sk;
             if constexpr (FIXED) {
                 // largest biased exponent over the values the strip's stored outputs read:
@@ -342,22 +362,18 @@ __device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const Vie
                 }
                 const int E = (int)__reduce_max_sync(0xffffffffu, emax);
                 if (E >= 64 && E <= 2040)
-                    rs_strip<T, CPL, R, G::BX>(FixedF64{E}, S, xs, cj0, ncols, nrows, cfp, coeff.sj, op, out.sj,
-                                               vec_ok != 0);
+                    rs_strip<T, CPL, R, G::BX>(FixedF64{E}, S, xs, cj0, ncols, nrows, cfp, cf_sj, op, out.sj,
+                                               cf_vec != 0, vec_ok != 0);
                 else
-                    rs_strip<T, CPL, R, G::BX>(Native<T>{}, S, xs, cj0, ncols, nrows, cfp, coeff.sj, op, out.sj,
-                                               vec_ok != 0);
+                    rs_strip<T, CPL, R, G::BX>(Native<T>{}, S, xs, cj0, ncols, nrows, cfp, cf_sj, op, out.sj,
+                                               cf_vec != 0, vec_ok != 0);
             } else {
-                rs_strip<T, CPL, R, G::BX>(Native<T>{}, S, xs, cj0, ncols, nrows, cfp, coeff.sj, op, out.sj,
-                                           vec_ok != 0);
+                rs_strip<T, CPL, R, G::BX>(Native<T>{}, S, xs, cj0, ncols, nrows, cfp, cf_sj, op, out.sj,
+                                           cf_vec != 0, vec_ok != 0);
             }
         }
         __syncthreads();  // every warp is done with this stage
-        if (USE_TMA && tid == 0 && p + STAGES < nk) {
-            const int s = p % STAGES;
-            mbar_arrive_expect_tx(&bars[s], G::box_bytes);
-            tma_load_3d(base + s * G::stage_stride, tmap, &bars[s], g.X0 + ti0, g.Y0 + tj0, g.Z0 + k + STAGES);
-        }
+        if (USE_TMA && tid == 0 && p + STAGES < nk) issue(p % STAGES, k + STAGES);
     }
     if (USE_TMA && failed) {
         if (tid == 0)
@@ -366,24 +382,25 @@ __device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const Vie
     }
 }
 
-template <typename T, int CPL, int W, int R, int STAGES>
+template <typename T, int CPL, int W, int R, int STAGES, bool CTMA = false>
 __device__ __forceinline__ unsigned char *hdiff_rs_smem(uint64_t **bars) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    *bars = reinterpret_cast<uint64_t *>(base + STAGES * RsTile<T, CPL, W, R>::stage_stride);
+    *bars = reinterpret_cast<uint64_t *>(base + STAGES * RsTile<T, CPL, W, R, CTMA>::stage_stride);
     return base;
 }
 
 // Single domain: one CTA per (tile, K-chunk) item.
-template <typename T, int CPL, int W, int R, int STAGES, bool USE_TMA, bool FIXED>
+template <typename T, int CPL, int W, int R, int STAGES, bool USE_TMA, bool FIXED, bool CTMA = false>
 __global__ void __launch_bounds__(32 * W)
-    hdiff_rs_kernel(const __grid_constant__ CUtensorMap tmap, const View<T> in, const View<T> coeff,
-                    const View<T> out, const HdiffGeom g, const int vec_ok) {
+    hdiff_rs_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap cmap,
+                    const View<T> in, const View<T> coeff, const View<T> out, const HdiffGeom g, const int vec_ok) {
     uint64_t *bars;
-    unsigned char *base = hdiff_rs_smem<T, CPL, W, R, STAGES>(&bars);
-    hdiff_rs_item<T, CPL, W, R, STAGES, USE_TMA, FIXED>(&tmap, in, coeff, out, g, vec_ok, blockIdx.x % g.n_tiles,
-                                                         blockIdx.x / g.n_tiles, base, bars);
+    unsigned char *base = hdiff_rs_smem<T, CPL, W, R, STAGES, CTMA>(&bars);
+    hdiff_rs_item<T, CPL, W, R, STAGES, USE_TMA, FIXED, CTMA>(&tmap, &cmap, in, coeff, out, g, vec_ok,
+                                                               blockIdx.x % g.n_tiles, blockIdx.x / g.n_tiles, base,
+                                                               bars);
 }
 
 }  // namespace gtb

@@ -55,8 +55,8 @@ _lib = None
 EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_hdiff_adj", "gtb_vadv_adj",
            "gtb_vadv_adj_workspace_bytes", "gtb_halo_periodic", "gtb_halo_periodic_adj", "gtb_device_status",
            "gtb_batch_plan", "gtb_batch_run", "gtb_plan_info", "gtb_plan_destroy", "gtb_hdiff_vadv",
-           "gtb_hdiff_vadv_workspace_bytes", "gtb_step", "gtb_selftest_wait", "gtb_last_error",
-           "gtb_version")
+           "gtb_hdiff_vadv_workspace_bytes", "gtb_step", "gtb_selftest_wait", "gtb_probe_fp64_fma",
+           "gtb_vadv_noalloc", "gtb_last_error", "gtb_version")
 GTB_ADJ_ACCUMULATE = 2
 GTB_SAVE_FACTORS = 4
 GTB_ADJ_FACTORS = 8
@@ -104,6 +104,11 @@ def lib() -> ctypes.CDLL:
         L.gtb_device_status.argtypes = [vp]
         L.gtb_selftest_wait.argtypes = [ctypes.c_longlong, ctypes.c_int, vp]
         L.gtb_selftest_wait.restype = ctypes.c_int
+        L.gtb_probe_fp64_fma.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp]
+        L.gtb_probe_fp64_fma.restype = ctypes.c_int
+        L.gtb_vadv_noalloc.argtypes = [P, P, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_uint, i64p, vp]
+        L.gtb_vadv_noalloc.restype = ctypes.c_int
         L.gtb_last_error.restype = ctypes.c_char_p
         L.gtb_version.restype = ctypes.c_char_p
         for n in ("gtb_hdiff", "gtb_vadv", "gtb_device_status"):
@@ -393,6 +398,13 @@ def selftest_wait(limit_ns: int, arrive: bool, stream=None):
     """Exercise the bounded-wait failure path (gtb_selftest_wait): with arrive=False the
     wait runs out after limit_ns and device_status() then raises GTB_ERR_DEVICE."""
     _check(lib().gtb_selftest_wait(int(limit_ns), 1 if arrive else 0, _stream(stream)))
+
+
+def probe_fp64_fma(blocks: int, iters: int, sink: torch.Tensor, stream=None):
+    """Launch the FP64 FMA issue-rate probe (gtb_probe_fp64_fma): blocks * 256 * 8 * iters
+    binary64 FMAs; the caller times it."""
+    _check(lib().gtb_probe_fp64_fma(int(blocks), int(iters), ctypes.c_void_p(sink.data_ptr()), _stream(stream)))
+    return blocks * 256 * 8 * iters
 
 
 def device_status(stream=None):

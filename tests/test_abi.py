@@ -216,3 +216,17 @@ def test_selftest_wait_arguments(L):
     lib = L.lib()
     for limit, arrive in ((0, 0), (-1, 1), (2_000_000_001, 0), (1000, 3)):
         assert lib.gtb_selftest_wait(limit, arrive, None) == -9
+
+
+def test_binding_export_list_matches_header(L):
+    """The Python binding names every entry point the header declares, and nothing else."""
+    assert sorted(L.EXPORTS) == declared_symbols()
+
+
+def test_fp64_probe_validation(L):
+    """The FP64 FMA-rate probe rejects bad sizes and a NULL or misaligned sink before launching."""
+    lib = L.lib()
+    assert lib.gtb_probe_fp64_fma(0, 16, ctypes.c_void_p(0x10000000), None) == -9
+    assert lib.gtb_probe_fp64_fma(8, 0, ctypes.c_void_p(0x10000000), None) == -9
+    assert lib.gtb_probe_fp64_fma(8, 16, None, None) == -1
+    assert lib.gtb_probe_fp64_fma(8, 16, ctypes.c_void_p(0x10000004), None) == -4

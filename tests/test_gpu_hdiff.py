@@ -4,7 +4,7 @@ against the oracle run in FP64 on the FP32-rounded inputs."""
 import numpy as np
 import pytest
 
-from helpers import region, rel_err
+from helpers import hdiff_point_bound, region, rel_err, s7_stats
 
 pytestmark = pytest.mark.gpu
 
@@ -57,9 +57,17 @@ def test_small_fp64(G, orc):
 
 
 def test_256_fp64_full_field(G, orc):
-    """256x256x80 FP64, the launch configuration the benchmark times; whole field."""
+    """256x256x80 FP64, the launch configuration the benchmark times; whole field.
+    Beside the max-norm: the per-point bound of the fixed-point form, the worst column,
+    the 99.9th percentile of the pointwise error and the fraction of points beyond 1e-12."""
     got, ref = run_case(G, orc, 256, 256, 80, seed=1)
-    assert rel_err(got, ref) <= F64_TOL
+    inp, coeff = draw(256, 256, 80, 1)
+    st = s7_stats(got, ref, F64_TOL)
+    print("hdiff 256x256x80 FP64:", st)
+    assert st["max_norm"] <= F64_TOL
+    assert np.all(np.abs(got - ref) <= hdiff_point_bound(ref, inp, coeff, (2, 2, 0), (256, 256, 80)))
+    assert st["worst_column"] <= F64_TOL
+    assert st["p99_9_pointwise"] <= F64_TOL
 
 
 @pytest.mark.parametrize("I,J,K", [(67, 19, 5), (1, 1, 1), (130, 3, 2), (65, 17, 1), (200, 33, 7), (63, 15, 3)])
@@ -156,11 +164,17 @@ def test_fp64_tiny_magnitudes(G, orc):
 
 def test_fp64_wide_dynamic_range(G, orc):
     """Inputs spanning 60 binades in every tile: small values are truncated in the
-    fixed-point form, far below the bound relative to the field maximum."""
+    fixed-point form, far below the bound relative to the field maximum.  The error is
+    absolute at the level's scale: every point meets the per-point bound, while points
+    far below the tile's largest input keep fewer significant bits than binary64 (their
+    pointwise relative error is reported, not bounded by 1e-12)."""
     inp, coeff = draw(130, 33, 4, 23)
     scale = 2.0 ** np.random.default_rng(24).integers(-60, 1, inp.shape)
     got, ref = run_fields(G, orc, inp * scale, coeff)
-    assert rel_err(got, ref) <= F64_TOL
+    st = s7_stats(got, ref, F64_TOL)
+    print("hdiff wide dynamic range FP64:", st)
+    assert st["max_norm"] <= F64_TOL
+    assert np.all(np.abs(got - ref) <= hdiff_point_bound(ref, inp * scale, coeff, (2, 2, 0), (130, 33, 4)))
 
 
 def test_fp64_limiter_sign_of_tiny_differences(G, orc):

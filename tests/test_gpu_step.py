@@ -6,13 +6,18 @@ for bit (the same column code), and through it against the oracle."""
 import numpy as np
 import pytest
 
-from helpers import region, rel_err
+from helpers import hdiff_point_bound, region, rel_err, s7_stats
 
 pytestmark = pytest.mark.gpu
 
 F64_TOL = 1e-12
 F32_TOL = 1e-5
 VN = ("u_stage", "wcon", "u_pos", "utens", "utens_stage")
+# The column solve's worst column has no a-priori bound: it scales with the column's
+# conditioning.  On these draws (256x256x80, seed 0) the binary64 oracle itself is
+# 2.7e-11 from an extended-precision Thomas solve in its worst column (max-norm 2.5e-13,
+# 99.9th percentile 4.1e-14): a sanity bound about 7x above that.
+VADV_WORST_COLUMN = 2e-10
 
 
 @pytest.fixture(scope="module")
@@ -67,9 +72,16 @@ def test_256_fp64_full_field(G, orc):
     f = draw(*dom, 0)
     h, v, v1 = run(G, f, dom)
     rh, rv = oracle(orc, f, dom)
-    assert rel_err(h, rh) <= F64_TOL
+    sh, sv = s7_stats(h, rh, F64_TOL), s7_stats(v, rv, F64_TOL)
+    print("step 256x256x80 FP64 hdiff_out:", sh)
+    print("step 256x256x80 FP64 utens_stage_out:", sv)
+    assert sh["max_norm"] <= F64_TOL
+    assert np.all(np.abs(h - rh) <= hdiff_point_bound(rh, f["inp"], f["coeff"], (2, 2, 0), dom))
+    assert sh["worst_column"] <= F64_TOL and sh["p99_9_pointwise"] <= F64_TOL
     assert np.array_equal(v, v1)
-    assert rel_err(v, rv) <= F64_TOL
+    assert sv["max_norm"] <= F64_TOL
+    assert sv["p99_9_pointwise"] <= F64_TOL
+    assert sv["worst_column"] <= VADV_WORST_COLUMN
 
 
 @pytest.mark.parametrize("I,J,K", [(64, 64, 40), (96, 40, 37), (33, 7, 1), (1, 1, 2), (31, 5, 3), (70, 9, 137),
