@@ -53,21 +53,24 @@ __device__ __forceinline__ int member_of(const M *mem, int n, int item) {
     return lo;
 }
 
-template <typename T, int CPL, int W, int R, int STAGES, bool FIXED>
+// maps: per member its in tensor map, followed (CTMA) by its coeff tensor map.
+template <typename T, int CPL, int W, int R, int STAGES, bool FIXED, bool CTMA>
 __global__ void __launch_bounds__(32 * W)
     hdiff_batch_kernel(const CUtensorMap *__restrict__ maps, const BatchHdiffMember<T> *__restrict__ mem, int n_mem,
                        int n_items, int *counter) {
+    constexpr int MPM = CTMA ? 2 : 1;
     __shared__ int slot;
     uint64_t *bars;
-    unsigned char *base = hdiff_rs_smem<T, CPL, W, R, STAGES>(&bars);
+    unsigned char *base = hdiff_rs_smem<T, CPL, W, R, STAGES, CTMA>(&bars);
     for (;;) {
         const int item = next_item(counter, n_items, &slot);
         if (item < 0) break;
         const int m = member_of(mem, n_mem, item);
         const BatchHdiffMember<T> M = mem[m];
         const int local = item - M.item0;
-        hdiff_rs_item<T, CPL, W, R, STAGES, true, FIXED>(&maps[m], &maps[m], M.in, M.coeff, M.out, M.g, M.vec_ok,
-                                                          local % M.g.n_tiles, local / M.g.n_tiles, base, bars);
+        hdiff_rs_item<T, CPL, W, R, STAGES, true, FIXED, CTMA>(&maps[MPM * m], &maps[MPM * m + MPM - 1], M.in,
+                                                                M.coeff, M.out, M.g, M.vec_ok, local % M.g.n_tiles,
+                                                                local / M.g.n_tiles, base, bars);
     }
 }
 
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(32 * BJ)
         const int m = member_of(mem, n_mem, item);
         const BatchVadvMember<T> M = mem[m];
         const int local = item - M.item0;
-        vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>()>(M.us, M.wc, M.up, M.ut, M.uts, M.out, M.g,
+        vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>(), true>(M.us, M.wc, M.up, M.ut, M.uts, M.out, M.g,
                                                         local % M.blocks_x, local / M.blocks_x, cpb, dpb, NT, t,
                                                         false, threadIdx.x, threadIdx.y);
     }

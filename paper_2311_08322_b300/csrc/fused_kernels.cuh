@@ -373,12 +373,14 @@ __device__ __forceinline__ void fused_consumer(const View<const T> &wc, const Vi
     N h2_prev = zero;
     for (int m = 0; m < K; ++m) {
         const T ut_k = ut_n, uts_k = uts_n, w_m = w_n, w1_m = w1_n;
+        // inputs read once: streaming loads (utens_stage may be the output array, whose
+        // level-m element is stored only after this value was used)
         if (m + 1 < K) {
-            w_n = pw[(int64_t)(m + 1) * wc.sk];
-            if (row_end) w1_n = pw1[(int64_t)(m + 1) * wc.sk];
+            w_n = ld_once(pw + (int64_t)(m + 1) * wc.sk);
+            if (row_end) w1_n = ld_once(pw1 + (int64_t)(m + 1) * wc.sk);
         }
-        ut_n = put[(int64_t)m * ut.sk];
-        uts_n = puts[(int64_t)m * uts.sk];
+        ut_n = ld_once(put + (int64_t)m * ut.sk);
+        uts_n = ld_once(puts + (int64_t)m * uts.sk);
         const int slot = m % RING;
         const bool ok = mbar_wait(&full[slot], (m / RING) & 1);
         if (!__all_sync(0xffffffffu, ok)) return;  // the producers gave up (device error word set)
@@ -392,33 +394,56 @@ __device__ __forceinline__ void fused_consumer(const View<const T> &wc, const Vi
     vstep(K - 1, false, h_prev, T(0), h2_prev, zero, ut_n, uts_n, T(0), T(0));
 
     // back substitution in z = x - h; levels in groups of BG, a group's inputs loaded
-    // before the previous group's outputs are stored (distinct levels, distinct addresses)
-    if (active) {
-        N z = e_last;
-        po[(int64_t)(K - 1) * out.sk] = to_store<T, N>(dtr * z);
-        constexpr int BG = 4;
-        N eq[BG], cq[BG];
-        auto load_group = [&](int k0) {
+    // before the previous group's outputs are stored (distinct levels, distinct addresses).
+    // Without kept factors the column state is dead once read: last reads are streaming
+    // loads, and the warp drops the state lines it owns whole (its 32 lanes on 32
+    // consecutive columns of one row, which needs TI a multiple of 32, all in the domain,
+    // the line 128-byte aligned) from L2 without a write-back.  Kept factors (rsave)
+    // stay: the adjoint reads c'_k and 1/p_k later.
+    const bool drop = rsave == nullptr;
+    const bool own = (TI % 32 == 0) && drop && __all_sync(0xffffffffu, active);
+    const size_t c0 = __shfl_sync(0xffffffffu, cidx, 0);
+    constexpr int kArrays = DPG ? 1 : 2;
+    constexpr int kLines = (int)(32 * sizeof(N) / 128);
+    auto ld_state = [&](const N *q) -> N { return drop ? ld_once(q) : *q; };
+    N z = e_last;
+    if (active) st_once(po + (int64_t)(K - 1) * out.sk, to_store<T, N>(dtr * z));
+    constexpr int BG = 4;
+    N eq[BG], cq[BG];
+    auto load_group = [&](int k0) {
 #pragma unroll
-            for (int q = 0; q < BG; ++q) {
-                const int k = k0 - q;
-                if (k < 0) break;
-                eq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : epb[(size_t)k * cstride + cidx];
-                cq[q] = cpb[(size_t)k * cstride + cidx];
-            }
-        };
-        if (K >= 2) load_group(K - 2);
-        for (int k0 = K - 2; k0 >= 0; k0 -= BG) {
-            N ec[BG], cc[BG];
+        for (int q = 0; q < BG; ++q) {
+            const int k = k0 - q;
+            if (k < 0) break;
+            eq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : ld_state(epb + (size_t)k * cstride + cidx);
+            cq[q] = ld_state(cpb + (size_t)k * cstride + cidx);
+        }
+    };
+    if (K >= 2) load_group(K - 2);
+    for (int k0 = K - 2; k0 >= 0; k0 -= BG) {
+        N ec[BG], cc[BG];
 #pragma unroll
-            for (int q = 0; q < BG; ++q) ec[q] = eq[q], cc[q] = cq[q];
-            if (k0 - BG >= 0) load_group(k0 - BG);
+        for (int q = 0; q < BG; ++q) ec[q] = eq[q], cc[q] = cq[q];
+        if (k0 - BG >= 0) load_group(k0 - BG);
 #pragma unroll
-            for (int q = 0; q < BG; ++q) {
-                const int k = k0 - q;
-                if (k < 0) break;
-                z = ec[q] - cc[q] * z;
-                po[(int64_t)k * out.sk] = to_store<T, N>(dtr * z);
+        for (int q = 0; q < BG; ++q) {
+            const int k = k0 - q;
+            if (k < 0) break;
+            z = ec[q] - cc[q] * z;
+            if (active) st_once(po + (int64_t)k * out.sk, to_store<T, N>(dtr * z));
+        }
+        if constexpr (kLines >= 1) {
+            if (own) {
+                __syncwarp();
+                if (lane < BG * kArrays * kLines) {
+                    const int m = lane % kLines, arr = (lane / kLines) % kArrays, q = lane / (kLines * kArrays);
+                    const int k = k0 - q;
+                    if (k >= 0) {
+                        const N *row = (arr == 0 ? cpb : epb) + (size_t)k * cstride + c0;
+                        const unsigned char *line = reinterpret_cast<const unsigned char *>(row) + m * 128;
+                        if ((reinterpret_cast<uintptr_t>(line) & 127) == 0) discard_l2_line(line);
+                    }
+                }
             }
         }
     }
@@ -500,7 +525,7 @@ __global__ void __launch_bounds__(32 * (BJ + PW), 7 * 4 / (BJ + PW))
         return;
     }
     const size_t cstride = (size_t)g.I * g.J;
-    vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>()>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
+    vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>(), true>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
                                                     ws + (size_t)g.K * cstride, cstride, 0, true, tid & 31, w);
 }
 

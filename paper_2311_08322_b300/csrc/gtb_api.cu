@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -237,9 +238,20 @@ template <> struct HdiffCfg<double> {  // 64 x 64 tile, 4 warps of 16 rows, 2 co
 template <> struct HdiffCfg<float> {   // 128 x 64 tile, 8 warps of 8 rows, 4 columns per lane
     static constexpr int CPL = 4, W = 8, R = 8, STAGES = 2;
 };
-// binary32 with coeff staged by TMA beside in (when coeff's layout allows a tensor map)
-struct HdiffF32CoeffTmaCfg {
-    static constexpr int CPL = 4, W = 4, R = 8, STAGES = 2;
+// coeff staged by TMA beside in (when coeff's layout allows a tensor map).  binary32:
+// 128 x 32 tiles of 8 warps x 4 rows, 2 stages (72 KB).  Measured at 512x512x80
+// (20-launch means, two input sets of 253 MB): 48.9 us, against 50.0 for 4 warps x 8
+// rows, 49.7 for 8 x 4 with 3 stages, 52.0 for 4 x 4 with 3, 54.0 for 8 x 8 (128 x 64,
+// 140 KB) and 56.4 for 4 x 8 with 3; 70.5 with coeff loaded row by row from global memory.
+template <typename T>
+struct HdiffCoeffTmaCfg;
+template <> struct HdiffCoeffTmaCfg<float> {
+    static constexpr bool kUse = true;
+    static constexpr int CPL = 4, W = 8, R = 4, STAGES = 2;
+};
+template <> struct HdiffCoeffTmaCfg<double> {
+    static constexpr bool kUse = false;
+    static constexpr int CPL = 2, W = 4, R = 8, STAGES = 2;
 };
 
 template <typename T, bool TMA, typename C = HdiffCfg<T>, bool CTMA = false>
@@ -350,9 +362,9 @@ static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field
         return reinterpret_cast<uintptr_t>(v.p) % 16 == 0 && (v.sj * es) % 16 == 0 && (v.sk * es) % 16 == 0;
     };
     CUtensorMap map, cmap;
-    if constexpr (sizeof(T) == 4) {
-        // binary32: in and coeff both by TMA when both layouts allow it, out by vector stores
-        using C = HdiffF32CoeffTmaCfg;
+    if constexpr (HdiffCoeffTmaCfg<T>::kUse) {
+        // in and coeff both by TMA when both layouts allow it, out by vector stores
+        using C = HdiffCoeffTmaCfg<T>;
         using Tile = RsTile<T, C::CPL, C::W, C::R, true>;
         HdiffGeom g = hdiff_geom<T, C>(dom);
         if (aligned(out) && encode_in_map<T>(fin, Tile::BX, Tile::BY, g, map) &&
@@ -1067,21 +1079,24 @@ static void plan_free(gtb_plan *p) {
 
 // hdiff tile variants of the batched form: variant 0 is the single-domain
 // configuration (so batched and single results agree bit for bit), variant 1
-// the other warp/row split.
-template <typename T, int V>
+// the other warp/row split.  CTMA: binary32 members with coeff staged by TMA (the
+// single-domain binary32 configuration); otherwise coeff is read from global memory
+// (the binary64 configuration, and binary32 plans whose coeff layouts rule TMA out).
+template <typename T, int V, bool CTMA = false>
 struct BatchHCfg {
-    static constexpr int CPL = HdiffCfg<T>::CPL, STAGES = 2;
-    static constexpr int W = V == 0 ? HdiffCfg<T>::W : (HdiffCfg<T>::W == 4 ? 8 : 4);
-    static constexpr int R = V == 0 ? HdiffCfg<T>::R : (HdiffCfg<T>::R == 16 ? 8 : 16);
+    using B = typename std::conditional<CTMA, HdiffCoeffTmaCfg<T>, HdiffCfg<T>>::type;
+    static constexpr int CPL = B::CPL, STAGES = 2;
+    static constexpr int W = V == 0 ? B::W : (B::W == 4 ? 8 : 4);
+    static constexpr int R = V == 0 ? B::R : (B::W == 4 ? B::R / 2 : B::R * 2);
 };
 
-template <typename T, int V>
+template <typename T, int V, bool CTMA>
 static int batch_hdiff_launch_info(int ctas_per_sm, int *slots, void (**kern)(const CUtensorMap *, const BatchHdiffMember<T> *, int, int, int *), int *smem) {
-    using C = BatchHCfg<T, V>;
+    using C = BatchHCfg<T, V, CTMA>;
     constexpr bool FIXED = sizeof(T) == 8;
     constexpr int W = C::W;
-    auto k = hdiff_batch_kernel<T, C::CPL, W, C::R, C::STAGES, FIXED>;
-    *smem = hdiff_rs_smem_bytes<T, C::CPL, W, C::R, C::STAGES>();
+    auto k = hdiff_batch_kernel<T, C::CPL, W, C::R, C::STAGES, FIXED, CTMA>;
+    *smem = hdiff_rs_smem_bytes<T, C::CPL, W, C::R, C::STAGES, CTMA>();
     if (prepare_kernel(k, *smem) != cudaSuccess) return launch_status("batch: hdiff shared-memory attribute");
     int rb = resident_blocks(k, 32 * W, *smem);
     if (ctas_per_sm > 0) rb = std::min(rb, ctas_per_sm);
@@ -1100,14 +1115,15 @@ static int batch_vadv_launch_info(int ctas_per_sm, int *slots, void (**kern)(con
     return GTB_OK;
 }
 
-template <typename T, typename N, int V, int BJ>
+template <typename T, typename N, int V, int BJ, bool CTMA>
 static int build_plan(const gtb_member *mem, int n, double dtr, double beta, unsigned flags, gtb_plan *P) {
-    using C = BatchHCfg<T, V>;
+    using C = BatchHCfg<T, V, CTMA>;
     constexpr int W = C::W;
-    using Tile = RsTile<T, C::CPL, W, C::R>;
+    using Tile = RsTile<T, C::CPL, W, C::R, CTMA>;
     const size_t es = sizeof(T);
     constexpr int kAlign = 16 / (int)sizeof(T);
-    std::vector<CUtensorMap> maps(n);
+    constexpr int MPM = CTMA ? 2 : 1;  // tensor maps per member: in (and coeff)
+    std::vector<CUtensorMap> maps(MPM * n);
     std::vector<BatchHdiffMember<T>> hm(n);
     std::vector<BatchVadvMember<T>> vm(n);
     std::vector<int> vorder(n);
@@ -1135,12 +1151,14 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
         cuuint64_t gstride[2] = {(cuuint64_t)(M.in.strides[1] * es), (cuuint64_t)(M.in.strides[2] * es)};
         cuuint32_t box[3] = {(cuuint32_t)Tile::BX, (cuuint32_t)Tile::BY, 1};
         cuuint32_t estr[3] = {1, 1, 1};
-        memset(&maps[q], 0, sizeof(CUtensorMap));
-        CUresult r = encode_fn()(&maps[q], sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+        memset(&maps[MPM * q], 0, sizeof(CUtensorMap));
+        CUresult r = encode_fn()(&maps[MPM * q], sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                                  3, reinterpret_cast<void *>(abase), gdim, gstride, box, estr,
                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(GTB_ERR_LAYOUT, "gtb_batch_plan: member %d: tensor-map encoding failed (%d)", q, (int)r);
+        if (CTMA && !encode_coeff_map<T>(&M.coeff, Tile::TI, Tile::TJ, g, maps[MPM * q + 1]))
+            return fail(GTB_ERR_LAYOUT, "gtb_batch_plan: member %d: coeff tensor map", q);
         const View<T> cf = view_of<T>(&M.coeff), out = view_of<T>(&M.h);
         auto aligned = [&](const View<T> &v) {
             return reinterpret_cast<uintptr_t>(v.p) % 16 == 0 && (v.sj * es) % 16 == 0 && (v.sk * es) % 16 == 0;
@@ -1167,7 +1185,7 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
     void (*hk)(const CUtensorMap *, const BatchHdiffMember<T> *, int, int, int *);
     void (*vk)(const BatchVadvMember<T> *, int, int, int *, N *, size_t, int);
     int hslots, vslots, hsmem, rc;
-    if ((rc = batch_hdiff_launch_info<T, V>(P->cfg.ctas_per_sm, &hslots, &hk, &hsmem))) return rc;
+    if ((rc = batch_hdiff_launch_info<T, V, CTMA>(P->cfg.ctas_per_sm, &hslots, &hk, &hsmem))) return rc;
     if ((rc = batch_vadv_launch_info<T, N, BJ>(P->cfg.ctas_per_sm, &vslots, &vk))) return rc;
     P->h_items = hitems, P->v_items = vitems;
     P->h_grid = std::max(1, std::min(hitems, hslots));
@@ -1175,11 +1193,11 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
     P->points = pts;
     const size_t slice = (size_t)vadv_state_arrays<T, N>() * k_max * 32 * BJ;
     cudaError_t e;
-    if ((e = cudaMalloc(&P->d_maps, sizeof(CUtensorMap) * n)) || (e = cudaMalloc(&P->d_hmem, sizeof(BatchHdiffMember<T>) * n)) ||
+    if ((e = cudaMalloc(&P->d_maps, sizeof(CUtensorMap) * MPM * n)) || (e = cudaMalloc(&P->d_hmem, sizeof(BatchHdiffMember<T>) * n)) ||
         (e = cudaMalloc(&P->d_vmem, sizeof(BatchVadvMember<T>) * n)) || (e = cudaMalloc(&P->d_counters, 2 * sizeof(int))) ||
         (e = cudaMalloc(&P->d_scratch, sizeof(N) * slice * P->v_grid)))
         return fail(GTB_ERR_LAUNCH, "gtb_batch_plan: device tables: %s", cudaGetErrorString(e));
-    if ((e = cudaMemcpy(P->d_maps, maps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice)) ||
+    if ((e = cudaMemcpy(P->d_maps, maps.data(), sizeof(CUtensorMap) * MPM * n, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(P->d_hmem, hm.data(), sizeof(BatchHdiffMember<T>) * n, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(P->d_vmem, vm.data(), sizeof(BatchVadvMember<T>) * n, cudaMemcpyHostToDevice)))
         return fail(GTB_ERR_LAUNCH, "gtb_batch_plan: table upload: %s", cudaGetErrorString(e));
@@ -1202,19 +1220,35 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
     return GTB_OK;
 }
 
-template <typename T, typename N, int V>
+template <typename T, typename N, int V, bool CTMA>
 static int build_plan_bj(const gtb_member *mem, int n, double dtr, double beta, unsigned flags, gtb_plan *P) {
     switch (P->cfg.vadv_warps) {
-    case 1: return build_plan<T, N, V, 1>(mem, n, dtr, beta, flags, P);
-    case 4: return build_plan<T, N, V, 4>(mem, n, dtr, beta, flags, P);
-    default: return build_plan<T, N, V, 2>(mem, n, dtr, beta, flags, P);
+    case 1: return build_plan<T, N, V, 1, CTMA>(mem, n, dtr, beta, flags, P);
+    case 4: return build_plan<T, N, V, 4, CTMA>(mem, n, dtr, beta, flags, P);
+    default: return build_plan<T, N, V, 2, CTMA>(mem, n, dtr, beta, flags, P);
     }
+}
+
+// Whether every member's coeff can be staged by TMA: its domain's first point on a
+// 16-byte boundary and 16-byte pitches.
+static bool batch_coeff_tma_ok(const gtb_member *mem, int n, size_t es) {
+    for (int q = 0; q < n; ++q) {
+        const gtb_field &c = mem[q].coeff;
+        const uintptr_t first = reinterpret_cast<uintptr_t>(c.ptr) + (uintptr_t)c.origin[0] * es;
+        if (first % 16 || (c.strides[1] * es) % 16 || (c.strides[2] * es) % 16) return false;
+    }
+    return true;
 }
 
 template <typename T, typename N>
 static int build_plan_w(const gtb_member *mem, int n, double dtr, double beta, unsigned flags, gtb_plan *P) {
-    return P->cfg.hdiff_tile == 1 ? build_plan_bj<T, N, 1>(mem, n, dtr, beta, flags, P)
-                                  : build_plan_bj<T, N, 0>(mem, n, dtr, beta, flags, P);
+    if constexpr (HdiffCoeffTmaCfg<T>::kUse) {
+        if (batch_coeff_tma_ok(mem, n, sizeof(T)))
+            return P->cfg.hdiff_tile == 1 ? build_plan_bj<T, N, 1, true>(mem, n, dtr, beta, flags, P)
+                                          : build_plan_bj<T, N, 0, true>(mem, n, dtr, beta, flags, P);
+    }
+    return P->cfg.hdiff_tile == 1 ? build_plan_bj<T, N, 1, false>(mem, n, dtr, beta, flags, P)
+                                  : build_plan_bj<T, N, 0, false>(mem, n, dtr, beta, flags, P);
 }
 
 }  // namespace gtb

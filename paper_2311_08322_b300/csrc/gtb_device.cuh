@@ -252,4 +252,55 @@ __device__ __forceinline__ df recip(df y) {
 // Exact sum / difference of two binary32 values as a double-word (TwoSum).
 __device__ __forceinline__ df df_add2(float a, float b) { return two_sum(a, b); }
 
+// Fused double-word forms of x - y z and x + y z: the exact product of the high parts
+// (TwoProd) with both cross terms added to its low part (y.lo z.lo, below u^2 |y z|,
+// dropped), combined with x by a TwoSum of the high parts and the low parts' sum, then
+// one renormalisation (FastTwoSum).  The product is not renormalised on its own, which
+// saves four operations against the double-word product followed by the double-word
+// sum (JMP17 Algs. 12 and 5), for an absolute error of the same order, a few
+// u^2 (|x| + |y z|) with u = 2^-24.
+__device__ __forceinline__ df df_fms(df x, df y, df z) {
+    const float ph = __fmul_rn(y.hi, z.hi);
+    float pl = __fmaf_rn(y.hi, z.hi, -ph);
+    pl = __fmaf_rn(y.hi, z.lo, pl);
+    pl = __fmaf_rn(y.lo, z.hi, pl);
+    const df s = two_sum(x.hi, -ph);
+    const float t = __fadd_rn(__fsub_rn(x.lo, pl), s.lo);
+    return fast_two_sum(s.hi, t);
+}
+__device__ __forceinline__ df df_fma(df x, df y, df z) {
+    return df_fms(x, -y, z);
+}
+// y z rounded once to binary32: the high product with both cross terms folded into
+// one FMA chain (the error is within one binary32 rounding of the exact product).
+__device__ __forceinline__ float df_mul_to_float(df y, df z) {
+    return __fmaf_rn(y.hi, z.hi, __fmaf_rn(y.hi, z.lo, __fmul_rn(y.lo, z.hi)));
+}
+
+// ---------------------------------------------------------------- streaming accesses
+// Loads and stores with the streaming cache operator (ld/st.global.cs: lines allocated
+// evict-first in L1 and L2) for data a kernel touches once: the column solve's inputs,
+// its final outputs and the last read of its column state.  They leave L2 to the state
+// that is written in the forward sweep and read back in the backward sweep.
+template <typename T>
+__device__ __forceinline__ T ld_once(const T *p) {
+    return __ldcs(p);
+}
+template <>
+__device__ __forceinline__ df ld_once<df>(const df *p) {
+    const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
+    return df{v.x, v.y};
+}
+template <typename T>
+__device__ __forceinline__ void st_once(T *p, T v) {
+    __stcs(p, v);
+}
+
+// Drops the 128-byte L2 line at p (128-byte aligned, global memory) without writing
+// it back (PTX discard.global.L2): its contents become undefined.  For column state
+// whose last read has completed, so that the dead lines cost no DRAM write-back.
+__device__ __forceinline__ void discard_l2_line(const void *p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(__cvta_generic_to_global(p)) : "memory");
+}
+
 }  // namespace gtb

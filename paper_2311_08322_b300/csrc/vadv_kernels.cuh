@@ -62,6 +62,15 @@ template <> __device__ __forceinline__ df addx<df, float>(df a, float b) { retur
 // a + b of two storage values (exact for double-float)
 template <typename N, typename T> __device__ __forceinline__ N add2(T a, T b) { return to_num<N, T>(a) + to_num<N, T>(b); }
 template <> __device__ __forceinline__ df add2<df, float>(float a, float b) { return df_add2(a, b); }
+// x - y z and x + y z: as written for binary64 and binary32 (contracted to one FMA),
+// the fused double-word forms for double-float
+template <typename N> __device__ __forceinline__ N fms(N x, N y, N z) { return x - y * z; }
+template <> __device__ __forceinline__ df fms<df>(df x, df y, df z) { return df_fms(x, y, z); }
+template <typename N> __device__ __forceinline__ N fma_n(N x, N y, N z) { return x + y * z; }
+template <> __device__ __forceinline__ df fma_n<df>(df x, df y, df z) { return df_fma(x, y, z); }
+// dtr v rounded to the storage type
+template <typename T, typename N> __device__ __forceinline__ T scaled_store(N dtr, N v) { return to_store<T, N>(dtr * v); }
+template <> __device__ __forceinline__ float scaled_store<float, df>(df dtr, df v) { return df_mul_to_float(dtr, v); }
 
 // Inputs of one level k for this lane's column (loaded one level ahead of their use).
 template <typename T>
@@ -74,15 +83,17 @@ template <typename T>
 __device__ __forceinline__ void load_level(Level<T> &L, int k, int K, const T *pup, const T *put, const T *puts,
                                            const T *pus, const T *pw, const T *pw1, int64_t sk_up, int64_t sk_ut,
                                            int64_t sk_uts, int64_t sk_us, int64_t sk_w, bool last_lane) {
+    // every input value is read once (streaming loads); utens_stage may be the output
+    // array itself, whose level-k element is stored only after its value was used
     if (k < K) {
-        L.ut = put[(int64_t)k * sk_ut];
-        L.uts = puts[(int64_t)k * sk_uts];
+        L.ut = ld_once(put + (int64_t)k * sk_ut);
+        L.uts = ld_once(puts + (int64_t)k * sk_uts);
     }
     if (k + 1 < K) {
-        L.us1 = pus[(int64_t)(k + 1) * sk_us];
-        L.up1 = pup[(int64_t)(k + 1) * sk_up];
-        L.w = pw[(int64_t)(k + 1) * sk_w];
-        if (last_lane) L.w1 = pw1[(int64_t)(k + 1) * sk_w];
+        L.us1 = ld_once(pus + (int64_t)(k + 1) * sk_us);
+        L.up1 = ld_once(pup + (int64_t)(k + 1) * sk_up);
+        L.w = ld_once(pw + (int64_t)(k + 1) * sk_w);
+        if (last_lane) L.w1 = ld_once(pw1 + (int64_t)(k + 1) * sk_w);
     }
 }
 
@@ -159,7 +170,9 @@ __host__ __device__ constexpr size_t vadv_smem_per_col_level() {
 // SYM (beta_v = 0): the explicit weights equal the implicit ones and the explicit
 // terms vanish into the matrix (below); a separate body, so that no FP64 instruction
 // of the general case is issued, even predicated off (the FP64 pipe is the bound).
-template <typename T, typename N, int BJ, bool DPG, bool YF, bool SYM>
+// GST: the column state is in global memory (its last reads are streaming loads); else
+// in shared memory.
+template <typename T, typename N, int BJ, bool DPG, bool YF, bool SYM, bool GST>
 __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                                const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                                const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
@@ -207,8 +220,8 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     Level<T> L0, L1;
     GTB_LOAD(L0, 0);
 
-    T us_cur = pus[0];
-    N s_cur = add2<N, T>(us_cur, pup[0]);  // s_0
+    T us_cur = ld_once(pus);
+    N s_cur = add2<N, T>(us_cur, ld_once(pup));  // s_0
     N dpl_prev = zero;                     // u_stage_k - u_stage_{k-1} (general case only)
     N a_cur = zero, g_cur = zero;          // a_0 = g_0 = 0
     N cp_prev = zero, dp_prev = zero, e_last = zero;
@@ -239,15 +252,18 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
             }
         }
         const N b = (dtr - a_cur) + a_next;  // dtr - a_k - c_k with c_k = -a_{k+1}
-        N d = addx<N, T>(addx<N, T>(dtr * s_cur, L0.ut), L0.uts);
+        // d = dtr s + utens + utens_stage: double-float adds the two inputs exactly first
+        N d;
+        if constexpr (std::is_same<N, df>::value) d = df_fma(add2<N, T>(L0.ut, L0.uts), dtr, s_cur);
+        else d = addx<N, T>(addx<N, T>(dtr * s_cur, L0.ut), L0.uts);
         if (!SYM) {  // + g_k (us_k - us_{k-1}) + g_{k+1} (us_{k+1} - us_k)
             if (k > 0) d = d + g_cur * dpl_prev;
             if (has_next) d = d + g_next * dpl;
         }
         N p = b, num = d;
         if (k > 0) {
-            p = b - a_cur * cp_prev;
-            num = d - a_cur * dp_prev;
+            p = b - a_cur * cp_prev;  // as the adjoint refactorises it (kept factors match bit for bit)
+            num = fms(d, a_cur, dp_prev);
         }
         const N r = recip(p);
         const N cpk = (-a_next) * r, dpk = num * r;
@@ -258,7 +274,7 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
             if (active) po[(int64_t)k * out.sk] = to_store<T, N>(dpk);
             if (wr) dpb[(size_t)k * cstride + cidx] = s_cur;
         } else {
-            ek = (dpk - s_cur) - cpk * s_next;  // s_K = 0 (c'_{K-1} = 0)
+            ek = fms(dpk - s_cur, cpk, s_next);  // s_K = 0 (c'_{K-1} = 0)
             if (DPG) {
                 if (active) po[(int64_t)k * out.sk] = to_store<T, N>(ek);
             } else if (wr) {
@@ -278,14 +294,19 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     // previous group's outputs are stored (distinct levels, so distinct addresses: the
     // out stride in k is nonzero), so the loads overlap instead of each waiting behind a
     // store.
-    auto result = [&](N v, N sk) -> N {
-        if constexpr (YF) return dtr * (v - sk);
-        else return dtr * v;
+    auto result = [&](N v, N sk) -> T {
+        if constexpr (YF) return to_store<T, N>(dtr * (v - sk));
+        else return scaled_store<T, N>(dtr, v);
+    };
+    // (the column state's last reads and the final outputs: streaming accesses; a value
+    // parked in the output array is read with a plain load before its element is stored)
+    auto ld_state = [&](const N *q) -> N {
+        if constexpr (GST) return ld_once(q);
+        else return *q;
     };
     N z = e_last;  // y_{K-1} = d'_{K-1} (YF) or z_{K-1} = e_{K-1}
     if (active)
-        po[(int64_t)(K - 1) * out.sk] =
-            to_store<T, N>(result(z, YF ? dpb[(size_t)(K - 1) * cstride + cidx] : zero));
+        st_once(po + (int64_t)(K - 1) * out.sk, result(z, YF ? ld_state(dpb + (size_t)(K - 1) * cstride + cidx) : zero));
     constexpr int BG = 4;
     N eq[BG], cq[BG], sq[BG];
     auto load_group = [&](int k0) {
@@ -293,11 +314,18 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
         for (int q = 0; q < BG; ++q) {
             const int k = k0 - q;
             if (k < 0) break;
-            eq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : dpb[(size_t)k * cstride + cidx];
-            cq[q] = cpb[(size_t)k * cstride + cidx];
-            sq[q] = YF ? dpb[(size_t)k * cstride + cidx] : zero;
+            eq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : ld_state(dpb + (size_t)k * cstride + cidx);
+            cq[q] = ld_state(cpb + (size_t)k * cstride + cidx);
+            sq[q] = YF ? ld_state(dpb + (size_t)k * cstride + cidx) : zero;
         }
     };
+    // Global state: once a group's values are consumed, its lines are dead and the warp
+    // drops the ones it owns whole (its 32 columns present, the line 128-byte aligned)
+    // from L2 without a write-back.  Arrays: c', and s (y form) or e_k (not parked).
+    constexpr int kArrays = (YF || !DPG) ? 2 : 1;
+    constexpr int kLines = (int)(32 * sizeof(N) / 128);  // lines per warp, level and array
+    const bool own = GST && __all_sync(0xffffffffu, ws_domain ? active : true);
+    const size_t c0 = __shfl_sync(0xffffffffu, cidx, 0);
     if (K >= 2) load_group(K - 2);
     for (int k0 = K - 2; k0 >= 0; k0 -= BG) {
         N ec[BG], cc[BG], sc[BG];
@@ -308,22 +336,37 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
         for (int q = 0; q < BG; ++q) {
             const int k = k0 - q;
             if (k < 0) break;
-            z = ec[q] - cc[q] * z;
-            if (active) po[(int64_t)k * out.sk] = to_store<T, N>(result(z, sc[q]));
+            z = fms(ec[q], cc[q], z);
+            if (active) st_once(po + (int64_t)k * out.sk, result(z, sc[q]));
+        }
+        if constexpr (GST && kLines >= 1) {
+            if (own) {
+                __syncwarp();
+                const int e = tx;  // (level in group, array, line) handled by this lane
+                if (e < BG * kArrays * kLines) {
+                    const int m = e % kLines, arr = (e / kLines) % kArrays, q = e / (kLines * kArrays);
+                    const int k = k0 - q;
+                    if (k >= 0) {
+                        const N *row = (arr == 0 ? cpb : dpb) + (size_t)k * cstride + c0;
+                        const unsigned char *line = reinterpret_cast<const unsigned char *>(row) + m * 128;
+                        if ((reinterpret_cast<uintptr_t>(line) & 127) == 0) discard_l2_line(line);
+                    }
+                }
+            }
         }
     }
 }
 
-template <typename T, typename N, int BJ, bool DPG, bool YF>
+template <typename T, typename N, int BJ, bool DPG, bool YF, bool GST>
 __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                              const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                              const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
                                              size_t cidx_ws, bool ws_domain, int tx, int ty) {
     if (g.sym)
-        vadv_columns_t<T, N, BJ, DPG, YF, true>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
+        vadv_columns_t<T, N, BJ, DPG, YF, true, GST>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
                                                 ws_domain, tx, ty);
     else
-        vadv_columns_t<T, N, BJ, DPG, YF, false>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
+        vadv_columns_t<T, N, BJ, DPG, YF, false, GST>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
                                                  ws_domain, tx, ty);
 }
 
@@ -338,12 +381,12 @@ __global__ void __launch_bounds__(32 * BJ)
     const int t = threadIdx.y * 32 + threadIdx.x;
     if (WS) {
         const size_t cstride = (size_t)g.I * g.J;
-        vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>()>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
+        vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>(), true>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
                                                         ws + (size_t)g.K * cstride, cstride, 0, true, threadIdx.x,
                                                         threadIdx.y);
     } else {
         N *cpb = reinterpret_cast<N *>(smem_raw);
-        vadv_columns<T, N, BJ, DPG, false>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, cpb,
+        vadv_columns<T, N, BJ, DPG, false, false>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, cpb,
                                            cpb + (size_t)g.K * NT, NT, t, false, threadIdx.x, threadIdx.y);
     }
 }
