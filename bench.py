@@ -462,6 +462,7 @@ def run_gtb(args):
     chain = fused_chain_compare(gtb, f, sets) if rank == 0 and not args.no_fused else None
     calls = call_overhead() if rank == 0 and not args.no_fused else None
     adj = adjoint_ratio(gtb, f, sets) if rank == 0 and not args.no_adjoint else None
+    adj32 = adjoint_ratio(gtb, f, sets, dtype=np.float32) if rank == 0 and not args.no_adjoint else None
     el_ms = max_over_ranks(el_ms, dist if world > 1 else None, "cuda")
     value = whole_job_mpoints(world, POINTS, args.steps, el_ms)
 
@@ -567,7 +568,7 @@ def run_gtb(args):
                              f"{(hdiff_bytes(I, J, K, 8) + vadv_bytes(I, J, K, 8)) / 1e6:.0f} MB each (> 126 MB L2)"},
             "kernels": kern, "roofline": roof, "fp64": fp64, "clocks": clk, "gpu_launches": args.steps,
             "fused_chain": chain, "call_overhead": calls,
-            "adjoint_forward_ratio": None if adj is None else adj["ratio"], "adjoint": adj,
+            "adjoint_forward_ratio": None if adj is None else adj["ratio"], "adjoint": adj, "adjoint_fp32": adj32,
             "e2e": {"value": round(e2e_value, 1), "unit": "Mpoints/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}}
     prec_outs = None
@@ -696,36 +697,43 @@ def fused_chain_compare(gtb, f, sets, reps=50):
             "speedup": round(sep / fus, 3), "fused_mpoints_s": round(POINTS / (fus / 1e3) / 1e6, 1)}
 
 
-def adjoint_ratio(gtb, f, sets, reps=50):
-    """Time of one chained step's backward over its forward at 256x256x80 FP64 (C ABI,
+def adjoint_ratio(gtb, f, sets, reps=50, dtype=np.float64):
+    """Time of one chained step's backward over its forward at 256x256x80 (C ABI,
     preallocated storages), as the differentiable chain runs them: forward = periodic halo
     refresh + the fused hdiff -> vadv kernel keeping the column factors, backward = vadv_adj
     on those factors (merged u_stage/u_pos cotangent) + hdiff_adj (with coeff_bar) + halo
     fold.  Forward and backward alternate (each backward consumes its forward's factors);
-    events around each side give both times."""
+    events around each side give both times.  FP64 storage, or FP32 storage with
+    double-float columns (its own storages, rounded from the same draws)."""
     import torch
-    o2 = (HDIFF_HALO, HDIFF_HALO, 0)
+    o2, o1 = (HDIFF_HALO, HDIFF_HALO, 0), (VADV_HALO, VADV_HALO, 0)
     dom = (I, J, K)
-    nfac = gtb.hdiff_vadv_workspace_bytes(torch.float64, "native", dom, save_factors=True)
+    f64 = dtype == np.float64
+    prec = "native" if f64 else "df"
+    tdt = torch.float64 if f64 else torch.float32
+    nfac = gtb.hdiff_vadv_workspace_bytes(tdt, prec, dom, save_factors=True)
     bufs = []
-    for s in sets:
-        bufs.append({"fs": s["in"], "cs": s["coeff"], "y": gtb.storage_from(np.zeros((K, J, I)), (0, 0, 0)),
+    for s in (sets if f64 else range(2)):
+        if not f64:  # binary32 storages of the same draws
+            s = {n: gtb.storage_from(f[n].astype(np.float32), o2 if n in ("in", "coeff") else o1)
+                 for n in ("in", "coeff", "wcon", "utens", "utens_stage")}
+        bufs.append({"fs": s["in"], "cs": s["coeff"], "y": gtb.storage_from(np.zeros((K, J, I), dtype), (0, 0, 0)),
                      "wcon": s["wcon"], "ut": s["utens"], "uts": s["utens_stage"],
-                     "yb": gtb.storage_from(f["u_pos"][:, 1:-1, 1:-1].copy(), (0, 0, 0)),
-                     "hb": gtb.storage_from(np.zeros((K, J, I)), (0, 0, 0)),
-                     "ib": gtb.storage_from(np.zeros_like(f["in"]), o2),
-                     "cb": gtb.storage_from(np.zeros_like(f["coeff"]), o2),
+                     "yb": gtb.storage_from(f["u_pos"][:, 1:-1, 1:-1].astype(dtype), (0, 0, 0)),
+                     "hb": gtb.storage_from(np.zeros((K, J, I), dtype), (0, 0, 0)),
+                     "ib": gtb.storage_from(np.zeros(f["in"].shape, dtype), o2),
+                     "cb": gtb.storage_from(np.zeros(f["coeff"].shape, dtype), o2),
                      "F": torch.empty(nfac, dtype=torch.uint8, device="cuda")})
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
     def fwd(b):
         gtb.halo_periodic(b["fs"], 2, 2, domain=dom)
-        gtb.hdiff_vadv(b["fs"], b["cs"], b["wcon"], b["ut"], b["uts"], b["y"], domain=dom, workspace=b["F"],
-                       save_factors=True)
+        gtb.hdiff_vadv(b["fs"], b["cs"], b["wcon"], b["ut"], b["uts"], b["y"], prec=prec, domain=dom,
+                       workspace=b["F"], save_factors=True)
 
     def bwd(b, e):
-        gtb.vadv_adj(b["wcon"], b["yb"], b["hb"], b["hb"], domain=dom, workspace=b["F"], factors=True)
+        gtb.vadv_adj(b["wcon"], b["yb"], b["hb"], b["hb"], prec=prec, domain=dom, workspace=b["F"], factors=True)
         e[2].record(stream)
         gtb.hdiff_adj(b["fs"], b["cs"], b["hb"], b["ib"], b["cb"], accumulate=True, domain=dom)
         e[3].record(stream)
@@ -744,12 +752,15 @@ def adjoint_ratio(gtb, f, sets, reps=50):
     es = es[5:]
     mean = lambda a, b: float(np.mean([e[a].elapsed_time(e[b]) for e in es]))
     f_ms, b_ms = mean(0, 1), mean(1, 4)
-    return {"ratio": round(b_ms / f_ms, 3), "forward_ms": round(f_ms, 4), "backward_ms": round(b_ms, 4),
-            "vadv_adj_ms": round(mean(1, 2), 4), "hdiff_adj_ms": round(mean(2, 3), 4),
-            "halo_adj_ms": round(mean(3, 4), 4),
-            "factors_mb_per_step": round(nfac / 1e6, 1),
-            "workload": "one chained step at 256x256x80 FP64 (halo refresh + fused hdiff -> vadv keeping the "
-                        "column factors vs the adjoints)"}
+    out = {"ratio": round(b_ms / f_ms, 3), "forward_ms": round(f_ms, 4), "backward_ms": round(b_ms, 4),
+           "vadv_adj_ms": round(mean(1, 2), 4), "hdiff_adj_ms": round(mean(2, 3), 4),
+           "halo_adj_ms": round(mean(3, 4), 4),
+           "factors_mb_per_step": round(nfac / 1e6, 1),
+           "workload": f"one chained step at 256x256x80 {'FP64' if f64 else 'FP32 storage, double-float columns'} "
+                       "(halo refresh + fused hdiff -> vadv keeping the column factors vs the adjoints)"}
+    del bufs
+    torch.cuda.empty_cache()
+    return out
 
 
 def literal_chain(steps=10):
