@@ -230,17 +230,24 @@ def host_cores():
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
+_POOLS = {}
+
+
 def oracle_slabs(fn, J_, n):
     """Run fn(j0, nj) over n contiguous J-slabs of [0, J_) on n threads (the oracle's C
-    calls release the GIL, so the slabs run on n cores), returning when all are done."""
+    calls release the GIL, so the slabs run on n cores), returning when all are done.
+    The thread pool of each size is created once and kept (its start-up stays out of
+    the timings)."""
     from concurrent.futures import ThreadPoolExecutor
     n = max(1, min(n, J_))
     bounds = [(J_ * q // n, J_ * (q + 1) // n) for q in range(n)]
     if n == 1:
         fn(0, J_)
         return
-    with ThreadPoolExecutor(n) as ex:
-        list(ex.map(lambda b: fn(b[0], b[1] - b[0]), bounds))
+    ex = _POOLS.get(n)
+    if ex is None:
+        ex = _POOLS[n] = ThreadPoolExecutor(n)
+    list(ex.map(lambda b: fn(b[0], b[1] - b[0]), bounds))
 
 
 def oracle_hdiff_par(inp, coeff, out, dom, threads):
