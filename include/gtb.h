@@ -365,7 +365,7 @@ int gtb_probe_fp64_fma(int blocks, int iters, void *sink, void *stream);
 /* Message for the last failed call on this thread ("" if none). */
 const char *gtb_last_error(void);
 
-/* Library version string, e.g. "gtb 0.1 sm_103a". */
+/* Library version string, e.g. "gtb 0.2 sm_103a". */
 const char *gtb_version(void);
 
 #ifdef __cplusplus

@@ -75,8 +75,13 @@ __global__ void __launch_bounds__(32 * W)
 }
 
 // scratch: per CTA a slice of (DPG ? 1 : 2) * k_max * 32*BJ values of N.
+// Registers capped for 28 resident warps per SM: the member descriptor a persistent CTA
+// loads from global memory (six field views and the geometry) stays in registers
+// through the column solve, which left the kernel at 122 registers and 16 warps per
+// SM; the column solve is latency-bound, and the ensemble's replay went 2.26 -> 2.09 ms
+// with the cap despite the spills (capped for 24 or 32 warps: 2.15, 2.21 ms).
 template <typename T, typename N, int BJ>
-__global__ void __launch_bounds__(32 * BJ)
+__global__ void __launch_bounds__(32 * BJ, 28 / BJ)
     vadv_batch_kernel(const BatchVadvMember<T> *__restrict__ mem, int n_mem, int n_items, int *counter,
                       N *__restrict__ scratch, size_t slice, int k_max) {
     constexpr int NT = 32 * BJ;

@@ -841,7 +841,7 @@ extern "C" int gtb_probe_fp64_fma(int blocks, int iters, void *sink, void *strea
 
 extern "C" const char *gtb_last_error(void) { return t_err; }
 
-extern "C" const char *gtb_version(void) { return "gtb 0.1 sm_103a"; }
+extern "C" const char *gtb_version(void) { return "gtb 0.2 sm_103a"; }
 
 // ====================================================================== allocation-free vadv
 // gtb_vadv_noalloc: gtb_vadv with its workspace in a fixed device array of this
