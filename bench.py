@@ -707,7 +707,8 @@ def fused_chain_compare(gtb, f, sets, reps=50):
 def adjoint_ratio(gtb, f, sets, reps=50, dtype=np.float64):
     """Time of one chained step's backward over its forward at 256x256x80 (C ABI,
     preallocated storages), as the differentiable chain runs them: forward = periodic halo
-    refresh + the fused hdiff -> vadv kernel keeping the column factors, backward = vadv_adj
+    refresh + the chained hdiff -> vadv call keeping the column factors (one fused kernel for
+    FP64; hdiff then vadv, h in the workspace, for FP32), backward = vadv_adj
     on those factors (merged u_stage/u_pos cotangent) + hdiff_adj (with coeff_bar) + halo
     fold.  Forward and backward alternate (each backward consumes its forward's factors);
     events around each side give both times.  FP64 storage, or FP32 storage with
@@ -762,9 +763,9 @@ def adjoint_ratio(gtb, f, sets, reps=50, dtype=np.float64):
     out = {"ratio": round(b_ms / f_ms, 3), "forward_ms": round(f_ms, 4), "backward_ms": round(b_ms, 4),
            "vadv_adj_ms": round(mean(1, 2), 4), "hdiff_adj_ms": round(mean(2, 3), 4),
            "halo_adj_ms": round(mean(3, 4), 4),
-           "factors_mb_per_step": round(nfac / 1e6, 1),
+           "workspace_mb_per_step": round(nfac / 1e6, 1),
            "workload": f"one chained step at 256x256x80 {'FP64' if f64 else 'FP32 storage, double-float columns'} "
-                       "(halo refresh + fused hdiff -> vadv keeping the column factors vs the adjoints)"}
+                       "(halo refresh + hdiff -> vadv keeping the column factors vs the adjoints)"}
     del bufs
     torch.cuda.empty_cache()
     return out

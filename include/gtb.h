@@ -204,20 +204,24 @@ int gtb_halo_periodic_adj(const gtb_field *f, int hi, int hj, const int64_t *dom
  * runs):
  *   h               = hdiff(in, coeff)                          (as gtb_hdiff)
  *   utens_stage_out = vadv(u_stage = h, wcon, u_pos = h, utens, utens_stage)
- * in one kernel; h is formed level by level on chip and never written to
- * memory.  The back substitution runs on z = x - h (the same unknowns,
- * utens_stage_out = dtr_stage z), and h's update may be formed in fixed point
- * as in gtb_step, so results agree with gtb_hdiff followed by gtb_vadv to
- * rounding, not bit for bit.
+ * GTB_F64 storage: in one kernel; h is formed level by level on chip and never
+ * written to memory.  The back substitution runs on z = x - h (the same
+ * unknowns, utens_stage_out = dtr_stage z), and h's update may be formed in
+ * fixed point as in gtb_step, so results agree with gtb_hdiff followed by
+ * gtb_vadv to rounding, not bit for bit.  GTB_F32 storage: the two kernels of
+ * gtb_hdiff and gtb_vadv back to back on the stream, h in the workspace (on
+ * B300 the HBM-bound binary32 hdiff and the FP32-pipe column solve run faster
+ * apart than sharing SMs), with gtb_vadv's results bit for bit.
  * Fields: in needs 2 halo points in I and J (as gtb_hdiff), wcon one point
  * above I unless GTB_WCON_LITERAL (as gtb_vadv); coeff, utens, utens_stage
  * and utens_stage_out cover the domain.  utens_stage_out may be the very same
  * view as utens_stage (in place); any other overlap of the output with an
  * input is GTB_ERR_ALIAS.  dtr_stage, beta_v, prec and flags as gtb_vadv.
  * workspace: REQUIRED caller-owned device scratch of at least
- * gtb_hdiff_vadv_workspace_bytes() bytes (c', and e when it cannot be parked
- * in the output), 16-byte aligned, overlapping no field; NULL or too small is
- * GTB_ERR_ARG.  No K limit beyond the workspace size.
+ * gtb_hdiff_vadv_workspace_bytes() bytes (c', e when it cannot be parked in
+ * the output, and h for GTB_F32 storage), 16-byte aligned, overlapping no
+ * field; NULL or too small is GTB_ERR_ARG.  No K limit beyond the workspace
+ * size.
  * flags: GTB_WCON_LITERAL, GTB_SAVE_FACTORS.  With GTB_SAVE_FACTORS the
  * workspace keeps, on return, the factors of the column solve for the adjoint
  * (gtb_vadv_adj with GTB_ADJ_FACTORS): c'_k in its first K*I*J values and

@@ -383,17 +383,22 @@ static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field
 // ------------------------------------------------------------------ vadv
 constexpr int kVadvMaxK = 448;
 
+// Workspace form: c' in ws and the second state array in ws2 (by default right after c'),
+// 1/p_k in rsave when the factors are kept (the chained call's binary32 storage path).
 template <typename T, typename N, int BJ, bool WS>
-static int launch_vadv_t(const gtb_field *const f[6], const VadvGeom &g, void *ws, cudaStream_t st) {
+static int launch_vadv_t(const gtb_field *const f[6], const VadvGeom &g, void *ws, cudaStream_t st,
+                         void *ws2 = nullptr, void *rsave = nullptr) {
     constexpr bool DPG = vadv_dp_global<T, N>();
     auto kern = vadv_kernel<T, N, BJ, DPG, WS>;
     const int smem = WS ? 0 : (int)(vadv_smem_per_col_level<T, N>() * g.K * 32 * BJ);
     if (!WS && prepare_kernel(kern, 227 * 1024) != cudaSuccess)
         return launch_status("vadv: shared-memory attribute");
+    N *w = static_cast<N *>(ws);
+    N *w2 = ws2 ? static_cast<N *>(ws2) : (WS ? w + (size_t)g.K * g.I * g.J : nullptr);
     dim3 block(32, BJ), grid((g.I + 31) / 32, (g.J + BJ - 1) / BJ);
     kern<<<grid, block, smem, st>>>(view_of<const T>(f[0]), view_of<const T>(f[1]), view_of<const T>(f[2]),
-                                    view_of<const T>(f[3]), view_of<const T>(f[4]), view_of<T>(f[5]), g,
-                                    static_cast<N *>(ws));
+                                    view_of<const T>(f[3]), view_of<const T>(f[4]), view_of<T>(f[5]), g, w, w2,
+                                    static_cast<N *>(rsave));
     return launch_status("vadv launch");
 }
 
@@ -496,20 +501,37 @@ static int run_halo(const gtb_field *f, int hi, int hj, const int64_t dom[3], bo
 // ------------------------------------------------------------------ fused hdiff -> vadv
 // Column tile TI x TJ (TI*TJ/32 consumer warps) and PW producer warps per CTA,
 // measured on B300: binary64 runs best with 32 x 2 tiles (1024 CTAs at 256 x 256,
-// every column resident at once, as the FP64 column solve needs), binary32 with
-// 16 x 8 tiles (fewer halo cells per column for its lighter solve).
+// every column resident at once, as the FP64 column solve needs).  Binary32 storage
+// does not use the fused kernel (run_chain32_n).
 template <typename T>
 struct FusedCfg;
 template <> struct FusedCfg<double> { static constexpr int TI = 32, TJ = 2, PW = 2; };
-template <> struct FusedCfg<float> { static constexpr int TI = 16, TJ = 8, PW = 2; };
 constexpr int kFusedStages = 2, kFusedRing = 8;
 
-// Workspace of the fused kernel: c', then 1/p when the factors are kept, then e
-// when it cannot be parked in the output (all [K][I*J] arrays of N).
+// Workspace of the chained call: c', then 1/p when the factors are kept, then e
+// when it cannot be parked in the output (all [K][I*J] arrays of N); for binary32
+// storage then h itself (chain_h_layout), which goes through the workspace there.
 template <typename T, typename N>
-static size_t fused_ws_bytes(const int64_t dom[3], bool save) {
+static size_t fused_state_bytes(const int64_t dom[3], bool save) {
     const size_t arr = sizeof(N) * (size_t)dom[0] * (size_t)dom[1] * (size_t)dom[2];
     return arr * ((vadv_dp_global<T, N>() ? 1 : 2) + (save ? 1 : 0));
+}
+
+// h of the binary32 chained call: rows padded to 32 values (128 bytes), the region
+// 256-byte aligned after the state arrays.  Returns its byte offset; *bytes its size.
+static size_t chain_h_layout(size_t state_bytes, const int64_t dom[3], int64_t *pitch, size_t *bytes) {
+    *pitch = (dom[0] + 31) / 32 * 32;
+    *bytes = sizeof(float) * (size_t)(*pitch) * (size_t)dom[1] * (size_t)dom[2];
+    return (state_bytes + 255) / 256 * 256;
+}
+
+template <typename T, typename N>
+static size_t fused_ws_bytes(const int64_t dom[3], bool save) {
+    const size_t st = fused_state_bytes<T, N>(dom, save);
+    if (sizeof(T) == 8) return st;
+    int64_t pitch;
+    size_t hb;
+    return chain_h_layout(st, dom, &pitch, &hb) + hb;
 }
 
 static size_t fused_ws_bytes_for(int dt, int prec, const int64_t dom[3], bool save) {
@@ -549,6 +571,26 @@ static int run_fused_n(const gtb_field *const f[6], const VadvGeom &g, void *ws,
     const bool tma = encode_in_map<T>(f[0], Tile::BX, Tile::BY, hg, map);
     return tma ? launch_fused_t<T, N, true>(map, f, hg, g, ws, save, st)
                : launch_fused_t<T, N, false>(map, f, hg, g, ws, save, st);
+}
+
+// Binary32 storage: the chain as its two kernels back to back, h through the workspace.
+// On B300 hdiff (coeff staged by TMA, bound by HBM) and the FP32-pipe column solve each
+// run faster on their own than sharing SMs in one kernel (512x512x80, double-float:
+// 49.9 + 218 us against 409 us).  f = {in, coeff, wcon, utens, utens_stage, out}.
+template <typename N>
+static int run_chain32_n(const gtb_field *const f[6], const VadvGeom &g, const int64_t dom[3], void *ws, bool save,
+                         cudaStream_t st) {
+    int64_t pitch;
+    size_t hb;
+    const size_t off = chain_h_layout(fused_state_bytes<float, N>(dom, save), dom, &pitch, &hb);
+    const gtb_field hf{static_cast<unsigned char *>(ws) + off, GTB_F32, 0, {pitch, dom[1], dom[2]},
+                       {1, pitch, pitch * dom[1]}, {0, 0, 0}};
+    int rc;
+    if ((rc = run_hdiff<float>(f[0], f[1], &hf, dom, st))) return rc;
+    const gtb_field *fv[6] = {&hf, f[2], &hf, f[3], f[4], f[5]};  // u_stage = u_pos = h
+    const size_t arr = (size_t)dom[0] * dom[1] * dom[2];
+    N *w = static_cast<N *>(ws);
+    return launch_vadv_t<float, N, 2, true>(fv, g, w, st, w + (save ? 2 : 1) * arr, save ? w + arr : nullptr);
 }
 
 // ------------------------------------------------------------------ co-scheduled step
@@ -731,9 +773,9 @@ extern "C" int gtb_hdiff_vadv(const gtb_field *in, const gtb_field *coeff, const
     const VadvGeom g = make_vadv_geom(dom, literal, dtr_stage, beta_v);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (dt == GTB_F64) return run_fused_n<double, double>(f, g, workspace, save, st);
-    if (prec == GTB_PREC_F64) return run_fused_n<float, double>(f, g, workspace, save, st);
-    if (prec == GTB_PREC_DF) return run_fused_n<float, df>(f, g, workspace, save, st);
-    return run_fused_n<float, float>(f, g, workspace, save, st);
+    if (prec == GTB_PREC_F64) return run_chain32_n<double>(f, g, dom, workspace, save, st);
+    if (prec == GTB_PREC_DF) return run_chain32_n<df>(f, g, dom, workspace, save, st);
+    return run_chain32_n<float>(f, g, dom, workspace, save, st);
 }
 
 extern "C" int gtb_step(const gtb_field *in, const gtb_field *coeff, const gtb_field *hdiff_out,

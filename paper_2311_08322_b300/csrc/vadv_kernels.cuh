@@ -171,12 +171,14 @@ __host__ __device__ constexpr size_t vadv_smem_per_col_level() {
 // terms vanish into the matrix (below); a separate body, so that no FP64 instruction
 // of the general case is issued, even predicated off (the FP64 pipe is the bound).
 // GST: the column state is in global memory (its last reads are streaming loads); else
-// in shared memory.
+// in shared memory.  rsave (global state only, or null): the forward sweep also stores
+// 1/p_k there, [k][column] like c'; c' and 1/p_k are then the factors the adjoint reads
+// (gtb_vadv_adj with GTB_ADJ_FACTORS), and c' is not dropped from L2.
 template <typename T, typename N, int BJ, bool DPG, bool YF, bool SYM, bool GST>
 __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                                const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                                const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
-                                               size_t cidx_ws, bool ws_domain, int tx, int ty) {
+                                               size_t cidx_ws, bool ws_domain, int tx, int ty, N *rsave = nullptr) {
     static_assert(!YF || DPG, "the y form parks d'_k in the output");
     const int i = bx * 32 + tx, j = by * BJ + ty;
     const bool active = (i < g.I) && (j < g.J);
@@ -268,6 +270,7 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
         const N r = recip(p);
         const N cpk = (-a_next) * r, dpk = num * r;
         if (wr) cpb[(size_t)k * cstride + cidx] = cpk;
+        if (rsave && wr) rsave[(size_t)k * cstride + cidx] = r;
         N ek;  // the backward sweep's term of level k: d'_k (YF) or e_k
         if constexpr (YF) {
             ek = dpk;
@@ -325,6 +328,7 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     constexpr int kArrays = (YF || !DPG) ? 2 : 1;
     constexpr int kLines = (int)(32 * sizeof(N) / 128);  // lines per warp, level and array
     const bool own = GST && __all_sync(0xffffffffu, ws_domain ? active : true);
+    const bool keep_cp = rsave != nullptr;  // c' is a kept factor: not dropped
     const size_t c0 = __shfl_sync(0xffffffffu, cidx, 0);
     if (K >= 2) load_group(K - 2);
     for (int k0 = K - 2; k0 >= 0; k0 -= BG) {
@@ -346,7 +350,7 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
                 if (e < BG * kArrays * kLines) {
                     const int m = e % kLines, arr = (e / kLines) % kArrays, q = e / (kLines * kArrays);
                     const int k = k0 - q;
-                    if (k >= 0) {
+                    if (k >= 0 && !(arr == 0 && keep_cp)) {
                         const N *row = (arr == 0 ? cpb : dpb) + (size_t)k * cstride + c0;
                         const unsigned char *line = reinterpret_cast<const unsigned char *>(row) + m * 128;
                         if ((reinterpret_cast<uintptr_t>(line) & 127) == 0) discard_l2_line(line);
@@ -361,29 +365,30 @@ template <typename T, typename N, int BJ, bool DPG, bool YF, bool GST>
 __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                              const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                              const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
-                                             size_t cidx_ws, bool ws_domain, int tx, int ty) {
+                                             size_t cidx_ws, bool ws_domain, int tx, int ty, N *rsave = nullptr) {
     if (g.sym)
         vadv_columns_t<T, N, BJ, DPG, YF, true, GST>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
-                                                ws_domain, tx, ty);
+                                                ws_domain, tx, ty, rsave);
     else
         vadv_columns_t<T, N, BJ, DPG, YF, false, GST>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
-                                                 ws_domain, tx, ty);
+                                                 ws_domain, tx, ty, rsave);
 }
 
 // Single domain: one CTA per 32 x BJ block of columns; WS selects a
-// domain-indexed global workspace over shared memory.
+// domain-indexed global workspace over shared memory: c' in ws, the second state
+// array in ws2, and (rsave, or null) 1/p_k kept for the adjoint.
 template <typename T, typename N, int BJ, bool DPG, bool WS>
 __global__ void __launch_bounds__(32 * BJ)
     vadv_kernel(const View<const T> us, const View<const T> wc, const View<const T> up, const View<const T> ut,
-                const View<const T> uts, const View<T> out, const VadvGeom g, N *__restrict__ ws) {
+                const View<const T> uts, const View<T> out, const VadvGeom g, N *__restrict__ ws,
+                N *__restrict__ ws2, N *__restrict__ rsave) {
     constexpr int NT = 32 * BJ;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int t = threadIdx.y * 32 + threadIdx.x;
     if (WS) {
         const size_t cstride = (size_t)g.I * g.J;
         vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>(), true>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
-                                                        ws + (size_t)g.K * cstride, cstride, 0, true, threadIdx.x,
-                                                        threadIdx.y);
+                                                        ws2, cstride, 0, true, threadIdx.x, threadIdx.y, rsave);
     } else {
         N *cpb = reinterpret_cast<N *>(smem_raw);
         vadv_columns<T, N, BJ, DPG, false, false>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, cpb,

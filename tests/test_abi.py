@@ -163,9 +163,12 @@ def test_hdiff_vadv_validation(L):
     dom = (ctypes.c_int64 * 3)(8, 8, 6)
     assert L.lib().gtb_hdiff_vadv_workspace_bytes(2, 0, 0, dom) == 8 * n       # c' (e parked in the output)
     assert L.lib().gtb_hdiff_vadv_workspace_bytes(2, 0, 4, dom) == 16 * n      # + 1/p (GTB_SAVE_FACTORS)
-    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 2, 0, dom) == 16 * n      # double-float c' and e
-    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 2, 4, dom) == 24 * n
-    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 0, 4, dom) == 8 * n       # binary32 c' and 1/p
+    # binary32 storage: then h itself, rows padded to 32 values, 256-byte aligned after the state
+    h = 4 * 32 * 8 * 6
+    up256 = lambda b: (b + 255) // 256 * 256
+    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 2, 0, dom) == up256(16 * n) + h  # double-float c' and e
+    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 2, 4, dom) == up256(24 * n) + h
+    assert L.lib().gtb_hdiff_vadv_workspace_bytes(1, 0, 4, dom) == up256(8 * n) + h   # binary32 c' and 1/p
     # the workspace with GTB_SAVE_FACTORS must be the larger size
     assert call(fs, flags=4, ws=40 * G, wsb=8 * n) == -9
     # gtb_vadv_adj: GTB_ADJ_FACTORS needs a workspace of the forward's factors
