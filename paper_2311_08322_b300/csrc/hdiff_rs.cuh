@@ -35,6 +35,9 @@ struct Native {
     __device__ __forceinline__ V lap(V c, V e, V w, V n, V s) const { return T(4) * c - (((e + w) + n) + s); }
     __device__ __forceinline__ Gd grad(V x1, V x0, const T *, const T *) const { return x1 - x0; }
     __device__ __forceinline__ V limit(V f, Gd g) const { return (f * g > T(0)) ? T(0) : f; }
+    // limit(f, grad(x1, x0, ...)) in one step; no ties to settle (kTies)
+    static constexpr bool kTies = false;
+    __device__ __forceinline__ V lim(V f, V x1, V x0, bool &) const { return limit(f, x1 - x0); }
     __device__ __forceinline__ T out(T in, T c, V D) const { return in - c * D; }
     __device__ __forceinline__ T outx(T in, V, T c, V D) const { return out(in, c, D); }
 };
@@ -55,6 +58,16 @@ struct FixedF64T {
         return exact_dir(x1, x0, *p1, *p0);
     }
     __device__ __forceinline__ V limit(V f, Gd g) const { return ((f > 0 && g > 0) || (f < 0 && g < 0)) ? 0 : f; }
+    // limit(f, grad(x1, x0, ...)) from the fixed-point values alone: f is zeroed where f
+    // and d = X1 - X0 have the same strict sign (sign bits equal, d != 0; f = 0 stays 0).
+    // Where X1 == X0 the binary64 values may still differ below the fixed point's unit:
+    // tie is raised, and the caller settles the row with grad before using its fluxes.
+    static constexpr bool kTies = true;
+    __device__ __forceinline__ V lim(V f, V x1, V x0, bool &tie) const {
+        const V d = x1 - x0;
+        tie |= d == 0;
+        return ((f ^ d) >= 0 && d != 0) ? V(0) : f;
+    }
     __device__ __forceinline__ double out(double in, double c, V D) const {
         return fma(-c, ICVT ? from_fixed_int(D, E) : from_fixed(D, E), in);
     }
@@ -208,10 +221,19 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
         }
         if (t >= 0) {
             // fy(row t-1) = lap(t) - lap(t-1), gradient in(t) - in(t-1)
+            // the fluxes from the policy's fast limiter (lim); a tie anywhere in the warp
+            // (fixed point only) recomputes the row's fluxes with the exact gradient sign
+            bool tie = false;
             V fyc[CPL];
+            auto fy_exact = [&]() {
 #pragma unroll
-            for (int q = 0; q < CPL; ++q)
-                fyc[q] = pol.limit(lc[q] - lp[q], pol.grad(xb[q], xa[q], ptr(ci0 + q, cj0 + t), ptr(ci0 + q, cj0 + t - 1)));
+                for (int q = 0; q < CPL; ++q)
+                    fyc[q] = pol.limit(lc[q] - lp[q],
+                                       pol.grad(xb[q], xa[q], ptr(ci0 + q, cj0 + t), ptr(ci0 + q, cj0 + t - 1)));
+            };
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) fyc[q] = pol.lim(lc[q] - lp[q], xb[q], xa[q], tie);
+            if (t == 0 && P::kTies && __any_sync(0xffffffffu, tie)) fy_exact();
             if (t >= 1) {
                 // output row j = t-1: fx(row j) from lap(t-1) (= lp) of this lane and its right neighbour
                 const int j = t - 1;
@@ -223,11 +245,25 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
                 for (int q = 0; q < CPL; ++q) {
                     const V ln = (q == CPL - 1) ? lnext : lp[q + 1];
                     const V xn = (q == CPL - 1) ? nbR_prev : xa[q + 1];
-                    fx[q] = pol.limit(ln - lp[q], pol.grad(xn, xa[q], ptr(ci0 + q + 1, cj0 + j), ptr(ci0 + q, cj0 + j)));
+                    fx[q] = pol.lim(ln - lp[q], xn, xa[q], tie);
+                }
+                // fx(i = -1) = lap(0) - lap(-1), lane 0's (every lane evaluates it)
+                bool tie0 = false;
+                V fx0 = pol.lim(lp[0] - el, xa[0], nbL_prev, tie0);
+                tie |= lane == 0 && tie0;
+                if (P::kTies && __any_sync(0xffffffffu, tie)) {
+                    fy_exact();
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) {
+                        const V ln = (q == CPL - 1) ? lnext : lp[q + 1];
+                        const V xn = (q == CPL - 1) ? nbR_prev : xa[q + 1];
+                        fx[q] = pol.limit(ln - lp[q],
+                                          pol.grad(xn, xa[q], ptr(ci0 + q + 1, cj0 + j), ptr(ci0 + q, cj0 + j)));
+                    }
+                    fx0 = pol.limit(lp[0] - el, pol.grad(xa[0], nbL_prev, ptr(0, cj0 + j), ptr(-1, cj0 + j)));
                 }
                 V fxw = __shfl_up_sync(0xffffffffu, fx[CPL - 1], 1);
-                if (lane == 0)  // fx(i = -1) = lap(0) - lap(-1)
-                    fxw = pol.limit(lp[0] - el, pol.grad(xa[0], nbL_prev, ptr(0, cj0 + j), ptr(-1, cj0 + j)));
+                if (lane == 0) fxw = fx0;
                 T r[CPL], xin[CPL];
                 row(cj0 + j, xin);
 #pragma unroll
