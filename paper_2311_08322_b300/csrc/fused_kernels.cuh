@@ -100,6 +100,7 @@ __device__ __forceinline__ void fused_hdiff_level(const P &pol, const C &c, type
     using V = typename P::V;
     using Tile = FusedTile<T, TI, TJ>;
     constexpr int NPT = 32 * PW, PPT = (Tile::NC + NPT - 1) / NPT;
+    static_assert(!P::kTies || Tile::NC % NPT == 0, "the tie vote needs every producer lane on every point");
     for_cells<Tile::LW, Tile::LH, NPT>(pt, [&](int idx, int la, int lb) {
         const int li = la - 1, lj = lb - 1;
         Lw[idx] = pol.lap(c.x(li, lj), c.x(li + 1, lj), c.x(li - 1, lj), c.x(li, lj + 1), c.x(li, lj - 1));
@@ -111,10 +112,19 @@ __device__ __forceinline__ void fused_hdiff_level(const P &pol, const C &c, type
         if (Tile::NC % NPT != 0 && p >= Tile::NC) break;
         const int ci = p % TI, cj = p / TI;
         const V x0 = c.x(ci, cj), l0 = c.lap(ci, cj);
-        const V fxe = pol.limit(c.lap(ci + 1, cj) - l0, pol.grad(c.x(ci + 1, cj), x0, c.sp(ci + 1, cj), c.sp(ci, cj)));
-        const V fxw = pol.limit(l0 - c.lap(ci - 1, cj), pol.grad(x0, c.x(ci - 1, cj), c.sp(ci, cj), c.sp(ci - 1, cj)));
-        const V fyn = pol.limit(c.lap(ci, cj + 1) - l0, pol.grad(c.x(ci, cj + 1), x0, c.sp(ci, cj + 1), c.sp(ci, cj)));
-        const V fys = pol.limit(l0 - c.lap(ci, cj - 1), pol.grad(x0, c.x(ci, cj - 1), c.sp(ci, cj), c.sp(ci, cj - 1)));
+        // the policy's fast limiter; a fixed-point tie anywhere in the warp recomputes
+        // the cell's fluxes with the exact gradient sign (every lane is here: NC % NPT == 0)
+        bool tie = false;
+        V fxe = pol.lim(c.lap(ci + 1, cj) - l0, c.x(ci + 1, cj), x0, tie);
+        V fxw = pol.lim(l0 - c.lap(ci - 1, cj), x0, c.x(ci - 1, cj), tie);
+        V fyn = pol.lim(c.lap(ci, cj + 1) - l0, c.x(ci, cj + 1), x0, tie);
+        V fys = pol.lim(l0 - c.lap(ci, cj - 1), x0, c.x(ci, cj - 1), tie);
+        if (P::kTies && __any_sync(0xffffffffu, tie)) {
+            fxe = pol.limit(c.lap(ci + 1, cj) - l0, pol.grad(c.x(ci + 1, cj), x0, c.sp(ci + 1, cj), c.sp(ci, cj)));
+            fxw = pol.limit(l0 - c.lap(ci - 1, cj), pol.grad(x0, c.x(ci - 1, cj), c.sp(ci, cj), c.sp(ci - 1, cj)));
+            fyn = pol.limit(c.lap(ci, cj + 1) - l0, pol.grad(c.x(ci, cj + 1), x0, c.sp(ci, cj + 1), c.sp(ci, cj)));
+            fys = pol.limit(l0 - c.lap(ci, cj - 1), pol.grad(x0, c.x(ci, cj - 1), c.sp(ci, cj), c.sp(ci, cj - 1)));
+        }
         const V D = (fxe - fxw) + (fyn - fys);
         em.put(m, p, pol.outx(*c.sp(ci, cj), x0, cf[q], D));
     }
