@@ -391,12 +391,33 @@ __device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const CUt
                     fence_proxy_async_shared();  // before the stage's next TMA refill
                     __syncwarp();
                 }
-                unsigned emax = 0;
-                for (int idx = lane; idx < wx * wy; idx += 32) {
-                    const int bx = idx % wx + xs, by = idx / wx + cj0;
-                    emax = max(emax, ((unsigned)__double2hiint(S[by * G::BX + bx]) >> 20) & 0x7FFu);
+                // the maximum of the exponent fields (hi word & 0x7FF00000, monotone in the
+                // exponent): each lane its own columns of every row, 16-byte loads where the
+                // box column allows; then the four columns outside the lanes' (-2, -1, TI, TI+1)
+                unsigned em = 0;
+                const int c0 = lane * CPL;
+                const bool vsm = ((2 + xs) % CPL) == 0;
+#pragma unroll
+                for (int r = 0; r < R + 4; ++r) {
+                    if (r < wy) {
+                        const T *rp = S + (cj0 + r) * G::BX + c0 + 2 + xs;
+                        T v[CPL];
+                        if (vsm) {
+                            load_vec<T, CPL>(rp, v);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < CPL; ++q) v[q] = rp[q];
+                        }
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q)
+                            if (c0 + q < wx - 2) em = max(em, (unsigned)__double2hiint(v[q]) & 0x7FF00000u);
+                    }
                 }
-                const int E = (int)__reduce_max_sync(0xffffffffu, emax);
+                for (int idx = lane; idx < 4 * wy; idx += 32) {
+                    const int sd = idx & 3, c = sd < 2 ? sd - 2 : G::TI + sd - 2;
+                    if (c < wx - 2) em = max(em, (unsigned)__double2hiint(S[(cj0 + (idx >> 2)) * G::BX + c + 2 + xs]) & 0x7FF00000u);
+                }
+                const int E = (int)(__reduce_max_sync(0xffffffffu, em) >> 20);
                 if (E >= 64 && E <= 2040)
                     rs_strip<T, CPL, R, G::BX>(FixedF64{E}, S, xs, cj0, ncols, nrows, cfp, cf_sj, op, out.sj,
                                                cf_vec != 0, vec_ok != 0);
