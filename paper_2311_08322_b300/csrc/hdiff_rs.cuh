@@ -181,7 +181,11 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
             lp[q] = V(0), fyp[q] = V(0);
         }
     }
-    // coeff ring: at the top of iteration t, cf0 .. cf4 hold rows t-1 .. t+3 (16-byte loads when aligned)
+    // coeff ring: at the top of iteration t, cf[0] .. cf[NCF-1] hold rows t-1 .. t+NCF-2
+    // (16-byte loads when aligned); a row is loaded NCF iterations before its use.  The
+    // binary64 strip's short fixed-point rows need the loads further ahead (measured on
+    // B300 at 256x256x80: 55.7 us with 5 rows, 52.9 with 9, 54.9 with 11, 55.8 with 13)
+    constexpr int NCF = sizeof(T) == 8 ? 9 : 5;
     auto load_cf = [&](int rw, T (&v)[CPL]) {
         if (rw >= 0 && rw < nrows) {
             const T *c = cfp + (int64_t)(cj0 + rw) * cf_sj;
@@ -196,12 +200,11 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
             for (int q = 0; q < CPL; ++q) v[q] = T(0);
         }
     };
-    T cf0[CPL], cf1[CPL], cf2[CPL], cf3[CPL], cf4[CPL];
+    T cf[NCF][CPL];
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) cf0[q] = T(0), cf1[q] = T(0);
-    load_cf(0, cf2);
-    load_cf(1, cf3);
-    load_cf(2, cf4);
+    for (int q = 0; q < CPL; ++q) cf[0][q] = T(0), cf[1][q] = T(0);
+#pragma unroll
+    for (int i = 2; i < NCF; ++i) load_cf(i - 2, cf[i]);
     // iteration t computes lap(row t) for t = -1 .. R and emits out(row t-1) for t >= 1;
     // fully unrolled, so the rolling rows need no register moves
 #pragma unroll
@@ -270,7 +273,7 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
                 for (int q = 0; q < CPL; ++q) {
                     const V fwq = (q == 0) ? fxw : fx[q - 1];
                     const V D = (fx[q] - fwq) + (fyc[q] - fyp[q]);
-                    r[q] = pol.out(xin[q], cf0[q], D);
+                    r[q] = pol.out(xin[q], cf[0][q], D);
                 }
                 if (j < nrows) {
                     T *o = op + (int64_t)(cj0 + j) * out_sj;
@@ -297,8 +300,10 @@ __device__ __forceinline__ void rs_strip(const P &pol, const T *S, int xs, int c
         }
         nbL_prev = up, nbR_prev = dn;
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) cf0[q] = cf1[q], cf1[q] = cf2[q], cf2[q] = cf3[q], cf3[q] = cf4[q];
-        load_cf(t + 4, cf4);
+        for (int i = 0; i + 1 < NCF; ++i)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) cf[i][q] = cf[i + 1][q];
+        load_cf(t + NCF - 1, cf[NCF - 1]);
     }
 }
 
