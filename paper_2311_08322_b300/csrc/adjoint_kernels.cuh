@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(32 * BJ)
             N a_next = zero;
             if (k + 1 < K) a_next = coef<N>(face_of(wk1, w1k1), ka, kexp);
             const N b = (dtr - a_cur) + a_next;
-            const N p = (k > 0) ? b - a_cur * cp_prev : b;
+            const N p = (k > 0) ? fms(b, a_cur, cp_prev) : b;
             const N r = recip(p);
             const N U = (k > 0) ? addx<N, T>(-(cp_prev * U_prev), yk) : to_num<N, T>(yk);
             const N cpk = (-a_next) * r;

@@ -238,12 +238,14 @@ __device__ __forceinline__ df operator*(df x, df y) {
     return fast_two_sum(c.hi, cl3);
 }
 
-// Reciprocal of a double-word: th = 1/y.hi in binary32, refined by one Newton
-// step whose residual e = (1 - y.hi*th) - y.lo*th is formed with FMAs (the
-// first product-difference is exact to within one rounding of a value of
-// size ~2^-24); result th + th*e as a double-word, relative error ~2^-46.
+// Reciprocal of a double-word: th ~ 1/y.hi from the hardware approximation
+// (rcp.approx.f32, within about one binary32 ulp), refined by one Newton step
+// whose residual e = (1 - y.hi*th) - y.lo*th is formed with FMAs (the first
+// product-difference is exact to within one rounding of a value of size
+// ~2^-22); result th + th*e as a double-word, relative error ~2^-44.
 __device__ __forceinline__ df recip(df y) {
-    const float th = __frcp_rn(y.hi);
+    float th;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(th) : "f"(y.hi));
     float e = __fmaf_rn(-y.hi, th, 1.0f);
     e = __fmaf_rn(-y.lo, th, e);
     return fast_two_sum(th, __fmul_rn(th, e));

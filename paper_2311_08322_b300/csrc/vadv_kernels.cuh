@@ -264,7 +264,7 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
         }
         N p = b, num = d;
         if (k > 0) {
-            p = b - a_cur * cp_prev;  // as the adjoint refactorises it (kept factors match bit for bit)
+            p = fms(b, a_cur, cp_prev);  // as the adjoint refactorises it (kept factors match bit for bit)
             num = fms(d, a_cur, dp_prev);
         }
         const N r = recip(p);
