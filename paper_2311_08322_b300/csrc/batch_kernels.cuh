@@ -79,9 +79,11 @@ __global__ void __launch_bounds__(32 * W)
 // loads from global memory (six field views and the geometry) stays in registers
 // through the column solve, which left the kernel at 122 registers and 16 warps per
 // SM; the column solve is latency-bound, and the ensemble's replay went 2.26 -> 2.09 ms
-// with the cap despite the spills (capped for 24 or 32 warps: 2.15, 2.21 ms).
+// with the cap despite the spills (capped for 24 or 32 warps: 2.15, 2.21 ms).  Column
+// pairs (two double-float columns a thread) capped for 12 warps: 2.03 ms, against 2.25
+// at 28 warps (1.2 KB of spills), 2.05 at 16 and 2.43 at 8.
 template <typename T, typename N, int BJ>
-__global__ void __launch_bounds__(32 * BJ, 28 / BJ)
+__global__ void __launch_bounds__(32 * BJ, (is_pair<T>() ? 12 : 28) / BJ)
     vadv_batch_kernel(const BatchVadvMember<T> *__restrict__ mem, int n_mem, int n_items, int *counter,
                       N *__restrict__ scratch, size_t slice, int k_max) {
     constexpr int NT = 32 * BJ;

@@ -383,11 +383,45 @@ static int run_hdiff(const gtb_field *fin, const gtb_field *fcf, const gtb_field
 // ------------------------------------------------------------------ vadv
 constexpr int kVadvMaxK = 448;
 
+// A binary32 field as pairs of columns (fpair): its domain column 0 8-byte aligned and
+// its strides even, so that column 2i starts a pair.
+static bool pairs_fit(const gtb_field *f) {
+    const View<float> v = view_of<float>(f);
+    return reinterpret_cast<uintptr_t>(v.p) % 8 == 0 && v.sj % 2 == 0 && v.sk % 2 == 0;
+}
+template <typename C>
+static View<C> pair_view(const gtb_field *f) {
+    const View<float> v = view_of<float>(f);
+    return View<C>{reinterpret_cast<C *>(v.p), v.sj / 2, v.sk / 2};
+}
+
+// Double-float columns two per thread (packed binary32 pairs): I even and every field
+// pair-aligned; the workspace and the kept factors keep the one-column layout.
+template <int BJ>
+static int launch_vadv_pairs(const gtb_field *const f[6], const VadvGeom &g, void *ws, cudaStream_t st, void *ws2,
+                             void *rsave) {
+    VadvGeom gp = g;
+    gp.I = g.I / 2;
+    dfpair *w = static_cast<dfpair *>(ws);
+    dfpair *w2 = ws2 ? static_cast<dfpair *>(ws2) : w + (size_t)gp.K * gp.I * gp.J;
+    dim3 block(32, BJ), grid((gp.I + 31) / 32, (gp.J + BJ - 1) / BJ);
+    vadv_kernel<fpair, dfpair, BJ, false, true><<<grid, block, 0, st>>>(
+        pair_view<const fpair>(f[0]), pair_view<const fpair>(f[1]), pair_view<const fpair>(f[2]),
+        pair_view<const fpair>(f[3]), pair_view<const fpair>(f[4]), pair_view<fpair>(f[5]), gp, w, w2,
+        static_cast<dfpair *>(rsave));
+    return launch_status("vadv launch");
+}
+
 // Workspace form: c' in ws and the second state array in ws2 (by default right after c'),
 // 1/p_k in rsave when the factors are kept (the chained call's binary32 storage path).
 template <typename T, typename N, int BJ, bool WS>
 static int launch_vadv_t(const gtb_field *const f[6], const VadvGeom &g, void *ws, cudaStream_t st,
                          void *ws2 = nullptr, void *rsave = nullptr) {
+    if constexpr (std::is_same<T, float>::value && std::is_same<N, df>::value && WS) {
+        bool fit = g.I % 2 == 0;
+        for (int q = 0; q < 6; ++q) fit = fit && pairs_fit(f[q]);
+        if (fit) return launch_vadv_pairs<BJ>(f, g, ws, st, ws2, rsave);
+    }
     constexpr bool DPG = vadv_dp_global<T, N>();
     auto kern = vadv_kernel<T, N, BJ, DPG, WS>;
     const int smem = WS ? 0 : (int)(vadv_smem_per_col_level<T, N>() * g.K * 32 * BJ);
@@ -1147,14 +1181,65 @@ static int batch_hdiff_launch_info(int ctas_per_sm, int *slots, void (**kern)(co
     return GTB_OK;
 }
 
-template <typename T, typename N, int BJ>
-static int batch_vadv_launch_info(int ctas_per_sm, int *slots, void (**kern)(const BatchVadvMember<T> *, int, int, int *, N *, size_t, int)) {
-    auto k = vadv_batch_kernel<T, N, BJ>;
+// The column-solve stage of a plan in storage type TV and arithmetic NV: members longest
+// column first (so the queue ends with short items), their device table, per-CTA scratch,
+// and the launch arguments (the stage is launched by cudaLaunchKernel inside the capture).
+struct VadvStageLaunch {
+    const void *func;
+    void *vmem, *scratch;
+    size_t slice;
+    int n, items, k_max;
+};
+
+template <typename TV, typename NV, int BJ>
+static int plan_vadv_stage(const gtb_member *mem, int n, bool literal, double dtr, double beta, int k_max, gtb_plan *P,
+                           VadvStageLaunch *L) {
+    std::vector<int> vorder(n);
+    for (int q = 0; q < n; ++q) vorder[q] = q;
+    std::stable_sort(vorder.begin(), vorder.end(), [&](int a, int b) { return mem[a].domain[2] > mem[b].domain[2]; });
+    std::vector<BatchVadvMember<TV>> vm(n);
+    constexpr bool PAIRS = is_pair<TV>();
+    auto view = [](const gtb_field *f) {
+        if constexpr (PAIRS) return pair_view<const fpair>(f);
+        else return view_of<const TV>(f);
+    };
+    int vitems = 0;
+    for (int r = 0; r < n; ++r) {
+        const gtb_member &M = mem[vorder[r]];
+        VadvGeom g = make_vadv_geom(M.domain, literal, dtr, beta);
+        if (PAIRS) g.I /= 2;  // pairs of columns
+        const int bx = (g.I + 31) / 32, by = (g.J + BJ - 1) / BJ;
+        const View<const TV> h = view(&M.h);
+        View<TV> out;
+        if constexpr (PAIRS) out = pair_view<fpair>(&M.out);
+        else out = view_of<TV>(&M.out);
+        vm[r] = BatchVadvMember<TV>{h, view(&M.wcon), h, view(&M.utens), view(&M.utens_stage), out, g, bx, vitems};
+        vitems += bx * by;
+    }
+    auto k = vadv_batch_kernel<TV, NV, BJ>;
     int rb = resident_blocks(k, 32 * BJ, 0);
-    if (ctas_per_sm > 0) rb = std::min(rb, ctas_per_sm);
-    *slots = rb * sm_count();
-    *kern = k;
+    if (P->cfg.ctas_per_sm > 0) rb = std::min(rb, P->cfg.ctas_per_sm);
+    P->v_items = vitems;
+    P->v_grid = std::max(1, std::min(vitems, rb * sm_count()));
+    const size_t slice = (size_t)vadv_state_arrays<TV, NV>() * k_max * 32 * BJ;
+    cudaError_t e;
+    if ((e = cudaMalloc(&P->d_vmem, sizeof(BatchVadvMember<TV>) * n)) ||
+        (e = cudaMalloc(&P->d_scratch, sizeof(NV) * slice * P->v_grid)) ||
+        (e = cudaMemcpy(P->d_vmem, vm.data(), sizeof(BatchVadvMember<TV>) * n, cudaMemcpyHostToDevice)))
+        return fail(GTB_ERR_LAUNCH, "gtb_batch_plan: column-solve tables: %s", cudaGetErrorString(e));
+    *L = VadvStageLaunch{reinterpret_cast<const void *>(k), P->d_vmem, P->d_scratch, slice, n, vitems, k_max};
     return GTB_OK;
+}
+
+// Members whose binary32 fields all fit column pairs (even I, pair-aligned fields).
+static bool batch_pairs_fit(const gtb_member *mem, int n) {
+    for (int q = 0; q < n; ++q) {
+        const gtb_member &M = mem[q];
+        if (M.domain[0] % 2 || !pairs_fit(&M.h) || !pairs_fit(&M.wcon) || !pairs_fit(&M.utens) ||
+            !pairs_fit(&M.utens_stage) || !pairs_fit(&M.out))
+            return false;
+    }
+    return true;
 }
 
 template <typename T, typename N, int V, int BJ, bool CTMA>
@@ -1167,8 +1252,6 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
     constexpr int MPM = CTMA ? 2 : 1;  // tensor maps per member: in (and coeff)
     std::vector<CUtensorMap> maps(MPM * n);
     std::vector<BatchHdiffMember<T>> hm(n);
-    std::vector<BatchVadvMember<T>> vm(n);
-    std::vector<int> vorder(n);
     int k_max = 1;
     double pts = 0;
     // hdiff members in the given order
@@ -1210,38 +1293,27 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
         k_max = std::max(k_max, g.K);
         pts += (double)g.I * g.J * g.K;
     }
-    // vadv members longest column first (largest K), so the queue ends with short items
-    for (int q = 0; q < n; ++q) vorder[q] = q;
-    std::stable_sort(vorder.begin(), vorder.end(), [&](int a, int b) { return mem[a].domain[2] > mem[b].domain[2]; });
     const bool literal = flags & GTB_WCON_LITERAL;
-    int vitems = 0;
-    for (int r = 0; r < n; ++r) {
-        const gtb_member &M = mem[vorder[r]];
-        const VadvGeom g = make_vadv_geom(M.domain, literal, dtr, beta);
-        const int bx = (g.I + 31) / 32, by = (g.J + BJ - 1) / BJ;
-        const View<const T> h = view_of<const T>(&M.h);
-        vm[r] = BatchVadvMember<T>{h, view_of<const T>(&M.wcon), h, view_of<const T>(&M.utens),
-                                   view_of<const T>(&M.utens_stage), view_of<T>(&M.out), g, bx, vitems};
-        vitems += bx * by;
-    }
     void (*hk)(const CUtensorMap *, const BatchHdiffMember<T> *, int, int, int *);
-    void (*vk)(const BatchVadvMember<T> *, int, int, int *, N *, size_t, int);
-    int hslots, vslots, hsmem, rc;
+    int hslots, hsmem, rc;
     if ((rc = batch_hdiff_launch_info<T, V, CTMA>(P->cfg.ctas_per_sm, &hslots, &hk, &hsmem))) return rc;
-    if ((rc = batch_vadv_launch_info<T, N, BJ>(P->cfg.ctas_per_sm, &vslots, &vk))) return rc;
-    P->h_items = hitems, P->v_items = vitems;
+    P->h_items = hitems;
     P->h_grid = std::max(1, std::min(hitems, hslots));
-    P->v_grid = std::max(1, std::min(vitems, vslots));
     P->points = pts;
-    const size_t slice = (size_t)vadv_state_arrays<T, N>() * k_max * 32 * BJ;
+    VadvStageLaunch vl{};
+    if constexpr (std::is_same<T, float>::value && std::is_same<N, df>::value) {
+        rc = batch_pairs_fit(mem, n) ? plan_vadv_stage<fpair, dfpair, BJ>(mem, n, literal, dtr, beta, k_max, P, &vl)
+                                     : plan_vadv_stage<T, N, BJ>(mem, n, literal, dtr, beta, k_max, P, &vl);
+    } else {
+        rc = plan_vadv_stage<T, N, BJ>(mem, n, literal, dtr, beta, k_max, P, &vl);
+    }
+    if (rc) return rc;
     cudaError_t e;
     if ((e = cudaMalloc(&P->d_maps, sizeof(CUtensorMap) * MPM * n)) || (e = cudaMalloc(&P->d_hmem, sizeof(BatchHdiffMember<T>) * n)) ||
-        (e = cudaMalloc(&P->d_vmem, sizeof(BatchVadvMember<T>) * n)) || (e = cudaMalloc(&P->d_counters, 2 * sizeof(int))) ||
-        (e = cudaMalloc(&P->d_scratch, sizeof(N) * slice * P->v_grid)))
+        (e = cudaMalloc(&P->d_counters, 2 * sizeof(int))))
         return fail(GTB_ERR_LAUNCH, "gtb_batch_plan: device tables: %s", cudaGetErrorString(e));
     if ((e = cudaMemcpy(P->d_maps, maps.data(), sizeof(CUtensorMap) * MPM * n, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(P->d_hmem, hm.data(), sizeof(BatchHdiffMember<T>) * n, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(P->d_vmem, vm.data(), sizeof(BatchVadvMember<T>) * n, cudaMemcpyHostToDevice)))
+        (e = cudaMemcpy(P->d_hmem, hm.data(), sizeof(BatchHdiffMember<T>) * n, cudaMemcpyHostToDevice)))
         return fail(GTB_ERR_LAUNCH, "gtb_batch_plan: table upload: %s", cudaGetErrorString(e));
     // capture: reset the two queues, hdiff stage, vadv stage
     cudaStream_t cs;
@@ -1252,8 +1324,9 @@ static int build_plan(const gtb_member *mem, int n, double dtr, double beta, uns
         cudaMemsetAsync(P->d_counters, 0, 2 * sizeof(int), cs);
         hk<<<P->h_grid, 32 * W, hsmem, cs>>>(static_cast<const CUtensorMap *>(P->d_maps),
                                              static_cast<const BatchHdiffMember<T> *>(P->d_hmem), n, hitems, P->d_counters);
-        vk<<<P->v_grid, dim3(32, BJ), 0, cs>>>(static_cast<const BatchVadvMember<T> *>(P->d_vmem), n, vitems,
-                                               P->d_counters + 1, static_cast<N *>(P->d_scratch), slice, k_max);
+        int *vcounter = P->d_counters + 1;
+        void *args[] = {&vl.vmem, &vl.n, &vl.items, &vcounter, &vl.scratch, &vl.slice, &vl.k_max};
+        cudaLaunchKernel(vl.func, dim3(P->v_grid), dim3(32, BJ), args, 0, cs);
         e = cudaStreamEndCapture(cs, &P->graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, P->graph, 0);

@@ -279,6 +279,119 @@ __device__ __forceinline__ float df_mul_to_float(df y, df z) {
     return __fmaf_rn(y.hi, z.hi, __fmaf_rn(y.hi, z.lo, __fmul_rn(y.lo, z.hi)));
 }
 
+// ---------------------------------------------------------------- packed pairs
+// Two binary32 values in one 64-bit register (the lower-addressed one in the low
+// half, as a float2 in memory) and the paired instructions of the sm_100 family
+// (add/sub/mul/fma .rn.f32x2): each half rounds exactly as the binary32 operation
+// alone, so a thread runs two columns' arithmetic in one issue slot per operation
+// with each column's result bit for bit that of the scalar form.
+struct fpair {
+    unsigned long long v;
+};
+__device__ __forceinline__ fpair fp_add(fpair a, fpair b) {
+    fpair d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ fpair fp_sub(fpair a, fpair b) {
+    fpair d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+// The product as fma(a, b, -0): the same value as the rounded product, sign included.
+// The code generator fuses a paired multiply into a following paired add or subtract
+// although both carry .rn (the scalar __fmul_rn never is), and it treats an fma whose
+// addend is a literal -0 as a multiply; a __constant__ addend (which the host may
+// rewrite, so neither compiler folds it) leaves nothing to fuse, and every operation
+// keeps its own rounding, as in the scalar form.
+__constant__ unsigned long long g_fp_negzero = 0x8000000080000000ull;
+__device__ __forceinline__ fpair fp_mul(fpair a, fpair b) {
+    fpair d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(g_fp_negzero));
+    return d;
+}
+__device__ __forceinline__ fpair fp_fma(fpair a, fpair b, fpair c) {
+    fpair d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+__device__ __forceinline__ fpair fp_neg(fpair a) { return fpair{a.v ^ 0x8000000080000000ull}; }
+__device__ __forceinline__ fpair fp_make(float x, float y) {
+    return fpair{(unsigned long long)__float_as_uint(x) | ((unsigned long long)__float_as_uint(y) << 32)};
+}
+__device__ __forceinline__ fpair fp_splat(float x) { return fp_make(x, x); }
+__device__ __forceinline__ float fp_x(fpair a) { return __uint_as_float((unsigned)a.v); }
+__device__ __forceinline__ float fp_y(fpair a) { return __uint_as_float((unsigned)(a.v >> 32)); }
+__device__ __forceinline__ fpair fp_zero() { return fpair{0ull}; }
+
+// Two columns' double-floats: the high parts in one pair, the low parts in the other;
+// every operation is the df operation above, element by element.
+struct dfpair {
+    fpair hi, lo;
+};
+__device__ __forceinline__ dfpair two_sum(fpair a, fpair b) {
+    const fpair s = fp_add(a, b);
+    const fpair bb = fp_sub(s, a);
+    const fpair e = fp_add(fp_sub(a, fp_sub(s, bb)), fp_sub(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ dfpair fast_two_sum(fpair a, fpair b) {
+    const fpair s = fp_add(a, b);
+    return {s, fp_sub(b, fp_sub(s, a))};
+}
+__device__ __forceinline__ dfpair two_prod(fpair a, fpair b) {
+    const fpair p = fp_mul(a, b);
+    return {p, fp_fma(a, b, fp_neg(p))};
+}
+__device__ __forceinline__ dfpair operator+(dfpair x, dfpair y) {
+    const dfpair s = two_sum(x.hi, y.hi);
+    const fpair v = fp_add(x.lo, y.lo);
+    const fpair w = fp_add(s.lo, v);
+    return fast_two_sum(s.hi, w);
+}
+__device__ __forceinline__ dfpair operator-(dfpair x) { return {fp_neg(x.hi), fp_neg(x.lo)}; }
+__device__ __forceinline__ dfpair operator-(dfpair x, dfpair y) { return x + (-y); }
+__device__ __forceinline__ dfpair operator+(dfpair x, fpair y) {
+    const dfpair s = two_sum(x.hi, y);
+    const fpair v = fp_add(x.lo, s.lo);
+    return fast_two_sum(s.hi, v);
+}
+__device__ __forceinline__ dfpair operator*(dfpair x, fpair y) {
+    const dfpair c = two_prod(x.hi, y);
+    const fpair cl3 = fp_fma(x.lo, y, c.lo);
+    return fast_two_sum(c.hi, cl3);
+}
+__device__ __forceinline__ dfpair operator*(dfpair x, dfpair y) {
+    const dfpair c = two_prod(x.hi, y.hi);
+    fpair tl = fp_mul(x.hi, y.lo);
+    tl = fp_fma(x.lo, y.hi, tl);
+    const fpair cl3 = fp_add(c.lo, tl);
+    return fast_two_sum(c.hi, cl3);
+}
+__device__ __forceinline__ dfpair recip(dfpair y) {
+    float t0, t1;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(t0) : "f"(fp_x(y.hi)));
+    asm("rcp.approx.f32 %0, %1;" : "=f"(t1) : "f"(fp_y(y.hi)));
+    const fpair th = fp_make(t0, t1);
+    fpair e = fp_fma(fp_neg(y.hi), th, fp_splat(1.0f));
+    e = fp_fma(fp_neg(y.lo), th, e);
+    return fast_two_sum(th, fp_mul(th, e));
+}
+__device__ __forceinline__ dfpair df_add2(fpair a, fpair b) { return two_sum(a, b); }
+__device__ __forceinline__ dfpair df_fms(dfpair x, dfpair y, dfpair z) {
+    const fpair ph = fp_mul(y.hi, z.hi);
+    fpair pl = fp_fma(y.hi, z.hi, fp_neg(ph));
+    pl = fp_fma(y.hi, z.lo, pl);
+    pl = fp_fma(y.lo, z.hi, pl);
+    const dfpair s = two_sum(x.hi, fp_neg(ph));
+    const fpair t = fp_add(fp_sub(x.lo, pl), s.lo);
+    return fast_two_sum(s.hi, t);
+}
+__device__ __forceinline__ dfpair df_fma(dfpair x, dfpair y, dfpair z) { return df_fms(x, -y, z); }
+__device__ __forceinline__ fpair df_mul_to_float(dfpair y, dfpair z) {
+    return fp_fma(y.hi, z.hi, fp_fma(y.hi, z.lo, fp_mul(y.lo, z.hi)));
+}
+
 // ---------------------------------------------------------------- streaming accesses
 // Loads and stores with the streaming cache operator (ld/st.global.cs: lines allocated
 // evict-first in L1 and L2) for data a kernel touches once: the column solve's inputs,
@@ -293,9 +406,23 @@ __device__ __forceinline__ df ld_once<df>(const df *p) {
     const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
     return df{v.x, v.y};
 }
+template <>
+__device__ __forceinline__ fpair ld_once<fpair>(const fpair *p) {
+    return fpair{__ldcs(reinterpret_cast<const unsigned long long *>(p))};
+}
+// a pair of double-floats is stored as two consecutive df (the scalar layout)
+template <>
+__device__ __forceinline__ dfpair ld_once<dfpair>(const dfpair *p) {
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+    return dfpair{fp_make(v.x, v.z), fp_make(v.y, v.w)};
+}
 template <typename T>
 __device__ __forceinline__ void st_once(T *p, T v) {
     __stcs(p, v);
+}
+template <>
+__device__ __forceinline__ void st_once<fpair>(fpair *p, fpair v) {
+    __stcs(reinterpret_cast<unsigned long long *>(p), v.v);
 }
 
 // Drops the 128-byte L2 line at p (128-byte aligned, global memory) without writing

@@ -33,6 +33,13 @@ struct VadvGeom {
     int ka_pow2;  // n < 0 when ka = -2^n exactly (a_k is then an exponent shift), else 0
 };
 
+// Two columns per thread: fpair storage (two binary32 columns) with dfpair arithmetic.
+template <typename T>
+__host__ __device__ constexpr bool is_pair() { return std::is_same<T, fpair>::value; }
+// double-float arithmetic, one column or two per thread
+template <typename N>
+__host__ __device__ constexpr bool is_df() { return std::is_same<N, df>::value || std::is_same<N, dfpair>::value; }
+
 template <typename N> __device__ __forceinline__ N num_const(double c);
 template <> __device__ __forceinline__ double num_const<double>(double c) { return c; }
 template <> __device__ __forceinline__ float num_const<float>(double c) { return (float)c; }
@@ -40,43 +47,69 @@ template <> __device__ __forceinline__ df num_const<df>(double c) {
     const float hi = __double2float_rn(c);
     return df{hi, __double2float_rn(c - (double)hi)};
 }
+template <> __device__ __forceinline__ dfpair num_const<dfpair>(double c) {
+    const df d = num_const<df>(c);
+    return dfpair{fp_splat(d.hi), fp_splat(d.lo)};
+}
 
 template <typename N, typename T> __device__ __forceinline__ N to_num(T x);
 template <> __device__ __forceinline__ double to_num<double, double>(double x) { return x; }
 template <> __device__ __forceinline__ float to_num<float, float>(float x) { return x; }
 template <> __device__ __forceinline__ double to_num<double, float>(float x) { return (double)x; }
 template <> __device__ __forceinline__ df to_num<df, float>(float x) { return df_from(x); }
+template <> __device__ __forceinline__ dfpair to_num<dfpair, fpair>(fpair x) { return dfpair{x, fp_zero()}; }
 
 template <typename T, typename N> __device__ __forceinline__ T to_store(N x);
 template <> __device__ __forceinline__ double to_store<double, double>(double x) { return x; }
 template <> __device__ __forceinline__ float to_store<float, float>(float x) { return x; }
 template <> __device__ __forceinline__ float to_store<float, double>(double x) { return __double2float_rn(x); }
 template <> __device__ __forceinline__ float to_store<float, df>(df x) { return df_to_float(x); }
+template <> __device__ __forceinline__ fpair to_store<fpair, dfpair>(dfpair x) { return fp_add(x.hi, x.lo); }
 
 // Mixed operations with a storage value b (binary32 storage and double-float
 // arithmetic use the cheaper double-word x word forms; other pairs convert).
 template <typename N, typename T> __device__ __forceinline__ N mulx(N a, T b) { return a * to_num<N, T>(b); }
 template <> __device__ __forceinline__ df mulx<df, float>(df a, float b) { return a * b; }
+template <> __device__ __forceinline__ dfpair mulx<dfpair, fpair>(dfpair a, fpair b) { return a * b; }
 template <typename N, typename T> __device__ __forceinline__ N addx(N a, T b) { return a + to_num<N, T>(b); }
 template <> __device__ __forceinline__ df addx<df, float>(df a, float b) { return a + b; }
+template <> __device__ __forceinline__ dfpair addx<dfpair, fpair>(dfpair a, fpair b) { return a + b; }
 // a + b of two storage values (exact for double-float)
 template <typename N, typename T> __device__ __forceinline__ N add2(T a, T b) { return to_num<N, T>(a) + to_num<N, T>(b); }
 template <> __device__ __forceinline__ df add2<df, float>(float a, float b) { return df_add2(a, b); }
+template <> __device__ __forceinline__ dfpair add2<dfpair, fpair>(fpair a, fpair b) { return df_add2(a, b); }
 // x - y z and x + y z: as written for binary64 and binary32 (contracted to one FMA),
 // the fused double-word forms for double-float
 template <typename N> __device__ __forceinline__ N fms(N x, N y, N z) { return x - y * z; }
 template <> __device__ __forceinline__ df fms<df>(df x, df y, df z) { return df_fms(x, y, z); }
+template <> __device__ __forceinline__ dfpair fms<dfpair>(dfpair x, dfpair y, dfpair z) { return df_fms(x, y, z); }
 template <typename N> __device__ __forceinline__ N fma_n(N x, N y, N z) { return x + y * z; }
 template <> __device__ __forceinline__ df fma_n<df>(df x, df y, df z) { return df_fma(x, y, z); }
+template <> __device__ __forceinline__ dfpair fma_n<dfpair>(dfpair x, dfpair y, dfpair z) { return df_fma(x, y, z); }
 // dtr v rounded to the storage type
 template <typename T, typename N> __device__ __forceinline__ T scaled_store(N dtr, N v) { return to_store<T, N>(dtr * v); }
 template <> __device__ __forceinline__ float scaled_store<float, df>(df dtr, df v) { return df_mul_to_float(dtr, v); }
+template <> __device__ __forceinline__ fpair scaled_store<fpair, dfpair>(dfpair dtr, dfpair v) {
+    return df_mul_to_float(dtr, v);
+}
+__device__ __forceinline__ fpair operator-(fpair a) { return fp_neg(a); }
+
+// One slot of column state: the pair form keeps the scalar layout (two consecutive df).
+template <typename N>
+__device__ __forceinline__ void put_state(N *p, N v) {
+    *p = v;
+}
+template <>
+__device__ __forceinline__ void put_state<dfpair>(dfpair *p, dfpair v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(fp_x(v.hi), fp_x(v.lo), fp_y(v.hi), fp_y(v.lo));
+}
 
 // Inputs of one level k for this lane's column (loaded one level ahead of their use).
 template <typename T>
 struct Level {
     T ut, uts, us1, up1, w;  // utens_k, utens_stage_k, u_stage_{k+1}, u_pos_{k+1}, wcon_{k+1}(i)
-    T w1;                    // wcon_{k+1}(i+1) (last lane only; others take it by shuffle)
+    T w1;                    // wcon_{k+1}(i+1) (last lane only; others take it by shuffle);
+                             // pairs: wcon_{k+1}(2i+2) in the low half, every lane
 };
 
 template <typename T>
@@ -93,7 +126,13 @@ __device__ __forceinline__ void load_level(Level<T> &L, int k, int K, const T *p
         L.us1 = ld_once(pus + (int64_t)(k + 1) * sk_us);
         L.up1 = ld_once(pup + (int64_t)(k + 1) * sk_up);
         L.w = ld_once(pw + (int64_t)(k + 1) * sk_w);
-        if (last_lane) L.w1 = ld_once(pw1 + (int64_t)(k + 1) * sk_w);
+        if constexpr (is_pair<T>()) {
+            // the one binary32 face value past the pair (pw1: its address; sk_w in pairs)
+            const float *f = reinterpret_cast<const float *>(pw1) + (int64_t)(k + 1) * sk_w * 2;
+            L.w1 = fpair{(unsigned long long)__float_as_uint(*f)};
+        } else {
+            if (last_lane) L.w1 = ld_once(pw1 + (int64_t)(k + 1) * sk_w);
+        }
     }
 }
 
@@ -119,6 +158,10 @@ __device__ __forceinline__ double coef<double>(double s, double k, int n) {
 template <>
 __device__ __forceinline__ df coef<df>(df s, df k, int n) {
     return n ? df{__fmul_rn(s.hi, k.hi), __fmul_rn(s.lo, k.hi)} : k * s;
+}
+template <>
+__device__ __forceinline__ dfpair coef<dfpair>(dfpair s, dfpair k, int n) {
+    return n ? dfpair{fp_mul(s.hi, k.hi), fp_mul(s.lo, k.hi)} : k * s;
 }
 
 template <typename T, typename N>
@@ -185,7 +228,8 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     const int ic = min(i, g.I - 1), jc = min(j, g.J - 1);
     // wcon is read up to i = I (I-staggered faces), or up to I-1 with the literal face velocity
     const int ilim = g.literal ? g.I - 1 : g.I;
-    const int iw = min(i, ilim);
+    // pairs (g.I counts them): the pair's own faces 2i, 2i+1 and, apart, face 2i+2 (<= 2 g.I)
+    const int iw = is_pair<T>() ? ic : min(i, ilim);
     const int K = g.K;
     const size_t cidx = ws_domain ? (size_t)jc * g.I + ic : cidx_ws;
     const bool wr = ws_domain ? active : true;
@@ -195,7 +239,10 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     const T *put = ut.p + ic + (int64_t)jc * ut.sj;
     const T *puts = uts.p + ic + (int64_t)jc * uts.sj;  // may alias po (in place)
     const T *pw = wc.p + iw + (int64_t)jc * wc.sj;
-    const T *pw1 = wc.p + min(i + 1, ilim) + (int64_t)jc * wc.sj;
+    const T *pw1 = is_pair<T>()
+                       ? reinterpret_cast<const T *>(reinterpret_cast<const float *>(wc.p + (int64_t)jc * wc.sj) +
+                                                     min(2 * ic + 2, 2 * g.I - (g.literal ? 1 : 0)))
+                       : wc.p + min(i + 1, ilim) + (int64_t)jc * wc.sj;
     T *po = out.p + ic + (int64_t)jc * out.sj;
     const bool last_lane = (tx == 31);
     const bool lit = g.literal != 0;
@@ -231,7 +278,7 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     // double-float: two levels per iteration let the compiler interleave one level's
     // FP32-pipe assembly with the previous level's recurrence (same results); binary64
     // gains nothing from it (its pipe is saturated)
-#pragma unroll(std::is_same<N, df>::value ? 2 : 1)
+#pragma unroll(is_df<N>() ? 2 : 1)
     for (int k = 0; k < K; ++k) {
         GTB_LOAD(L1, k + 1);
         const bool has_next = (k + 1 < K);
@@ -240,6 +287,9 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
             N sf;
             if (lit) {
                 sf = to_num<N, T>(L0.w);
+            } else if constexpr (is_pair<T>()) {
+                // faces (2i, 2i+1) and (2i+1, 2i+2): the pair against itself shifted by one
+                sf = add2<N, T>(L0.w, fpair{(L0.w.v >> 32) | (L0.w1.v << 32)});
             } else {
                 T hi = __shfl_down_sync(0xffffffffu, L0.w, 1);
                 if (last_lane) hi = L0.w1;
@@ -256,7 +306,7 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
         const N b = (dtr - a_cur) + a_next;  // dtr - a_k - c_k with c_k = -a_{k+1}
         // d = dtr s + utens + utens_stage: double-float adds the two inputs exactly first
         N d;
-        if constexpr (std::is_same<N, df>::value) d = df_fma(add2<N, T>(L0.ut, L0.uts), dtr, s_cur);
+        if constexpr (is_df<N>()) d = df_fma(add2<N, T>(L0.ut, L0.uts), dtr, s_cur);
         else d = addx<N, T>(addx<N, T>(dtr * s_cur, L0.ut), L0.uts);
         if (!SYM) {  // + g_k (us_k - us_{k-1}) + g_{k+1} (us_{k+1} - us_k)
             if (k > 0) d = d + g_cur * dpl_prev;
@@ -269,19 +319,19 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
         }
         const N r = recip(p);
         const N cpk = (-a_next) * r, dpk = num * r;
-        if (wr) cpb[(size_t)k * cstride + cidx] = cpk;
-        if (rsave && wr) rsave[(size_t)k * cstride + cidx] = r;
+        if (wr) put_state(cpb + (size_t)k * cstride + cidx, cpk);
+        if (rsave && wr) put_state(rsave + (size_t)k * cstride + cidx, r);
         N ek;  // the backward sweep's term of level k: d'_k (YF) or e_k
         if constexpr (YF) {
             ek = dpk;
             if (active) po[(int64_t)k * out.sk] = to_store<T, N>(dpk);
-            if (wr) dpb[(size_t)k * cstride + cidx] = s_cur;
+            if (wr) put_state(dpb + (size_t)k * cstride + cidx, s_cur);
         } else {
             ek = fms(dpk - s_cur, cpk, s_next);  // s_K = 0 (c'_{K-1} = 0)
             if (DPG) {
                 if (active) po[(int64_t)k * out.sk] = to_store<T, N>(ek);
             } else if (wr) {
-                dpb[(size_t)k * cstride + cidx] = ek;
+                put_state(dpb + (size_t)k * cstride + cidx, ek);
             }
         }
         cp_prev = cpk, dp_prev = dpk, e_last = ek;
@@ -377,15 +427,19 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
 // Single domain: one CTA per 32 x BJ block of columns; WS selects a
 // domain-indexed global workspace over shared memory: c' in ws, the second state
 // array in ws2, and (rsave, or null) 1/p_k kept for the adjoint.
+// Column pairs: registers capped for 28 resident warps per SM (72 a thread, a few
+// spilled); their chains of dependent paired operations need the warps more than the
+// registers (512x512x80 double-float: 213 us uncapped at 114 registers, 192 us capped).
 template <typename T, typename N, int BJ, bool DPG, bool WS>
-__global__ void __launch_bounds__(32 * BJ)
+__global__ void __launch_bounds__(32 * BJ, is_pair<T>() ? 28 / BJ : 1)
     vadv_kernel(const View<const T> us, const View<const T> wc, const View<const T> up, const View<const T> ut,
                 const View<const T> uts, const View<T> out, const VadvGeom g, N *__restrict__ ws,
                 N *__restrict__ ws2, N *__restrict__ rsave) {
     constexpr int NT = 32 * BJ;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int t = threadIdx.y * 32 + threadIdx.x;
-    if (WS) {
+    static_assert(WS || !is_pair<T>(), "column pairs keep their state in a workspace");
+    if constexpr (WS) {
         const size_t cstride = (size_t)g.I * g.J;
         vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>(), true>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
                                                         ws2, cstride, 0, true, threadIdx.x, threadIdx.y, rsave);

@@ -127,6 +127,38 @@ def test_fp32_ragged(G, orc, prec):
     assert rel_err(got, ref) <= (F32_TOL if prec != "native" else 1e-4)
 
 
+@pytest.mark.parametrize("literal,beta_v", [(False, 0.0), (True, 0.0), (False, 0.3)])
+def test_df_column_pairs_equal_single_columns(G, literal, beta_v):
+    """Double-float columns two per thread (binary32 storages whose column pairs are
+    8-byte aligned, I even) give, bit for bit, what one column per thread gives: the same
+    values in storages shifted by one element, whose pairs are not aligned."""
+    import torch
+    I, J, K = 130, 34, 45
+    f = {k: v.astype(np.float32) for k, v in draw(I, J, K, seed=12, wamp=0.4).items()}
+    o, dom = (1, 1, 0), (I, J, K)
+
+    def storages(shift):
+        st = {}
+        for n in NAMES + ("out",):
+            a = np.zeros_like(f["utens_stage"]) if n == "out" else f[n]
+            nk, nj, ni = a.shape
+            t = G.empty_storage(ni + 1, nj, nk, dtype=torch.float32, halo_i=o[0])
+            v = t[:, :, 1:] if shift else t[:, :, :ni]
+            v.copy_(torch.from_numpy(np.ascontiguousarray(a)))
+            st[n] = G.Storage(v, o)
+        return st
+
+    outs = []
+    for shift in (False, True):
+        st = storages(shift)
+        # domain column 0 8-byte aligned (pairs) only in the unshifted storages
+        assert ((st["u_stage"].data.data_ptr() + 4 * o[0]) % 8 == 0) != shift
+        G.vadv(*[st[n] for n in NAMES], st["out"], prec="df", literal=literal, beta_v=beta_v, domain=dom)
+        G.device_status()
+        outs.append(region(st["out"].numpy(), o, dom))
+    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
+
+
 def test_zero_pivot_column(G, orc):
     """b_0 = 0 exactly (dtr = 1/4, wcon = 1 on both faces of level 1): the unpivoted
     solve breaks down in that column on both sides; every other column is exact."""
