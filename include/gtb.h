@@ -31,6 +31,13 @@
  * and data type (Sec. 3.1), done in C at a cost of well under a microsecond.
  * Kernels never trap: a device-side wait that runs out of its time limit
  * records GTB_ERR_DEVICE, which gtb_device_status() reports.
+ *
+ * Checked build: libgtb_checked.so exports the same entry points with the same
+ * results; before its first access each kernel tests the ends of every run of
+ * addresses it will touch against the storage its gtb_field declares (shape and
+ * strides from ptr), and a run outside it is not accessed and records
+ * GTB_ERR_DEVICE as well (the library's own index arithmetic under test, in
+ * place of a memory sanitizer).  Slower; for debugging and tests.
  */
 #ifndef GTB_H
 #define GTB_H
@@ -340,7 +347,9 @@ int gtb_vadv_noalloc(const gtb_field *u_stage, const gtb_field *wcon, const gtb_
 /*
  * gtb_device_status -- synchronises `stream`, then returns and clears the
  * device error word: GTB_OK, or GTB_ERR_DEVICE if a kernel's bounded wait
- * expired since the last call (the affected outputs are then unspecified).
+ * expired since the last call, or (checked build) a kernel found a run of
+ * addresses outside a field's storage; gtb_last_error() says which.  The
+ * affected outputs are then unspecified.
  */
 int gtb_device_status(void *stream);
 

@@ -126,6 +126,17 @@ __global__ void __launch_bounds__(32 * BJ)
     const T *py = yb.p + ic + (int64_t)jc * yb.sj;
     const bool last_lane = (tx == 31);
     const bool lit = g.literal != 0;
+    if constexpr (kChecked) {  // every level of the column inside every field's storage
+        const int64_t kl = K - 1;
+        auto col = [&](const View<T> &v) {
+            if (!v.p) return true;
+            const T *q = v.p + ic + (int64_t)jc * v.sj;
+            return in_storage(v, q, q + kl * v.sk);
+        };
+        bool ok = in_storage(yb, py, py + kl * yb.sk) && col(usb) && col(upb) && col(utb) && col(utsb);
+        if (!FACT) ok = ok && in_storage(wc, pw, pw + kl * wc.sk) && in_storage(wc, pw1, pw1 + kl * wc.sk);
+        if (!__all_sync(0xffffffffu, ok)) return;
+    }
 
     const N dtr = num_const<N>(g.dtr);
     const N ka = num_const<N>(g.ka);
@@ -395,11 +406,15 @@ __device__ __forceinline__ void hdiff_adj_tile(const P &pol, typename P::V *S_x,
         if (da < -2 || da >= I + 2 || db < -2 || db >= J + 2) return;
         const V tr = pol.lap(LB(a, b), LB(a + 1, b), LB(a - 1, b), LB(a, b + 1), LB(a, b - 1));
         const bool dom = da >= 0 && da < I && db >= 0 && db < J;
-        const T o = dom ? ob.p[da + (int64_t)db * ob.sj + (int64_t)k * ob.sk] : T(0);
-        ib.p[da + (int64_t)db * ib.sj + (int64_t)k * ib.sk] = o - pol.out_q(tr);
+        const T *po = ob.p + da + (int64_t)db * ob.sj + (int64_t)k * ob.sk;
+        T *pi = ib.p + da + (int64_t)db * ib.sj + (int64_t)k * ib.sk;
+        if (kChecked && !(in_storage(ib, pi, pi) && (!dom || in_storage(ob, po, po)))) return;
+        const T o = dom ? *po : T(0);
+        *pi = o - pol.out_q(tr);
         if (cb.p && dom) {
             const T D = pol.out_in((FX(a, b) - FX(a - 1, b)) + (FY(a, b) - FY(a, b - 1)));
             T *c = cb.p + da + (int64_t)db * cb.sj + (int64_t)k * cb.sk;
+            if (kChecked && !in_storage(cb, c, c)) return;
             *c = g.accumulate_coeff_bar ? *c - D * o : -D * o;
         }
     });
@@ -466,8 +481,10 @@ __global__ void __launch_bounds__(NT)
             const int idx = tid + c * NT;
             if (idx >= H::IX * H::IY) break;
             const int a = ti0 - 3 + ca, b = tj0 - 3 + cb_;
-            const bool rd = hdiff_reads(a, b, I, J);
-            cp_async_elem(S_in + idx, rd ? in.p + a + (int64_t)b * in.sj + (int64_t)k * in.sk : in.p, rd);
+            bool rd = hdiff_reads(a, b, I, J);
+            const T *src = rd ? in.p + a + (int64_t)b * in.sj + (int64_t)k * in.sk : in.p;
+            if (kChecked && rd) rd = in_storage(in, src, src);
+            cp_async_elem(S_in + idx, rd ? src : in.p, rd);
             ca += NT % H::IX, cb_ += NT / H::IX;
             if (ca >= H::IX) ca -= H::IX, ++cb_;
         }
@@ -479,9 +496,12 @@ __global__ void __launch_bounds__(NT)
             const int idx = tid + c * NT;
             if (idx >= H::QX * H::QY) break;
             const int a = ti0 - 2 + ca, b = tj0 - 2 + cb_;
-            const bool dom = a >= 0 && a < I && b >= 0 && b < J;
-            cp_async_elem(S_q + idx, dom ? coeff.p + a + (int64_t)b * coeff.sj + (int64_t)k * coeff.sk : coeff.p, dom);
-            cp_async_elem(S_ob + idx, dom ? ob.p + a + (int64_t)b * ob.sj + (int64_t)k * ob.sk : ob.p, dom);
+            bool dom = a >= 0 && a < I && b >= 0 && b < J;
+            const T *sc = dom ? coeff.p + a + (int64_t)b * coeff.sj + (int64_t)k * coeff.sk : coeff.p;
+            const T *so = dom ? ob.p + a + (int64_t)b * ob.sj + (int64_t)k * ob.sk : ob.p;
+            if (kChecked && dom) dom = in_storage(coeff, sc, sc) && in_storage(ob, so, so);
+            cp_async_elem(S_q + idx, dom ? sc : coeff.p, dom);
+            cp_async_elem(S_ob + idx, dom ? so : ob.p, dom);
             ca += NT % H::QX, cb_ += NT / H::QX;
             if (ca >= H::QX) ca -= H::QX, ++cb_;
         }
@@ -575,7 +595,10 @@ __global__ void halo_periodic_kernel(const View<T> f, int I, int J, int K, int h
         const int a = (int)(idx % W) - hi, b = (int)((idx / W) % H) - hj, k = (int)(idx / ((int64_t)W * H));
         if (a >= 0 && a < I && b >= 0 && b < J) continue;
         const int sa = (a + I) % I, sb = (b + J) % J;
-        f.p[a + (int64_t)b * f.sj + (int64_t)k * f.sk] = f.p[sa + (int64_t)sb * f.sj + (int64_t)k * f.sk];
+        T *dst = f.p + a + (int64_t)b * f.sj + (int64_t)k * f.sk;
+        const T *src = f.p + sa + (int64_t)sb * f.sj + (int64_t)k * f.sk;
+        if (kChecked && !(in_storage(f, dst, dst) && in_storage(f, src, src))) continue;
+        *dst = *src;
     }
 }
 
@@ -615,10 +638,13 @@ __global__ void halo_periodic_adj_kernel(const View<T> f, int I, int J, int K, i
             for (int sb = -1; sb <= 1; ++sb) {
                 if (sa == 0 && sb == 0) continue;
                 const int x = a + sa * I, y = b + sb * J;
-                if (x >= -hi && x < I + hi && y >= -hj && y < J + hj && !(x >= 0 && x < I && y >= 0 && y < J))
-                    acc += f.p[x + (int64_t)y * f.sj + (int64_t)k * f.sk];
+                if (x >= -hi && x < I + hi && y >= -hj && y < J + hj && !(x >= 0 && x < I && y >= 0 && y < J)) {
+                    const T *src = f.p + x + (int64_t)y * f.sj + (int64_t)k * f.sk;
+                    if (!kChecked || in_storage(f, src, src)) acc += *src;
+                }
             }
-        f.p[a + (int64_t)b * f.sj + (int64_t)k * f.sk] += acc;
+        T *dst = f.p + a + (int64_t)b * f.sj + (int64_t)k * f.sk;
+        if (!kChecked || in_storage(f, dst, dst)) *dst += acc;
     }
 }
 

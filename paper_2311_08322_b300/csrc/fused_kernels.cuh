@@ -155,7 +155,10 @@ struct GlobalEmit {
     __device__ __forceinline__ bool acquire(int) const { return true; }
     __device__ __forceinline__ void put(int m, int p, T v) const {
         const int i = ti0 + p % ti, j = tj0 + p / ti;
-        if (i < I && j < J) out.p[i + (int64_t)j * out.sj + (int64_t)m * out.sk] = v;
+        if (i < I && j < J) {
+            T *q = out.p + i + (int64_t)j * out.sj + (int64_t)m * out.sk;
+            if (!kChecked || in_storage(out, q, q)) *q = v;
+        }
     }
     __device__ __forceinline__ void publish(int) const {}
 };
@@ -206,7 +209,9 @@ __device__ __forceinline__ void hdiff_producer(const CUtensorMap *tmap, const Vi
     for (int q = 0; q < PPT; ++q) {
         const int p = min(pt + q * NPT, NC - 1);
         pcf[q] = coeff.p + min(ti0 + p % TI, I - 1) + (int64_t)min(tj0 + p / TI, J - 1) * coeff.sj;
-        cf_n[q] = pcf[q][0];
+        // checked build: a point whose coeff column leaves the storage reads coeff = 0 instead
+        if (kChecked && !in_storage(coeff, pcf[q], pcf[q] + (int64_t)(K - 1) * coeff.sk)) pcf[q] = nullptr;
+        cf_n[q] = (!kChecked || pcf[q]) ? pcf[q][0] : T(0);
     }
     bool failed = false;
     for (int m = 0; m < K; ++m) {
@@ -214,7 +219,7 @@ __device__ __forceinline__ void hdiff_producer(const CUtensorMap *tmap, const Vi
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
             cf[q] = cf_n[q];
-            if (m + 1 < K) cf_n[q] = pcf[q][(int64_t)(m + 1) * coeff.sk];
+            if (m + 1 < K && (!kChecked || pcf[q])) cf_n[q] = pcf[q][(int64_t)(m + 1) * coeff.sk];
         }
         const int s = USE_TMA ? m % STAGES : 0;
         const T *S = reinterpret_cast<const T *>(base + s * Tile::stage_stride);
@@ -226,8 +231,10 @@ __device__ __forceinline__ void hdiff_producer(const CUtensorMap *tmap, const Vi
                 const int bx = idx % Tile::BX, by = idx / Tile::BX;
                 const int gi = ti0 - 2 + bx, gj = tj0 - 2 + by;
                 T v = T(0);
-                if (gi >= -2 && gi < I + 2 && gj >= -2 && gj < J + 2)
-                    v = in.p[(int64_t)gi + (int64_t)gj * in.sj + (int64_t)m * in.sk];
+                if (gi >= -2 && gi < I + 2 && gj >= -2 && gj < J + 2) {
+                    const T *q = in.p + (int64_t)gi + (int64_t)gj * in.sj + (int64_t)m * in.sk;
+                    if (!kChecked || in_storage(in, q, q)) v = *q;
+                }
                 D[idx] = v;
             }
             producer_sync<PW>();
@@ -319,6 +326,14 @@ __device__ __forceinline__ void fused_consumer(const View<const T> &wc, const Vi
     const T *pw1 = wc.p + min(i + 1, ilim) + (int64_t)jc * wc.sj;
     T *po = out.p + ic + (int64_t)jc * out.sj;
     const size_t cstride = (size_t)I * J, cidx = (size_t)jc * I + ic;
+    if constexpr (kChecked) {  // every level of the column inside every field's storage
+        const int64_t kl = K - 1;
+        const bool ok = in_storage(ut, put, put + kl * ut.sk) && in_storage(uts, puts, puts + kl * uts.sk) &&
+                        in_storage(wc, pw, pw + kl * wc.sk) && in_storage(wc, pw1, pw1 + kl * wc.sk) &&
+                        in_storage(out, po, po + kl * out.sk);
+        // the warp leaves; the producers' waits on its ring slots then expire (bounded)
+        if (!__all_sync(0xffffffffu, ok)) return;
+    }
     N *cpb = ws;
     N *epb = ework;  // e_k when it is not parked in the output
     const bool row_end = (ci == TI - 1);  // wcon(i+1) is not held by the next lane

@@ -106,7 +106,17 @@ static bool same_view(const gtb_field *a, const gtb_field *b) {
 template <typename T>
 static View<T> view_of(const gtb_field *f) {
     T *p = static_cast<T *>(f->ptr) + f->origin[0] + f->origin[1] * f->strides[1] + f->origin[2] * f->strides[2];
-    return View<T>{p, f->strides[1], f->strides[2]};
+    View<T> v{p, f->strides[1], f->strides[2]};
+#ifdef GTB_CHECKED
+    // the storage's bytes: its last element is (shape - 1) along every axis
+    int64_t last = -1;
+    if (f->shape[0] > 0 && f->shape[1] > 0 && f->shape[2] > 0)
+        last = (f->shape[0] - 1) + (f->shape[1] - 1) * f->strides[1] + (f->shape[2] - 1) * f->strides[2];
+    const size_t es = dtype_size(f->dtype);
+    v.lo = f->ptr;
+    v.hi = static_cast<const char *>(f->ptr) + (last + 1) * (int64_t)es;
+#endif
+    return v;
 }
 
 static int resolve_domain(const int64_t *domain, int64_t dom[3]) {
@@ -392,7 +402,11 @@ static bool pairs_fit(const gtb_field *f) {
 template <typename C>
 static View<C> pair_view(const gtb_field *f) {
     const View<float> v = view_of<float>(f);
-    return View<C>{reinterpret_cast<C *>(v.p), v.sj / 2, v.sk / 2};
+    View<C> pv{reinterpret_cast<C *>(v.p), v.sj / 2, v.sk / 2};
+#ifdef GTB_CHECKED
+    pv.lo = v.lo, pv.hi = v.hi;
+#endif
+    return pv;
 }
 
 // Double-float columns two per thread (packed binary32 pairs): I even and every field
@@ -892,6 +906,8 @@ extern "C" int gtb_device_status(void *stream) {
     if (flag) {
         const int zero = 0;
         cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
+        if (flag == kDeviceErrBounds)
+            return fail(GTB_ERR_DEVICE, "a kernel's address run fell outside a field's storage (checked build)");
         return fail(GTB_ERR_DEVICE, "a kernel's bounded wait expired");
     }
     return ok();
@@ -917,7 +933,11 @@ extern "C" int gtb_probe_fp64_fma(int blocks, int iters, void *sink, void *strea
 
 extern "C" const char *gtb_last_error(void) { return t_err; }
 
+#ifdef GTB_CHECKED
+extern "C" const char *gtb_version(void) { return "gtb 0.2 sm_103a checked"; }
+#else
 extern "C" const char *gtb_version(void) { return "gtb 0.2 sm_103a"; }
+#endif
 
 // ====================================================================== allocation-free vadv
 // gtb_vadv_noalloc: gtb_vadv with its workspace in a fixed device array of this

@@ -24,7 +24,42 @@ template <typename T>
 struct View {  // p points at compute-domain point (0,0,0); i stride is 1
     T *p;
     int64_t sj, sk;
+#ifdef GTB_CHECKED
+    const void *lo = nullptr, *hi = nullptr;  // checked build: the storage's bytes [lo, hi)
+#endif
 };
+
+// Checked build (compiled with GTB_CHECKED: libgtb_checked.so).  Before its first
+// access a kernel tests the first and the last element of each affine run of
+// addresses it will touch (a column's levels, a strip's rows) against the storage
+// the host declared for that field (shape and strides of its gtb_field); a run
+// outside it sets the device error word to kDeviceErrBounds and the run is not
+// accessed.  This is the build's stand-in for a memory sanitizer: it checks the
+// kernels' own index arithmetic, not the caller's descriptors (the host validates
+// those in every build).  In the default build the test is compiled out.
+constexpr int kDeviceErrBounds = 2;
+#ifdef GTB_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+// Whether elements a and b (the ends of a run) lie in v's storage (always true in the
+// default build, and for views the host built without a storage range).
+template <typename V, typename Q>
+__device__ __forceinline__ bool in_storage(const View<V> &v, const Q *a, const Q *b) {
+#ifdef GTB_CHECKED
+    if (!v.lo) return true;
+    const char *lo = static_cast<const char *>(v.lo), *hi = static_cast<const char *>(v.hi);
+    const char *x = reinterpret_cast<const char *>(a), *y = reinterpret_cast<const char *>(b);
+    if (x >= lo && x + sizeof(Q) <= hi && y >= lo && y + sizeof(Q) <= hi) return true;
+    atomicCAS(&g_device_error, 0, kDeviceErrBounds);
+    return false;
+#else
+    (void)v, (void)a, (void)b;
+    return true;
+#endif
+}
 
 struct HdiffGeom {
     int I, J, K;

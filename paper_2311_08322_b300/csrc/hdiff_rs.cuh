@@ -360,8 +360,10 @@ __device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const CUt
                 const int bx = idx % G::BX, by = idx / G::BX;
                 const int i = ti0 - 2 - xs + bx, j = tj0 - 2 + by;
                 T v = T(0);
-                if (i >= -2 && i < g.I + 2 && j >= -2 && j < g.J + 2)
-                    v = in.p[(int64_t)i + (int64_t)j * in.sj + (int64_t)k * in.sk];
+                if (i >= -2 && i < g.I + 2 && j >= -2 && j < g.J + 2) {
+                    const T *q = in.p + (int64_t)i + (int64_t)j * in.sj + (int64_t)k * in.sk;
+                    if (!kChecked || in_storage(in, q, q)) v = *q;
+                }
                 D[idx] = v;
             }
             __syncthreads();
@@ -375,7 +377,19 @@ __device__ __forceinline__ void hdiff_rs_item(const CUtensorMap *tmap, const CUt
             const int64_t cf_sj = CTMA ? (int64_t)G::TI : coeff.sj;
             const int cf_vec = CTMA ? 1 : vec_ok;
             T *op = out.p + (int64_t)(ti0 + lane * CPL) + (int64_t)tj0 * out.sj + (int64_t)k * out.sk;
-            if constexpr (FIXED) {
+            // checked build: the strip's coeff and out rows inside their storages (else the warp skips it)
+            bool run = true;
+            if constexpr (kChecked) {
+                bool ok = true;
+                if (ncols > 0) {
+                    const int64_t r0 = cj0, r1 = cj0 + nrows - 1;
+                    ok = in_storage(out, op + r0 * out.sj, op + r1 * out.sj + (ncols - 1));
+                    if (!CTMA) ok = ok && in_storage(coeff, cfp + r0 * cf_sj, cfp + r1 * cf_sj + (ncols - 1));
+                }
+                run = __all_sync(0xffffffffu, ok);
+            }
+            if (!run) {
+            } else if constexpr (FIXED) {
                 // largest biased exponent over the values the strip's stored outputs read:
                 // rows cj0-2 .. cj0+nrows+1, columns -2 .. ntile+1 of the tile, restricted to the
                 // cells the definition reads (never the storage padding beyond the halo or the

@@ -246,6 +246,19 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     T *po = out.p + ic + (int64_t)jc * out.sj;
     const bool last_lane = (tx == 31);
     const bool lit = g.literal != 0;
+    if constexpr (kChecked) {  // every level of the column inside every field's storage
+        const int64_t kl = K > 0 ? K - 1 : 0;
+        bool ok = in_storage(us, pus, pus + kl * us.sk) && in_storage(up, pup, pup + kl * up.sk) &&
+                  in_storage(ut, put, put + kl * ut.sk) && in_storage(uts, puts, puts + kl * uts.sk) &&
+                  in_storage(wc, pw, pw + kl * wc.sk) && in_storage(out, po, po + kl * out.sk);
+        if constexpr (is_pair<T>()) {
+            const float *f1 = reinterpret_cast<const float *>(pw1);
+            ok = ok && in_storage(wc, f1, f1 + kl * wc.sk * 2);
+        } else {
+            ok = ok && in_storage(wc, pw1, pw1 + kl * wc.sk);
+        }
+        if (!__all_sync(0xffffffffu, ok)) return;
+    }
 
     const N dtr = num_const<N>(g.dtr);
     const N ka = num_const<N>(g.ka);

@@ -20,7 +20,10 @@ import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libgtb.so")
+# GTB_CHECKED=1 in the environment loads the checked build (libgtb_checked.so): the same
+# kernels, each testing its address runs against the fields' storages first; a run
+# outside them is not accessed and device_status() raises GTB_ERR_DEVICE
+LIB_PATH = os.path.join(_PKG, "libgtb_checked.so" if os.environ.get("GTB_CHECKED") == "1" else "libgtb.so")
 
 GTB_F32, GTB_F64 = 1, 2
 PREC = {"native": 0, "f64": 1, "df": 2}

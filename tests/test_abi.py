@@ -33,6 +33,16 @@ def test_exports_every_declared_symbol(L):
     assert not missing, missing
 
 
+def test_checked_build_exports_every_declared_symbol(L):
+    """The checked build (GTB_CHECKED=1) is a drop-in for the default library."""
+    from paper_2311_08322_b300 import build
+    lib = ctypes.CDLL(build.LIB_CHECKED)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+    lib.gtb_version.restype = ctypes.c_char_p
+    assert lib.gtb_version().decode().endswith(" checked")
+
+
 def test_version(L):
     assert L.version().startswith("gtb ")
 
