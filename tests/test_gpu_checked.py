@@ -116,6 +116,9 @@ def battery(path):
 
 @pytest.mark.gpu
 def test_checked_build_is_clean_and_bit_identical(tmp_path):
+    sys.path.insert(0, ROOT)
+    from paper_2311_08322_b300 import build
+    build.build()  # both libraries, if missing or older than the sources
     env_default = {k: v for k, v in os.environ.items() if k != "GTB_CHECKED"}
     env_checked = dict(env_default, GTB_CHECKED="1")
     for name, env in (("default", env_default), ("checked", env_checked)):
