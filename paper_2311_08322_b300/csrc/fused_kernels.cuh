@@ -297,6 +297,26 @@ __device__ __forceinline__ void hdiff_producer(const CUtensorMap *tmap, const Vi
         for (int s = 0; s < STAGES; ++s) mbar_wait(&tbar[s], 0), mbar_wait(&tbar[s], 1);
 }
 
+// 2 h in the arithmetic type: exact.  Binary64 storage and arithmetic: the exponent
+// field raised by one on the integer pipe (bit for bit the binary64 sum h + h: a
+// subnormal h shifts its significand, 2 h past the largest finite value is infinity,
+// infinities and NaN stay), which takes one of the chain's operations off the FP64
+// pipe that bounds it.
+template <typename N, typename T>
+__device__ __forceinline__ N twice(T h) {
+    return add2<N, T>(h, h);
+}
+template <>
+__device__ __forceinline__ double twice<double, double>(double h) {
+    const long long b = __double_as_longlong(h);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const long long sign = b & (1ll << 63);
+    if (e != 0 && e < 2046) return __longlong_as_double(b + (1ll << 52));
+    if (e == 0) return __longlong_as_double(sign | ((b & 0x7FFFFFFFFFFFFFFFll) << 1));
+    if (e == 2046) return __longlong_as_double(sign | 0x7FF0000000000000ll);
+    return h;
+}
+
 // The consumer warps of hdiff_vadv_kernel: the vadv column solve of the tile's
 // columns, level by level as the producers publish h.  With u_stage = u_pos = h
 // the system of Sec. 3.1 is solved in the shifted unknown y = x + h (the explicit
@@ -412,7 +432,7 @@ __device__ __forceinline__ void fused_consumer(const View<const T> &wc, const Vi
         const T h = H[slot * NC + tid];
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
-        const N h2 = add2<N, T>(h, h);  // s_m = 2 h_m, exact
+        const N h2 = twice<N, T>(h);  // s_m = 2 h_m, exact
         if (m >= 1) vstep(m - 1, true, h_prev, h, h2_prev, h2, ut_k, uts_k, w_m, w1_m);
         h_prev = h, h2_prev = h2;
     }
