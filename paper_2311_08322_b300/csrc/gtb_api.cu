@@ -107,15 +107,14 @@ template <typename T>
 static View<T> view_of(const gtb_field *f) {
     T *p = static_cast<T *>(f->ptr) + f->origin[0] + f->origin[1] * f->strides[1] + f->origin[2] * f->strides[2];
     View<T> v{p, f->strides[1], f->strides[2]};
-#ifdef GTB_CHECKED
-    // the storage's bytes: its last element is (shape - 1) along every axis
+    // the storage's bytes (for the kernels' address checks): its last element is
+    // (shape - 1) along every axis
     int64_t last = -1;
     if (f->shape[0] > 0 && f->shape[1] > 0 && f->shape[2] > 0)
         last = (f->shape[0] - 1) + (f->shape[1] - 1) * f->strides[1] + (f->shape[2] - 1) * f->strides[2];
     const size_t es = dtype_size(f->dtype);
     v.lo = f->ptr;
     v.hi = static_cast<const char *>(f->ptr) + (last + 1) * (int64_t)es;
-#endif
     return v;
 }
 
@@ -403,9 +402,7 @@ template <typename C>
 static View<C> pair_view(const gtb_field *f) {
     const View<float> v = view_of<float>(f);
     View<C> pv{reinterpret_cast<C *>(v.p), v.sj / 2, v.sk / 2};
-#ifdef GTB_CHECKED
     pv.lo = v.lo, pv.hi = v.hi;
-#endif
     return pv;
 }
 
@@ -907,7 +904,7 @@ extern "C" int gtb_device_status(void *stream) {
         const int zero = 0;
         cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
         if (flag == kDeviceErrBounds)
-            return fail(GTB_ERR_DEVICE, "a kernel's address run fell outside a field's storage (checked build)");
+            return fail(GTB_ERR_DEVICE, "a kernel's address run fell outside a field's storage");
         return fail(GTB_ERR_DEVICE, "a kernel's bounded wait expired");
     }
     return ok();

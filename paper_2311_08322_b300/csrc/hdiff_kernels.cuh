@@ -24,9 +24,7 @@ template <typename T>
 struct View {  // p points at compute-domain point (0,0,0); i stride is 1
     T *p;
     int64_t sj, sk;
-#ifdef GTB_CHECKED
-    const void *lo = nullptr, *hi = nullptr;  // checked build: the storage's bytes [lo, hi)
-#endif
+    const void *lo = nullptr, *hi = nullptr;  // the storage's bytes [lo, hi) (null: not checked)
 };
 
 // Checked build (compiled with GTB_CHECKED: libgtb_checked.so).  Before its first
@@ -36,7 +34,8 @@ struct View {  // p points at compute-domain point (0,0,0); i stride is 1
 // outside it sets the device error word to kDeviceErrBounds and the run is not
 // accessed.  This is the build's stand-in for a memory sanitizer: it checks the
 // kernels' own index arithmetic, not the caller's descriptors (the host validates
-// those in every build).  In the default build the test is compiled out.
+// those in every build).  In the default build the tests are compiled out, except
+// in the batched column solve (vadv_batch_kernel), where they stay (see there).
 constexpr int kDeviceErrBounds = 2;
 #ifdef GTB_CHECKED
 constexpr bool kChecked = true;
@@ -48,17 +47,12 @@ constexpr bool kChecked = false;
 // default build, and for views the host built without a storage range).
 template <typename V, typename Q>
 __device__ __forceinline__ bool in_storage(const View<V> &v, const Q *a, const Q *b) {
-#ifdef GTB_CHECKED
     if (!v.lo) return true;
     const char *lo = static_cast<const char *>(v.lo), *hi = static_cast<const char *>(v.hi);
     const char *x = reinterpret_cast<const char *>(a), *y = reinterpret_cast<const char *>(b);
     if (x >= lo && x + sizeof(Q) <= hi && y >= lo && y + sizeof(Q) <= hi) return true;
     atomicCAS(&g_device_error, 0, kDeviceErrBounds);
     return false;
-#else
-    (void)v, (void)a, (void)b;
-    return true;
-#endif
 }
 
 struct HdiffGeom {

@@ -217,7 +217,7 @@ __host__ __device__ constexpr size_t vadv_smem_per_col_level() {
 // in shared memory.  rsave (global state only, or null): the forward sweep also stores
 // 1/p_k there, [k][column] like c'; c' and 1/p_k are then the factors the adjoint reads
 // (gtb_vadv_adj with GTB_ADJ_FACTORS), and c' is not dropped from L2.
-template <typename T, typename N, int BJ, bool DPG, bool YF, bool SYM, bool GST>
+template <typename T, typename N, int BJ, bool DPG, bool YF, bool SYM, bool GST, bool CHK>
 __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                                const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                                const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
@@ -246,7 +246,7 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     T *po = out.p + ic + (int64_t)jc * out.sj;
     const bool last_lane = (tx == 31);
     const bool lit = g.literal != 0;
-    if constexpr (kChecked) {  // every level of the column inside every field's storage
+    if constexpr (CHK) {  // every level of the column inside every field's storage
         const int64_t kl = K > 0 ? K - 1 : 0;
         bool ok = in_storage(us, pus, pus + kl * us.sk) && in_storage(up, pup, pup + kl * up.sk) &&
                   in_storage(ut, put, put + kl * ut.sk) && in_storage(uts, puts, puts + kl * uts.sk) &&
@@ -424,16 +424,18 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     }
 }
 
-template <typename T, typename N, int BJ, bool DPG, bool YF, bool GST>
+// CHK: test the column's address runs before the first access (the checked build, and
+// the batched solve in every build)
+template <typename T, typename N, int BJ, bool DPG, bool YF, bool GST, bool CHK = kChecked>
 __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                              const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                              const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
                                              size_t cidx_ws, bool ws_domain, int tx, int ty, N *rsave = nullptr) {
     if (g.sym)
-        vadv_columns_t<T, N, BJ, DPG, YF, true, GST>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
+        vadv_columns_t<T, N, BJ, DPG, YF, true, GST, CHK>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
                                                 ws_domain, tx, ty, rsave);
     else
-        vadv_columns_t<T, N, BJ, DPG, YF, false, GST>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
+        vadv_columns_t<T, N, BJ, DPG, YF, false, GST, CHK>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
                                                  ws_domain, tx, ty, rsave);
 }
 
