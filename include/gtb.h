@@ -347,9 +347,10 @@ int gtb_vadv_noalloc(const gtb_field *u_stage, const gtb_field *wcon, const gtb_
 /*
  * gtb_device_status -- synchronises `stream`, then returns and clears the
  * device error word: GTB_OK, or GTB_ERR_DEVICE if a kernel's bounded wait
- * expired since the last call, or (checked build) a kernel found a run of
- * addresses outside a field's storage; gtb_last_error() says which.  The
- * affected outputs are then unspecified.
+ * expired since the last call, or a kernel found a run of addresses outside a
+ * field's storage (every kernel of the checked build tests its runs; in the
+ * default build the batched column solve does); gtb_last_error() says which.
+ * The affected outputs are then unspecified.
  */
 int gtb_device_status(void *stream);
 
