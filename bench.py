@@ -896,10 +896,12 @@ def precision_compare(hbm, reps=20):
         sets = make(dt)
         es = 8 if dt == np.float64 else 4
         r = {"hdiff_ms": timed(lambda q: gtb.hdiff(sets[q % 2]["in"], sets[q % 2]["coeff"], sets[q % 2]["hout"]))}
-        precs = ("native",) if dt == np.float64 else ("native", "f64", "df")
+        # df48: double-float with the column state in 48 bits (GTB_STATE48)
+        precs = ("native",) if dt == np.float64 else ("native", "f64", "df", "df48")
+        kw = lambda pr: {"prec": pr[:2] if pr == "df48" else pr, "state48": pr == "df48"}
         for pr in precs:
             r[f"vadv_{pr}_ms"] = timed(lambda q: gtb.vadv(*[sets[q % 2][n] for n in VADV_NAMES], sets[q % 2]["vout"],
-                                                          prec=pr))
+                                                          **kw(pr)))
         r["hdiff_gbs"] = round(hdiff_bytes(I3, J3, K3, es) / (r["hdiff_ms"] / 1e3) / 1e9, 1)
         for pr in precs:
             r[f"vadv_{pr}_gbs"] = round(vadv_bytes(I3, J3, K3, es) / (r[f"vadv_{pr}_ms"] / 1e3) / 1e9, 1)
@@ -915,15 +917,15 @@ def precision_compare(hbm, reps=20):
         gtb.hdiff(st["in"], st["coeff"], st["hout"])
         kept = {"hdiff": st["hout"].numpy()[:, 2:-2, 2:-2]}
         for pr in precs:
-            gtb.vadv(*[st[n] for n in VADV_NAMES], st["vout"], prec=pr)
+            gtb.vadv(*[st[n] for n in VADV_NAMES], st["vout"], **kw(pr))
             kept[f"vadv_{pr}"] = st["vout"].numpy()[:, 1:-1, 1:-1]
         gtb.device_status()
         outs[name] = kept
         del sets
         torch.cuda.empty_cache()
     gtb.device_status()
-    res["note"] = ("fp32 step uses the fastest vadv form that meets the 1e-5 bound (f64 or df); all-binary32 vadv "
-                   "does not meet it on ill-conditioned columns")
+    res["note"] = ("fp32 step uses the fastest vadv form that meets the 1e-5 bound (f64, df or df48: df with its "
+                   "column state in 48 bits); all-binary32 vadv does not meet it on ill-conditioned columns")
     return res, outs
 
 

@@ -86,6 +86,7 @@ typedef enum {
 #define GTB_ADJ_ACCUMULATE 2u /* adjoints: add into the cotangent outputs instead of overwriting them */
 #define GTB_SAVE_FACTORS 4u   /* gtb_hdiff_vadv: keep the column factors (c'_k, 1/p_k) in the workspace */
 #define GTB_ADJ_FACTORS 8u    /* gtb_vadv_adj: the workspace holds those factors; use them, do not refactorise */
+#define GTB_STATE48 16u       /* gtb_vadv, GTB_F32 + GTB_PREC_DF: column state in the workspace in 48 bits */
 
 /*
  * gtb_hdiff -- horizontal diffusion (paper Sec. 3.1; one PARALLEL computation,
@@ -124,6 +125,15 @@ int gtb_hdiff(const gtb_field *in, const gtb_field *coeff, const gtb_field *out,
  * prec: gtb_prec.  For GTB_F64 storage only GTB_PREC_NATIVE is accepted
  * (binary64); for GTB_F32 storage NATIVE is all-binary32, F64 and DF keep the
  * whole column computation in binary64 / double-float.
+ * flags: GTB_WCON_LITERAL; GTB_STATE48 (GTB_F32 storage with GTB_PREC_DF only,
+ * else GTB_ERR_ARG): the forward sweep stores c'_k and the back-substitution
+ * term in the workspace as their binary32 high part and the top 16 bits of
+ * their low part (12 bytes per point instead of 16, less DRAM traffic when the
+ * column state outgrows L2); the back substitution then starts from values
+ * within 2^-32 of the computed ones.  The max-norm error stays that of the
+ * full-width form, but a column whose outputs are small beside its intermediate
+ * values loses accuracy (worst column 9e-4 relative at 512x512x80, against
+ * 6e-8).  Without a workspace the flag has no effect (shared-memory state).
  * A zero pivot (singular leading minor) yields non-finite values in that column,
  * as the unpivoted method does.  Limit without a workspace: K <= 448 (the column
  * state then lives in shared memory); larger K is GTB_ERR_UNSUPPORTED unless a

@@ -410,31 +410,36 @@ static View<C> pair_view(const gtb_field *f) {
 // pair-aligned; the workspace and the kept factors keep the one-column layout.
 template <int BJ>
 static int launch_vadv_pairs(const gtb_field *const f[6], const VadvGeom &g, void *ws, cudaStream_t st, void *ws2,
-                             void *rsave) {
+                             void *rsave, bool packed) {
     VadvGeom gp = g;
     gp.I = g.I / 2;
     dfpair *w = static_cast<dfpair *>(ws);
     dfpair *w2 = ws2 ? static_cast<dfpair *>(ws2) : w + (size_t)gp.K * gp.I * gp.J;
     dim3 block(32, BJ), grid((gp.I + 31) / 32, (gp.J + BJ - 1) / BJ);
-    vadv_kernel<fpair, dfpair, BJ, false, true><<<grid, block, 0, st>>>(
-        pair_view<const fpair>(f[0]), pair_view<const fpair>(f[1]), pair_view<const fpair>(f[2]),
-        pair_view<const fpair>(f[3]), pair_view<const fpair>(f[4]), pair_view<fpair>(f[5]), gp, w, w2,
-        static_cast<dfpair *>(rsave));
+    auto kern = packed ? vadv_kernel<fpair, dfpair, BJ, false, true, kStatePacked> : vadv_kernel<fpair, dfpair, BJ, false, true>;
+    kern<<<grid, block, 0, st>>>(pair_view<const fpair>(f[0]), pair_view<const fpair>(f[1]),
+                                 pair_view<const fpair>(f[2]), pair_view<const fpair>(f[3]),
+                                 pair_view<const fpair>(f[4]), pair_view<fpair>(f[5]), gp, w, w2,
+                                 static_cast<dfpair *>(rsave));
     return launch_status("vadv launch");
 }
 
 // Workspace form: c' in ws and the second state array in ws2 (by default right after c'),
 // 1/p_k in rsave when the factors are kept (the chained call's binary32 storage path).
+// packed (double-float, no rsave): the column state in 48 bits (GTB_STATE48).
 template <typename T, typename N, int BJ, bool WS>
 static int launch_vadv_t(const gtb_field *const f[6], const VadvGeom &g, void *ws, cudaStream_t st,
-                         void *ws2 = nullptr, void *rsave = nullptr) {
+                         void *ws2 = nullptr, void *rsave = nullptr, bool packed = false) {
     if constexpr (std::is_same<T, float>::value && std::is_same<N, df>::value && WS) {
         bool fit = g.I % 2 == 0;
         for (int q = 0; q < 6; ++q) fit = fit && pairs_fit(f[q]);
-        if (fit) return launch_vadv_pairs<BJ>(f, g, ws, st, ws2, rsave);
+        if (fit) return launch_vadv_pairs<BJ>(f, g, ws, st, ws2, rsave, packed && !rsave);
     }
     constexpr bool DPG = vadv_dp_global<T, N>();
     auto kern = vadv_kernel<T, N, BJ, DPG, WS>;
+    if constexpr (is_df<N>() && WS) {
+        if (packed && !rsave) kern = vadv_kernel<T, N, BJ, DPG, WS, kStatePacked>;
+    }
     const int smem = WS ? 0 : (int)(vadv_smem_per_col_level<T, N>() * g.K * 32 * BJ);
     if (!WS && prepare_kernel(kern, 227 * 1024) != cudaSuccess)
         return launch_status("vadv: shared-memory attribute");
@@ -456,9 +461,11 @@ static size_t vadv_ws_bytes(const int64_t dom[3]) {
 // per block.  Without: column state in shared memory, two warps per block while
 // it stays within 48 KB (several blocks per SM), else one.
 template <typename T, typename N>
-static int run_vadv_n(const gtb_field *const f[6], const VadvGeom &g, void *ws, size_t ws_bytes, cudaStream_t st) {
+static int run_vadv_n(const gtb_field *const f[6], const VadvGeom &g, void *ws, size_t ws_bytes, cudaStream_t st,
+                      bool packed = false) {
     const int64_t dom[3] = {g.I, g.J, g.K};
-    if (ws && ws_bytes >= vadv_ws_bytes<T, N>(dom)) return launch_vadv_t<T, N, 2, true>(f, g, ws, st);
+    if (ws && ws_bytes >= vadv_ws_bytes<T, N>(dom))
+        return launch_vadv_t<T, N, 2, true>(f, g, ws, st, nullptr, nullptr, packed);
     const size_t per_col = vadv_smem_per_col_level<T, N>() * (size_t)g.K;
     if (per_col * 64 <= 48 * 1024) return launch_vadv_t<T, N, 2, false>(f, g, nullptr, st);
     return launch_vadv_t<T, N, 1, false>(f, g, nullptr, st);
@@ -720,8 +727,10 @@ extern "C" int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const g
     int rc;
     for (int q = 0; q < 6; ++q)
         if ((rc = check_field(names[q], f[q], dt))) return rc;
-    if (flags & ~GTB_WCON_LITERAL) return fail(GTB_ERR_ARG, "gtb_vadv: unknown flags 0x%x", flags);
+    if (flags & ~(GTB_WCON_LITERAL | GTB_STATE48)) return fail(GTB_ERR_ARG, "gtb_vadv: unknown flags 0x%x", flags);
     if (prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return fail(GTB_ERR_ARG, "gtb_vadv: unknown prec %d", prec);
+    if ((flags & GTB_STATE48) && (dt != GTB_F32 || prec != GTB_PREC_DF))
+        return fail(GTB_ERR_ARG, "gtb_vadv: GTB_STATE48 applies to GTB_F32 storage with GTB_PREC_DF");
     if (dt == GTB_F64 && prec != GTB_PREC_NATIVE)
         return fail(GTB_ERR_ARG, "gtb_vadv: FP64 storage computes in binary64 (prec must be GTB_PREC_NATIVE)");
     if (!(dtr_stage == dtr_stage) || !(beta_v == beta_v)) return fail(GTB_ERR_ARG, "gtb_vadv: NaN scalar");
@@ -757,7 +766,8 @@ extern "C" int gtb_vadv(const gtb_field *u_stage, const gtb_field *wcon, const g
     }
     if (dt == GTB_F64) return run_vadv_n<double, double>(f, g, workspace, workspace_bytes, st);
     if (prec == GTB_PREC_F64) return run_vadv_n<float, double>(f, g, workspace, workspace_bytes, st);
-    if (prec == GTB_PREC_DF) return run_vadv_n<float, df>(f, g, workspace, workspace_bytes, st);
+    if (prec == GTB_PREC_DF)
+        return run_vadv_n<float, df>(f, g, workspace, workspace_bytes, st, (flags & GTB_STATE48) != 0);
     return run_vadv_n<float, float>(f, g, workspace, workspace_bytes, st);
 }
 

@@ -104,6 +104,46 @@ __device__ __forceinline__ void put_state<dfpair>(dfpair *p, dfpair v) {
     *reinterpret_cast<float4 *>(p) = make_float4(fp_x(v.hi), fp_x(v.lo), fp_y(v.hi), fp_y(v.lo));
 }
 
+// Double-float column state in 48 bits (GTB_STATE48; global workspace): the binary32
+// high part and the top 16 bits of the low part (its sign, exponent and 7 leading
+// fraction bits), i.e. a value within 2^-8 |lo| <= 2^-32 |v| of the computed one.
+// c'_k and e_k of one level go together: their high parts in one slot of the first
+// array (float2 per column, float4 per column pair), their low parts packed into one
+// word per column of the second (uint32, uint2 per pair).
+__device__ __forceinline__ unsigned lo16_pack(float a, float b) {  // top halves of a (low) and b (high)
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+// bytes of one slot of the low-part array (the first array's slot is sizeof(N))
+template <typename N>
+__host__ __device__ constexpr int sq_lo_bytes() {
+    return sizeof(N) / 2;
+}
+__device__ __forceinline__ void put_state_sq(df *h, df *l, size_t idx, df c, df e) {
+    reinterpret_cast<float2 *>(h)[idx] = make_float2(c.hi, e.hi);
+    reinterpret_cast<unsigned *>(l)[idx] = lo16_pack(c.lo, e.lo);
+}
+__device__ __forceinline__ void put_state_sq(dfpair *h, dfpair *l, size_t idx, dfpair c, dfpair e) {
+    reinterpret_cast<float4 *>(h)[idx] = make_float4(fp_x(c.hi), fp_y(c.hi), fp_x(e.hi), fp_y(e.hi));
+    reinterpret_cast<uint2 *>(l)[idx] =
+        make_uint2(lo16_pack(fp_x(c.lo), fp_y(c.lo)), lo16_pack(fp_x(e.lo), fp_y(e.lo)));
+}
+// the last read of a slot pair (streaming loads)
+__device__ __forceinline__ void get_state_sq(const df *h, const df *l, size_t idx, df &c, df &e) {
+    const float2 v = __ldcs(reinterpret_cast<const float2 *>(h) + idx);
+    const unsigned w = __ldcs(reinterpret_cast<const unsigned *>(l) + idx);
+    c = df{v.x, __uint_as_float(w << 16)};
+    e = df{v.y, __uint_as_float(w & 0xFFFF0000u)};
+}
+__device__ __forceinline__ fpair lo16_unpack(unsigned w) {
+    return fpair{((unsigned long long)(w & 0xFFFF0000u) << 32) | (unsigned long long)(w << 16)};
+}
+__device__ __forceinline__ void get_state_sq(const dfpair *h, const dfpair *l, size_t idx, dfpair &c, dfpair &e) {
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(h) + idx);
+    const uint2 w = __ldcs(reinterpret_cast<const uint2 *>(l) + idx);
+    c = dfpair{fp_make(v.x, v.y), lo16_unpack(w.x)};
+    e = dfpair{fp_make(v.z, v.w), lo16_unpack(w.y)};
+}
+
 // Inputs of one level k for this lane's column (loaded one level ahead of their use).
 template <typename T>
 struct Level {
@@ -216,13 +256,19 @@ __host__ __device__ constexpr size_t vadv_smem_per_col_level() {
 // GST: the column state is in global memory (its last reads are streaming loads); else
 // in shared memory.  rsave (global state only, or null): the forward sweep also stores
 // 1/p_k there, [k][column] like c'; c' and 1/p_k are then the factors the adjoint reads
-// (gtb_vadv_adj with GTB_ADJ_FACTORS), and c' is not dropped from L2.
-template <typename T, typename N, int BJ, bool DPG, bool YF, bool SYM, bool GST, bool CHK>
+// (gtb_vadv_adj with GTB_ADJ_FACTORS), and c' is not dropped from L2.  SF, the width of
+// a double-float solve's global state: kStateFull, or kStatePacked, 48 bits
+// (put_state_sq: 12 bytes per column and level instead of 16, so that less of it
+// overflows L2 while every column of the grid is in flight; no rsave).
+constexpr int kStateFull = 0, kStatePacked = 1;
+template <typename T, typename N, int BJ, bool DPG, bool YF, bool SYM, bool GST, bool CHK, int SF>
 __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                                const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                                const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
                                                size_t cidx_ws, bool ws_domain, int tx, int ty, N *rsave = nullptr) {
     static_assert(!YF || DPG, "the y form parks d'_k in the output");
+    constexpr bool SQ = is_df<N>() && GST && SF == kStatePacked;  // 48-bit double-float state
+    static_assert(!SQ || (!DPG && !YF), "48-bit state holds c' and e_k");
     const int i = bx * 32 + tx, j = by * BJ + ty;
     const bool active = (i < g.I) && (j < g.J);
     const int ic = min(i, g.I - 1), jc = min(j, g.J - 1);
@@ -332,7 +378,7 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
         }
         const N r = recip(p);
         const N cpk = (-a_next) * r, dpk = num * r;
-        if (wr) put_state(cpb + (size_t)k * cstride + cidx, cpk);
+        if (!SQ && wr) put_state(cpb + (size_t)k * cstride + cidx, cpk);
         if (rsave && wr) put_state(rsave + (size_t)k * cstride + cidx, r);
         N ek;  // the backward sweep's term of level k: d'_k (YF) or e_k
         if constexpr (YF) {
@@ -343,6 +389,8 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
             ek = fms(dpk - s_cur, cpk, s_next);  // s_K = 0 (c'_{K-1} = 0)
             if (DPG) {
                 if (active) po[(int64_t)k * out.sk] = to_store<T, N>(ek);
+            } else if constexpr (SQ) {
+                if (wr) put_state_sq(cpb, dpb, (size_t)k * cstride + cidx, cpk, ek);
             } else if (wr) {
                 put_state(dpb + (size_t)k * cstride + cidx, ek);
             }
@@ -380,8 +428,12 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
         for (int q = 0; q < BG; ++q) {
             const int k = k0 - q;
             if (k < 0) break;
-            eq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : ld_state(dpb + (size_t)k * cstride + cidx);
-            cq[q] = ld_state(cpb + (size_t)k * cstride + cidx);
+            if constexpr (SQ) {
+                get_state_sq(cpb, dpb, (size_t)k * cstride + cidx, cq[q], eq[q]);
+            } else {
+                eq[q] = DPG ? to_num<N, T>(po[(int64_t)k * out.sk]) : ld_state(dpb + (size_t)k * cstride + cidx);
+                cq[q] = ld_state(cpb + (size_t)k * cstride + cidx);
+            }
             sq[q] = YF ? ld_state(dpb + (size_t)k * cstride + cidx) : zero;
         }
     };
@@ -390,6 +442,10 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
     // from L2 without a write-back.  Arrays: c', and s (y form) or e_k (not parked).
     constexpr int kArrays = (YF || !DPG) ? 2 : 1;
     constexpr int kLines = (int)(32 * sizeof(N) / 128);  // lines per warp, level and array
+    // lines per warp and level of the first array (c', or the high parts) and the second
+    constexpr int kL0 = kLines, kL1 = SQ ? 32 * sq_lo_bytes<N>() / 128 : (kArrays == 2 ? kLines : 0);
+    constexpr int kPer = kL0 + kL1;
+    constexpr size_t kSlot1 = SQ ? (size_t)sq_lo_bytes<N>() : sizeof(N);
     const bool own = GST && __all_sync(0xffffffffu, ws_domain ? active : true);
     const bool keep_cp = rsave != nullptr;  // c' is a kept factor: not dropped
     const size_t c0 = __shfl_sync(0xffffffffu, cidx, 0);
@@ -410,12 +466,16 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
             if (own) {
                 __syncwarp();
                 const int e = tx;  // (level in group, array, line) handled by this lane
-                if (e < BG * kArrays * kLines) {
-                    const int m = e % kLines, arr = (e / kLines) % kArrays, q = e / (kLines * kArrays);
+                if (e < BG * kPer) {
+                    const int q = e / kPer, r = e % kPer;
+                    const int arr = r < kL0 ? 0 : 1, m = arr ? r - kL0 : r;
                     const int k = k0 - q;
                     if (k >= 0 && !(arr == 0 && keep_cp)) {
-                        const N *row = (arr == 0 ? cpb : dpb) + (size_t)k * cstride + c0;
-                        const unsigned char *line = reinterpret_cast<const unsigned char *>(row) + m * 128;
+                        const size_t slot = (size_t)k * cstride + c0;
+                        const unsigned char *line =
+                            (arr == 0 ? reinterpret_cast<const unsigned char *>(cpb + slot)
+                                      : reinterpret_cast<const unsigned char *>(dpb) + slot * kSlot1) +
+                            m * 128;
                         if ((reinterpret_cast<uintptr_t>(line) & 127) == 0) discard_l2_line(line);
                     }
                 }
@@ -426,16 +486,16 @@ __device__ __forceinline__ void vadv_columns_t(const View<const T> &us, const Vi
 
 // CHK: test the column's address runs before the first access (the checked build, and
 // the batched solve in every build)
-template <typename T, typename N, int BJ, bool DPG, bool YF, bool GST, bool CHK = kChecked>
+template <typename T, typename N, int BJ, bool DPG, bool YF, bool GST, bool CHK = kChecked, int SF = kStateFull>
 __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View<const T> &wc, const View<const T> &up,
                                              const View<const T> &ut, const View<const T> &uts, const View<T> &out,
                                              const VadvGeom &g, int bx, int by, N *cpb, N *dpb, size_t cstride,
                                              size_t cidx_ws, bool ws_domain, int tx, int ty, N *rsave = nullptr) {
     if (g.sym)
-        vadv_columns_t<T, N, BJ, DPG, YF, true, GST, CHK>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
+        vadv_columns_t<T, N, BJ, DPG, YF, true, GST, CHK, SF>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
                                                 ws_domain, tx, ty, rsave);
     else
-        vadv_columns_t<T, N, BJ, DPG, YF, false, GST, CHK>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
+        vadv_columns_t<T, N, BJ, DPG, YF, false, GST, CHK, SF>(us, wc, up, ut, uts, out, g, bx, by, cpb, dpb, cstride, cidx_ws,
                                                  ws_domain, tx, ty, rsave);
 }
 
@@ -445,7 +505,8 @@ __device__ __forceinline__ void vadv_columns(const View<const T> &us, const View
 // Column pairs: registers capped for 28 resident warps per SM (72 a thread, a few
 // spilled); their chains of dependent paired operations need the warps more than the
 // registers (512x512x80 double-float: 213 us uncapped at 114 registers, 192 us capped).
-template <typename T, typename N, int BJ, bool DPG, bool WS>
+// SF: the width of a double-float workspace state (kStatePacked: rsave must be null).
+template <typename T, typename N, int BJ, bool DPG, bool WS, int SF = kStateFull>
 __global__ void __launch_bounds__(32 * BJ, is_pair<T>() ? 28 / BJ : 1)
     vadv_kernel(const View<const T> us, const View<const T> wc, const View<const T> up, const View<const T> ut,
                 const View<const T> uts, const View<T> out, const VadvGeom g, N *__restrict__ ws,
@@ -456,8 +517,9 @@ __global__ void __launch_bounds__(32 * BJ, is_pair<T>() ? 28 / BJ : 1)
     static_assert(WS || !is_pair<T>(), "column pairs keep their state in a workspace");
     if constexpr (WS) {
         const size_t cstride = (size_t)g.I * g.J;
-        vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>(), true>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws,
-                                                        ws2, cstride, 0, true, threadIdx.x, threadIdx.y, rsave);
+        vadv_columns<T, N, BJ, DPG, vadv_yform<T, N>(), true, kChecked, SF>(
+            us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, ws, ws2, cstride, 0, true, threadIdx.x, threadIdx.y,
+            rsave);
     } else {
         N *cpb = reinterpret_cast<N *>(smem_raw);
         vadv_columns<T, N, BJ, DPG, false, false>(us, wc, up, ut, uts, out, g, blockIdx.x, blockIdx.y, cpb,

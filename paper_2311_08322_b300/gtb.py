@@ -63,6 +63,7 @@ EXPORTS = ("gtb_hdiff", "gtb_vadv", "gtb_vadv_workspace_bytes", "gtb_hdiff_adj",
 GTB_ADJ_ACCUMULATE = 2
 GTB_SAVE_FACTORS = 4
 GTB_ADJ_FACTORS = 8
+GTB_STATE48 = 16
 
 
 def lib() -> ctypes.CDLL:
@@ -266,11 +267,12 @@ def _vadv_domain(fs, literal):
 
 
 def vadv(u_stage, wcon, u_pos, utens, utens_stage, out=None, *, dtr_stage=3.0 / 20.0, beta_v=0.0,
-         prec="native", literal=False, domain=None, workspace="auto", stream=None):
+         prec="native", literal=False, domain=None, workspace="auto", state48=False, stream=None):
     """utens_stage_out = vadv(...) (gtb_vadv); ``out=None`` updates utens_stage in place.
 
     ``workspace``: "auto" (a cached buffer from :func:`workspace`, the fast
-    form), a CUDA tensor, or None (column state in shared memory)."""
+    form), a CUDA tensor, or None (column state in shared memory).
+    ``state48``: GTB_STATE48 (FP32 storage, prec "df": the column state in 48 bits)."""
     out = utens_stage if out is None else out
     fs = [_as_field(x) for x in (u_stage, wcon, u_pos, utens, utens_stage, out)]
     ws_ptr, ws_bytes = None, 0
@@ -282,7 +284,8 @@ def vadv(u_stage, wcon, u_pos, utens, utens_stage, out=None, *, dtr_stage=3.0 / 
         if workspace is not None:
             ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     _check(lib().gtb_vadv(*[ctypes.byref(f) for f in fs], float(dtr_stage), float(beta_v),
-                          PREC[prec] if isinstance(prec, str) else int(prec), GTB_WCON_LITERAL if literal else 0,
+                          PREC[prec] if isinstance(prec, str) else int(prec),
+                          (GTB_WCON_LITERAL if literal else 0) | (GTB_STATE48 if state48 else 0),
                           _dom(domain), ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes, _stream(stream)))
     return out
 

@@ -58,6 +58,10 @@ def battery(path):
                 o = zeros_like(sv["utens"])
                 gtb.vadv(*[sv[n] for n in names], o, prec=pr, literal=literal, beta_v=beta, domain=dom)
                 keep(f"vadv.{dt.__name__}.{pr}.{literal}.{beta}", o)
+            if pr == "df":  # the column state in 48 bits
+                o = zeros_like(sv["utens"])
+                gtb.vadv(*[sv[n] for n in names], o, prec=pr, domain=dom, state48=True)
+                keep(f"vadv_state48.{dt.__name__}", o)
             o = zeros_like(sv["utens"])
             gtb.vadv(*[sv[n] for n in names], o, prec=pr, domain=dom, workspace=None)  # shared-memory state
             keep(f"vadv_smem.{dt.__name__}.{pr}", o)

@@ -208,3 +208,40 @@ def test_general_weights_every_form(G, orc, workspace, dtype, prec):
         got, ref = run_case(G, orc, 67, 13, 41, seed=9, dtype=dtype, prec=prec, literal=literal, beta_v=beta,
                             wamp=0.25, workspace=workspace)
         assert rel_err(got, ref) <= tol, (literal, beta)
+
+
+@pytest.mark.parametrize("I,J,K,literal,beta_v,inplace", [
+    (130, 34, 45, False, 0.0, False),  # column pairs, ragged J
+    (129, 9, 37, False, 0.0, False),   # odd I: one column a thread
+    (96, 40, 137, True, 0.0, True),    # literal face velocity, in place, the ensemble's largest K
+    (70, 33, 41, False, 0.3, False),   # general weights
+])
+def test_state48_fp32_df(G, orc, I, J, K, literal, beta_v, inplace):
+    """GTB_STATE48: double-float columns whose workspace state is kept in 48 bits meet the
+    1e-5 bound against the FP64 oracle and differ from the full-width form in the last
+    bits; without a workspace (shared-memory state) the flag has no effect, bit for bit."""
+    f = {k: v.astype(np.float32) for k, v in draw(I, J, K, seed=17).items()}
+    o, dom = (1, 1, 0), (I, J, K)
+    ref = region(orc.vadv(*[f[n].astype(np.float64) for n in NAMES], origin=o, domain=dom, beta_v=beta_v,
+                          wmode=1 if literal else 0), o, dom)
+    outs = []
+    for state48, ws in ((True, "auto"), (False, "auto"), (True, None), (False, None)):
+        st = {n: G.storage_from(f[n], o) for n in NAMES}
+        out = st["utens_stage"] if inplace else G.storage_from(np.zeros_like(f["utens_stage"]), o)
+        G.vadv(*[st[n] for n in NAMES], out, prec="df", literal=literal, beta_v=beta_v, domain=dom, workspace=ws,
+               state48=state48)
+        G.device_status()
+        outs.append(region(out.numpy(), o, dom))
+    assert rel_err(outs[0], ref) <= F32_TOL
+    assert rel_err(outs[1], ref) <= F32_TOL
+    assert not np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
+    assert np.array_equal(outs[2].view(np.uint32), outs[3].view(np.uint32))
+
+
+def test_state48_rejected_outside_df_fp32(G):
+    f = draw(8, 8, 4, seed=1)
+    for dt, prec in ((np.float64, "native"), (np.float32, "native"), (np.float32, "f64")):
+        st = {n: G.storage_from(f[n].astype(dt), (1, 1, 0)) for n in NAMES}
+        with pytest.raises(G.GtbError) as e:
+            G.vadv(*[st[n] for n in NAMES], prec=prec, state48=True)
+        assert e.value.code == -9
