@@ -275,7 +275,8 @@ size_t gtb_hdiff_vadv_workspace_bytes(int dtype, int prec, unsigned flags, const
  * Both stencils share one domain (deduced from all nine fields when NULL).
  * Reach and in-place rules: as gtb_hdiff and gtb_vadv; hdiff_out may overlap
  * no other field, utens_stage_out none but possibly utens_stage itself (the
- * very same view).  dtr_stage, beta_v, prec and flags as gtb_vadv.
+ * very same view).  dtr_stage, beta_v, prec and flags (GTB_WCON_LITERAL,
+ * GTB_STATE48) as gtb_vadv.
  * workspace: REQUIRED, at least gtb_vadv_workspace_bytes() bytes, 16-byte
  * aligned, overlapping no field (NULL or too small: GTB_ERR_ARG).
  */

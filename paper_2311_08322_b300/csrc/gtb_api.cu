@@ -848,10 +848,12 @@ extern "C" int gtb_step(const gtb_field *in, const gtb_field *coeff, const gtb_f
     int rc;
     for (int q = 0; q < 9; ++q)
         if ((rc = check_field(names[q], f[q], dt))) return rc;
-    if (flags & ~GTB_WCON_LITERAL) return fail(GTB_ERR_ARG, "gtb_step: unknown flags 0x%x", flags);
+    if (flags & ~(GTB_WCON_LITERAL | GTB_STATE48)) return fail(GTB_ERR_ARG, "gtb_step: unknown flags 0x%x", flags);
     if (prec < GTB_PREC_NATIVE || prec > GTB_PREC_DF) return fail(GTB_ERR_ARG, "gtb_step: unknown prec %d", prec);
     if (dt == GTB_F64 && prec != GTB_PREC_NATIVE)
         return fail(GTB_ERR_ARG, "gtb_step: FP64 storage computes in binary64 (prec must be GTB_PREC_NATIVE)");
+    if ((flags & GTB_STATE48) && (dt != GTB_F32 || prec != GTB_PREC_DF))
+        return fail(GTB_ERR_ARG, "gtb_step: GTB_STATE48 applies to GTB_F32 storage with GTB_PREC_DF");
     if (!(dtr_stage == dtr_stage) || !(beta_v == beta_v)) return fail(GTB_ERR_ARG, "gtb_step: NaN scalar");
     const bool literal = flags & GTB_WCON_LITERAL;
     const Reach r_in{{2, 2, 0}, {2, 2, 0}}, r0{{0, 0, 0}, {0, 0, 0}}, rw{{0, 0, 0}, {literal ? 0 : 1, 0, 0}};
@@ -893,7 +895,8 @@ extern "C" int gtb_step(const gtb_field *in, const gtb_field *coeff, const gtb_f
     // on B300 the two separate kernels back to back are faster than sharing SMs
     if ((rc = run_hdiff<float>(in, coeff, hdiff_out, dom, st))) return rc;
     if (prec == GTB_PREC_F64) return run_vadv_n<float, double>(fv, g, workspace, workspace_bytes, st);
-    if (prec == GTB_PREC_DF) return run_vadv_n<float, df>(fv, g, workspace, workspace_bytes, st);
+    if (prec == GTB_PREC_DF)
+        return run_vadv_n<float, df>(fv, g, workspace, workspace_bytes, st, (flags & GTB_STATE48) != 0);
     return run_vadv_n<float, float>(fv, g, workspace, workspace_bytes, st);
 }
 

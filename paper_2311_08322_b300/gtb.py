@@ -332,10 +332,11 @@ def hdiff_vadv(in_, coeff, wcon, utens, utens_stage, out=None, *, dtr_stage=3.0 
 
 
 def step(in_, coeff, hdiff_out, u_stage, wcon, u_pos, utens, utens_stage, out=None, *, dtr_stage=3.0 / 20.0,
-         beta_v=0.0, prec="native", literal=False, domain=None, workspace="auto", stream=None):
+         beta_v=0.0, prec="native", literal=False, domain=None, workspace="auto", state48=False, stream=None):
     """Both benchmark stencils on their own fields in one co-scheduled kernel (gtb_step):
     hdiff_out = hdiff(in_, coeff); out = vadv(u_stage, wcon, u_pos, utens, utens_stage)
-    (``out=None`` updates utens_stage in place).  ``workspace``: "auto" or a CUDA tensor."""
+    (``out=None`` updates utens_stage in place).  ``workspace``: "auto" or a CUDA tensor.
+    ``state48``: as :func:`vadv`."""
     out = utens_stage if out is None else out
     fs = [_as_field(x) for x in (in_, coeff, hdiff_out, u_stage, wcon, u_pos, utens, utens_stage, out)]
     ws_ptr, ws_bytes = None, 0
@@ -349,7 +350,8 @@ def step(in_, coeff, hdiff_out, u_stage, wcon, u_pos, utens, utens_stage, out=No
     if workspace is not None:
         ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     _check(lib().gtb_step(*[ctypes.byref(f) for f in fs], float(dtr_stage), float(beta_v),
-                          PREC[prec] if isinstance(prec, str) else int(prec), GTB_WCON_LITERAL if literal else 0,
+                          PREC[prec] if isinstance(prec, str) else int(prec),
+                          (GTB_WCON_LITERAL if literal else 0) | (GTB_STATE48 if state48 else 0),
                           _dom(domain), ctypes.c_void_p(ws_ptr) if ws_ptr else None, ws_bytes, _stream(stream)))
     return out
 

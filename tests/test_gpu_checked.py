@@ -62,6 +62,9 @@ def battery(path):
                 o = zeros_like(sv["utens"])
                 gtb.vadv(*[sv[n] for n in names], o, prec=pr, domain=dom, state48=True)
                 keep(f"vadv_state48.{dt.__name__}", o)
+                h2, o2 = zeros_like(s_cf), zeros_like(sv["utens"])
+                gtb.step(s_in, s_cf, h2, *[sv[n] for n in names], o2, prec=pr, domain=dom, state48=True)
+                keep(f"step_state48.{dt.__name__}", h2, o2)
             o = zeros_like(sv["utens"])
             gtb.vadv(*[sv[n] for n in names], o, prec=pr, domain=dom, workspace=None)  # shared-memory state
             keep(f"vadv_smem.{dt.__name__}.{pr}", o)

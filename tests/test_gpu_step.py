@@ -39,7 +39,8 @@ def draw(I, J, K, seed, wamp=0.5):
     return f
 
 
-def run(G, f, dom, dtype=np.float64, prec="native", beta_v=0.0, literal=False, inplace=False, contiguous=False):
+def run(G, f, dom, dtype=np.float64, prec="native", beta_v=0.0, literal=False, inplace=False, contiguous=False,
+        state48=False):
     """(hdiff_out, utens_stage_out) of gtb_step, and utens_stage_out of gtb_vadv."""
     import torch
     g = {k: v.astype(dtype) for k, v in f.items()}
@@ -50,7 +51,7 @@ def run(G, f, dom, dtype=np.float64, prec="native", beta_v=0.0, literal=False, i
     hout = G.storage_from(np.zeros_like(g["coeff"]), (2, 2, 0))
     sv = {n: G.storage_from(g[n], (1, 1, 0)) for n in VN}
     vout = sv["utens_stage"] if inplace else G.storage_from(np.zeros_like(g["utens"]), (1, 1, 0))
-    kw = dict(prec=prec, beta_v=beta_v, literal=literal, domain=dom)
+    kw = dict(prec=prec, beta_v=beta_v, literal=literal, domain=dom, state48=state48)
     ref_v = G.storage_from(np.zeros_like(g["utens"]), (1, 1, 0))
     G.vadv(*[sv[n] for n in VN], ref_v, **kw)  # before an in-place step overwrites utens_stage
     G.step(sin, scf, hout, *[sv[n] for n in VN], vout, **kw)
@@ -136,11 +137,13 @@ def test_unread_corners_and_nonfinite_fp64(G, orc):
     assert np.array_equal(v, v1)
 
 
-@pytest.mark.parametrize("prec", ["native", "f64", "df"])
+@pytest.mark.parametrize("prec", ["native", "f64", "df", "df48"])
 def test_fp32_storage(G, orc, prec):
+    """FP32 storage: hdiff_out within 1e-5 of the oracle, utens_stage_out gtb_vadv's bit for
+    bit (df48: double-float with the column state in 48 bits, GTB_STATE48, in both calls)."""
     dom = (96, 40, 37)
     f = draw(*dom, 3)
-    h, v, v1 = run(G, f, dom, np.float32, prec)
+    h, v, v1 = run(G, f, dom, np.float32, prec[:2] if prec == "df48" else prec, state48=prec == "df48")
     f32 = {k: a.astype(np.float32).astype(np.float64) for k, a in f.items()}
     rh, rv = oracle(orc, f32, dom)
     assert rel_err(h, rh) <= F32_TOL
@@ -256,3 +259,15 @@ def test_cuda_graph_capture_fp64(G):
             assert np.array_equal(a, st.numpy(), equal_nan=True)  # halos stay NaN in both
         assert np.isfinite(region(got[0], (2, 2, 0), dom)).all()
         assert np.isfinite(region(got[2], (1, 1, 0), dom)).all()
+
+
+def test_state48_rejected_fp64(G):
+    """GTB_STATE48 applies to FP32 storage with double-float columns only (GTB_ERR_ARG)."""
+    dom = (8, 8, 4)
+    f = draw(*dom, 1)
+    sin, scf = G.storage_from(f["inp"], (2, 2, 0)), G.storage_from(f["coeff"], (2, 2, 0))
+    hout = G.storage_from(np.zeros_like(f["coeff"]), (2, 2, 0))
+    sv = {n: G.storage_from(f[n], (1, 1, 0)) for n in VN}
+    with pytest.raises(G.GtbError) as e:
+        G.step(sin, scf, hout, *[sv[n] for n in VN], state48=True)
+    assert e.value.code == -9
