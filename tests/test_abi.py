@@ -108,6 +108,11 @@ def test_vadv_validation(L):
     assert L.lib().gtb_vadv(*args(fs)) == 0
     assert L.lib().gtb_vadv(*args(fs, prec=1)) == -9       # FP64 storage: binary64 only
     assert L.lib().gtb_vadv(*args(fs, flags=4)) == -9
+    assert L.lib().gtb_vadv(*args(fs, flags=16)) == -9      # GTB_STATE48: FP32 + double-float only
+    f32 = [fake(L, 10, 10, 6, origin=(1, 1, 0), dtype=1, ptr=n * G) for n in range(1, 7)]
+    assert L.lib().gtb_vadv(*args(f32, prec=0, flags=16)) == -9
+    assert L.lib().gtb_vadv(*args(f32, prec=1, flags=16)) == -9
+    assert L.lib().gtb_vadv(*args(f32, prec=2, flags=17)) == 0  # empty domain: nothing launched
     assert L.lib().gtb_vadv(*args(fs, dom=(9, 8, 6))) == -3  # wcon needs i+1 <= 9
     assert L.lib().gtb_vadv(*args(fs, flags=1, dom=(0, 8, 6))) == 0
     big = [fake(L, 10, 10, 500, origin=(1, 1, 0), ptr=n * (1 << 28)) for n in range(1, 7)]
@@ -215,6 +220,7 @@ def test_step_validation(L):
     assert call(fs, dom=(9, 8, 6), **ok_ws) == -3                  # wcon needs i+1
     assert call(fs, prec=2, **ok_ws) == -9                         # FP64 storage: binary64 only
     assert call(fs, flags=8, **ok_ws) == -9
+    assert call(fs, flags=16, **ok_ws) == -9                       # GTB_STATE48: FP32 + double-float only
     assert call(fs[:2] + [fin(1)] + fs[3:], **ok_ws) == -5         # hdiff_out on in
     assert call(fs[:2] + [mk(4)] + fs[3:], **ok_ws) == -5          # hdiff_out on u_stage
     assert call(fs[:8] + [mk(6)], **ok_ws) == -5                   # vadv output on u_pos
