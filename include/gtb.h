@@ -233,13 +233,15 @@ int gtb_halo_periodic_adj(const gtb_field *f, int hi, int hj, const int64_t *dom
  * above I unless GTB_WCON_LITERAL (as gtb_vadv); coeff, utens, utens_stage
  * and utens_stage_out cover the domain.  utens_stage_out may be the very same
  * view as utens_stage (in place); any other overlap of the output with an
- * input is GTB_ERR_ALIAS.  dtr_stage, beta_v, prec and flags as gtb_vadv.
+ * input is GTB_ERR_ALIAS.  dtr_stage, beta_v and prec as gtb_vadv.
  * workspace: REQUIRED caller-owned device scratch of at least
  * gtb_hdiff_vadv_workspace_bytes() bytes (c', e when it cannot be parked in
  * the output, and h for GTB_F32 storage), 16-byte aligned, overlapping no
  * field; NULL or too small is GTB_ERR_ARG.  No K limit beyond the workspace
  * size.
- * flags: GTB_WCON_LITERAL, GTB_SAVE_FACTORS.  With GTB_SAVE_FACTORS the
+ * flags: GTB_WCON_LITERAL, GTB_SAVE_FACTORS (any other flag, GTB_STATE48
+ * included, is GTB_ERR_ARG: the chained call keeps its column state at full
+ * width).  With GTB_SAVE_FACTORS the
  * workspace keeps, on return, the factors of the column solve for the adjoint
  * (gtb_vadv_adj with GTB_ADJ_FACTORS): c'_k in its first K*I*J values and
  * 1/p_k in the next K*I*J (value type: binary64, or binary32 / binary64 /
