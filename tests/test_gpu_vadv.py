@@ -245,3 +245,39 @@ def test_state48_rejected_outside_df_fp32(G):
         with pytest.raises(G.GtbError) as e:
             G.vadv(*[st[n] for n in NAMES], prec=prec, state48=True)
         assert e.value.code == -9
+
+
+def test_state48_zero_pivot_column(G, orc):
+    """GTB_STATE48 on the zero-pivot column of test_zero_pivot_column (binary32 storage,
+    column pairs): the breakdown stays in that column, every other column meets 1e-5."""
+    I, J, K = 8, 2, 5
+    f = draw(I, J, K, 12, 0.1)
+    f["wcon"][1, 1, 3:5] = 1.0
+    f = {k: v.astype(np.float32) for k, v in f.items()}
+    o = (1, 1, 0)
+    st = {n: G.storage_from(f[n], o) for n in NAMES}
+    out = G.storage_from(np.zeros_like(f["utens"]), o)
+    G.vadv(*[st[n] for n in NAMES], out, dtr_stage=0.25, prec="df", state48=True)
+    G.device_status()
+    got = region(out.numpy(), o, (I, J, K)).astype(np.float64)
+    ref = region(orc.vadv(*[f[n].astype(np.float64) for n in NAMES], dtr_stage=0.25), o, (I, J, K))
+    bad_ref = ~np.all(np.isfinite(ref), axis=0)
+    bad_got = ~np.all(np.isfinite(got), axis=0)
+    assert bad_ref[0, 2] and np.array_equal(bad_ref, bad_got)
+    assert rel_err(got[:, ~bad_ref], ref[:, ~bad_ref]) <= F32_TOL
+
+
+def test_state48_largest_ensemble_member(G, orc):
+    """GTB_STATE48 at the ensemble's largest member shape, 384x384x137 (the longest columns
+    and the most live state), within 1e-5 of the FP64 oracle on the FP32-rounded inputs."""
+    from paper_2311_08322_b300 import inputs
+    I, J, K = 384, 384, 137
+    f = {k: v.astype(np.float32) for k, v in inputs.hdiff_vadv(I, J, K, seed=2).items()}
+    o = (1, 1, 0)
+    st = {n: G.storage_from(f[n], o) for n in NAMES}
+    out = G.storage_from(np.zeros_like(f["utens"]), o)
+    G.vadv(*[st[n] for n in NAMES], out, prec="df", state48=True)
+    G.device_status()
+    got = region(out.numpy(), o, (I, J, K))
+    ref = region(orc.vadv(*[f[n].astype(np.float64) for n in NAMES]), o, (I, J, K))
+    assert rel_err(got, ref) <= F32_TOL
