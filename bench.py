@@ -421,23 +421,31 @@ def run_gtb(args):
         gtb.vadv(*[s[n] for n in VADV_NAMES], s["vout"], stream=stream)
         ev[2].record(stream)
 
-    for w in range(args.warmup):
-        step(sets[w % len(sets)])
-    gtb.device_status()
-
+    # the FP64 rate probe (outside the timed region, on every rank's GPU) and the clock
+    # sampler's start come before the warm-up steps, so that the timed steps follow the
+    # warm-up with no idle gap in between
+    fma_gops = fp64_fma_rate()
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         uuid = str(dev)
     clocks = ClockSampler(uuid)
     clocks.start()
+    for w in range(args.warmup - 1):
+        step(sets[w % len(sets)])
+    gtb.device_status()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    # the last of the W warm-up steps goes after the barrier: the start event then fires
+    # as it completes, with the first timed step already queued behind it, so the timed
+    # region holds the K steps' device time and not the host's first launch latency
+    if args.warmup > 0:
+        step(sets[(args.warmup - 1) % len(sets)])
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for q in range(args.steps):
-        step(sets[q % len(sets)])
+    for q in range(args.steps):  # the input sets rotate on from the warm-up's
+        step(sets[(args.warmup + q) % len(sets)])
     t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -536,7 +544,6 @@ def run_gtb(args):
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6400.0))
     hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs, torch copy)" if "hbm_gbs" in peaks else "fallback 6.4 TB/s"
-    fma_gops = fp64_fma_rate() if rank == 0 else None
     kern = {}
     hb, vb = hdiff_bytes(I, J, K, 8), vadv_bytes(I, J, K, 8)
     for name, ms, nbytes in (("step", st_ms, hb + vb), ("hdiff", h_ms, hb), ("vadv", v_ms, vb)):
