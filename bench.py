@@ -701,6 +701,7 @@ def fused_chain_compare(gtb, f, sets, reps=50):
         for q in range(5):
             fn(q)
         torch.cuda.synchronize()
+        fn(-1)  # untimed: the start event then fires behind it, with the first timed call queued
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for q in range(reps):
@@ -828,6 +829,7 @@ def batched_compare(hbm, reps=20):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
+        fn()  # untimed: the start event then fires behind it, with the first timed call queued
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
@@ -893,6 +895,7 @@ def precision_compare(hbm, reps=20):
         for q in range(4):
             fn(q)
         torch.cuda.synchronize()
+        fn(-1)  # untimed: the start event then fires behind it, with the first timed call queued
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for q in range(reps):
